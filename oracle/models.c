@@ -1,0 +1,338 @@
+/*
+ * Oracle models: DDM, LCA, layered logistic transfer network, predator-prey
+ * grid search. Plain FP64, one trial at a time, steps in the paper's order.
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include "oracle.h"
+
+/* Noise stream of one (seed, trial, candidate): normal d is lane d&3 of the
+   Box-Muller output of Philox block d>>2 (purpose 0). Keeps the last block so
+   consecutive draws do not recompute it. */
+typedef struct {
+  uint64_t seed;
+  uint32_t trial, cand;
+  int64_t block;
+  double z[4];
+} noise_stream;
+
+static void noise_open(noise_stream* s, uint64_t seed, uint32_t trial, uint32_t cand) {
+  s->seed = seed;
+  s->trial = trial;
+  s->cand = cand;
+  s->block = -1;
+}
+
+static double noise_at(noise_stream* s, uint64_t d) {
+  int64_t block = (int64_t)(d >> 2);
+  if (block != s->block) {
+    uint32_t w[4];
+    or_philox_words(s->seed, s->trial, s->cand, 0u, (uint32_t)block, 1, w);
+    or_box_muller(w, s->z);
+    s->block = block;
+  }
+  return s->z[d & 3];
+}
+
+/* ------------------------------------------------------------------ DDM --- */
+
+void or_ddm_run(const float* A, const float* z, const uint32_t* trial_ids, int64_t n_ids,
+                uint64_t seed, double dt, double sigma, double x0, int32_t max_steps,
+                int8_t* choice, int32_t* step, double* x_final, double* margin) {
+  const double diffusion = sigma * sqrt(dt);
+  for (int64_t k = 0; k < n_ids; ++k) {
+    uint32_t t = trial_ids[k];
+    double drift = (double)A[t];
+    double bound = (double)z[t];
+    noise_stream ns;
+    noise_open(&ns, seed, t, 0u);
+    double x = x0;
+    double m = INFINITY;
+    int8_t c = -1;
+    int32_t s = max_steps;
+    for (int32_t j = 1; j <= max_steps; ++j) {
+      double eps = noise_at(&ns, (uint64_t)(j - 1));
+      x = x + (drift * dt + diffusion * eps);
+      double d = fabs(fabs(x) - bound);
+      if (d < m) m = d;
+      if (fabs(x) >= bound) {
+        c = (x > 0.0) ? 1 : 0;
+        s = j;
+        break;
+      }
+    }
+    if (choice) choice[k] = c;
+    if (step) step[k] = s;
+    if (x_final) x_final[k] = x;
+    if (margin) margin[k] = m;
+  }
+}
+
+/* ------------------------------------------------------------------ LCA --- */
+
+void or_lca_run(int N, const float* I, const uint32_t* trial_ids, int64_t n_ids,
+                uint64_t seed, double leak, double inhibition, double sigma, double dt,
+                double threshold, int32_t max_steps, int rectify, int two_sided,
+                int8_t* choice, int32_t* step, double* x_final, double* margin) {
+  const double diffusion = sigma * sqrt(dt);
+  double* x = (double*)malloc(sizeof(double) * (size_t)N);
+  double* xn = (double*)malloc(sizeof(double) * (size_t)N);
+  for (int64_t k = 0; k < n_ids; ++k) {
+    uint32_t t = trial_ids[k];
+    const float* in = I + (size_t)t * (size_t)N;
+    noise_stream ns;
+    noise_open(&ns, seed, t, 0u);
+    for (int i = 0; i < N; ++i) x[i] = 0.0;
+    double m = INFINITY;
+    int8_t c = -1;
+    int32_t s = max_steps;
+    for (int32_t j = 1; j <= max_steps; ++j) {
+      /* synchronous update: every unit reads the step j-1 values */
+      for (int i = 0; i < N; ++i) {
+        double others = 0.0;
+        for (int q = 0; q < N; ++q)
+          if (q != i) others += x[q];
+        double eps = noise_at(&ns, (uint64_t)(j - 1) * (uint64_t)N + (uint64_t)i);
+        double v = x[i] + (((double)in[i] - leak * x[i] - inhibition * others) * dt +
+                           diffusion * eps);
+        if (rectify && v < 0.0) v = 0.0;
+        xn[i] = v;
+      }
+      memcpy(x, xn, sizeof(double) * (size_t)N);
+      if (two_sided) {
+        double d = fabs(fabs(x[0]) - threshold);
+        if (d < m) m = d;
+        if (fabs(x[0]) >= threshold) {
+          c = (x[0] > 0.0) ? 1 : 0;
+          s = j;
+          break;
+        }
+      } else {
+        int best = 0;
+        for (int i = 1; i < N; ++i)
+          if (x[i] > x[best]) best = i;
+        double d = fabs(x[best] - threshold);
+        if (d < m) m = d;
+        if (x[best] >= threshold) {
+          c = (int8_t)best;
+          s = j;
+          break;
+        }
+      }
+    }
+    if (choice) choice[k] = c;
+    if (step) step[k] = s;
+    if (x_final)
+      for (int i = 0; i < N; ++i) x_final[(size_t)k * (size_t)N + (size_t)i] = x[i];
+    if (margin) margin[k] = m;
+  }
+  free(x);
+  free(xn);
+}
+
+/* ------------------------------------------------------ transfer network --- */
+
+static double logistic(double gain, double bias, double s) {
+  return 1.0 / (1.0 + exp(-gain * (s + bias)));
+}
+
+/* top1 - top2 and the index of top1 (lowest index on exact ties) */
+static double top_gap(const double* y, int n, int* arg) {
+  int best = 0;
+  for (int i = 1; i < n; ++i)
+    if (y[i] > y[best]) best = i;
+  double second = -INFINITY;
+  for (int i = 0; i < n; ++i)
+    if (i != best && y[i] > second) second = y[i];
+  *arg = best;
+  if (n == 1) return y[best];
+  return y[best] - second;
+}
+
+void or_transfer_run(const or_net* net, const float* cond_inputs, int n_cond, int cond_block,
+                     const uint32_t* trial_ids, int64_t n_ids, uint64_t seed,
+                     int8_t* choice, int32_t* step, double* y_final, double* margin,
+                     double* trace, int32_t trace_steps) {
+  int L = net->n_layers;
+  int off[OR_MAX_LAYERS + 1];     /* unit offset of each layer (all units) */
+  int noisy_off[OR_MAX_LAYERS];   /* offset among logistic units, -1 for inputs */
+  int n_in = 0, U = 0;
+  off[0] = 0;
+  for (int l = 0; l < L; ++l) {
+    off[l + 1] = off[l] + net->size[l];
+    if (net->is_input[l]) {
+      noisy_off[l] = -1;
+      n_in += net->size[l];
+    } else {
+      noisy_off[l] = U;
+      U += net->size[l];
+    }
+  }
+  int total = off[L];
+  double* y = (double*)malloc(sizeof(double) * (size_t)total);
+  double* yn = (double*)malloc(sizeof(double) * (size_t)total);
+  double* s = (double*)malloc(sizeof(double) * (size_t)total);
+  double* sn = (double*)malloc(sizeof(double) * (size_t)total);
+  int sl = net->stop_layer;
+  int ssize = net->size[sl];
+  int32_t run_steps = net->max_steps;
+  if (trace && trace_steps > run_steps) run_steps = trace_steps;
+
+  for (int64_t k = 0; k < n_ids; ++k) {
+    uint32_t t = trial_ids[k];
+    int cond = (int)((t / (uint32_t)cond_block) % (uint32_t)n_cond);
+    const float* cin = cond_inputs + (size_t)cond * (size_t)n_in;
+    noise_stream ns;
+    noise_open(&ns, seed, t, 0u);
+    /* step 0: inputs clamped, logistic units at s = 0 */
+    int in_pos = 0;
+    for (int l = 0; l < L; ++l) {
+      for (int i = 0; i < net->size[l]; ++i) {
+        int u = off[l] + i;
+        if (net->is_input[l]) {
+          y[u] = (double)cin[in_pos++];
+          s[u] = 0.0;
+        } else {
+          s[u] = 0.0;
+          y[u] = logistic(net->gain[l], net->bias[l], 0.0);
+        }
+      }
+    }
+    double* tr = trace ? trace + (size_t)k * (size_t)(trace_steps + 1) * (size_t)total : NULL;
+    if (tr) memcpy(tr, y, sizeof(double) * (size_t)total);
+
+    double m = INFINITY;
+    int8_t c = -1;
+    int32_t st = net->max_steps;
+    int stopped = 0;
+    double yst[64];
+    for (int32_t j = 1; j <= run_steps; ++j) {
+      /* synchronous update (Sec. 3.3): all layers read the step j-1 outputs y */
+      for (int l = 0; l < L; ++l) {
+        for (int i = 0; i < net->size[l]; ++i) {
+          int u = off[l] + i;
+          if (net->is_input[l]) {
+            sn[u] = s[u];
+            yn[u] = y[u];
+            continue;
+          }
+          double nt = 0.0;
+          for (int p = 0; p < net->n_proj; ++p) {
+            if (net->proj_receiver[p] != l) continue;
+            int snd = net->proj_sender[p];
+            const float* w = net->proj_w[p] + (size_t)i * (size_t)net->size[snd];
+            for (int q = 0; q < net->size[snd]; ++q) nt += (double)w[q] * y[off[snd] + q];
+          }
+          double eps = noise_at(&ns, (uint64_t)(j - 1) * (uint64_t)U +
+                                         (uint64_t)(noisy_off[l] + i));
+          sn[u] = (1.0 - net->rate) * s[u] + net->rate * nt + net->noise_sd * eps;
+          yn[u] = logistic(net->gain[l], net->bias[l], sn[u]);
+        }
+      }
+      memcpy(s, sn, sizeof(double) * (size_t)total);
+      memcpy(y, yn, sizeof(double) * (size_t)total);
+      if (tr && j <= trace_steps) memcpy(tr + (size_t)j * (size_t)total, y, sizeof(double) * (size_t)total);
+      if (!stopped && j <= net->max_steps) {
+        int arg;
+        double gap = top_gap(y + off[sl], ssize, &arg);
+        double d = fabs(gap - net->stop_threshold);
+        if (d < m) m = d;
+        if (gap > net->stop_threshold) {
+          stopped = 1;
+          c = (int8_t)arg;
+          st = j;
+          for (int i = 0; i < ssize && i < 64; ++i) yst[i] = y[off[sl] + i];
+        }
+      }
+      if (stopped && (!tr || j >= trace_steps)) break;
+      if (!stopped && j >= net->max_steps && (!tr || j >= trace_steps)) break;
+    }
+    if (!stopped)
+      for (int i = 0; i < ssize && i < 64; ++i) yst[i] = y[off[sl] + i];
+    /* with a trace longer than max_steps, y has moved on; the timeout value is
+       the one at max_steps, which the trace holds */
+    if (!stopped && tr && trace_steps > net->max_steps)
+      for (int i = 0; i < ssize && i < 64; ++i)
+        yst[i] = tr[(size_t)net->max_steps * (size_t)total + (size_t)(off[sl] + i)];
+    if (choice) choice[k] = c;
+    if (step) step[k] = st;
+    if (margin) margin[k] = m;
+    if (y_final)
+      for (int i = 0; i < ssize && i < 64; ++i) y_final[(size_t)k * (size_t)ssize + (size_t)i] = yst[i];
+  }
+  free(y);
+  free(yn);
+  free(s);
+  free(sn);
+}
+
+/* ------------------------------------------------- predator-prey grid --- */
+
+static void unit2(double vx, double vy, double* ox, double* oy) {
+  double n = sqrt(vx * vx + vy * vy);
+  if (n > 0.0) {
+    *ox = vx / n;
+    *oy = vy / n;
+  } else {
+    *ox = 0.0;
+    *oy = 0.0;
+  }
+}
+
+double or_pp_outcome(const float pos[6], const double a[3], uint64_t seed, uint32_t trial,
+                     uint32_t cand, double obs_offset, double pred_weight, double* perceived) {
+  noise_stream ns;
+  noise_open(&ns, seed, trial, cand);
+  double ph[6];
+  for (int e = 0; e < 3; ++e) {
+    double sd = 1.0 / (obs_offset + a[e]);
+    for (int c = 0; c < 2; ++c) {
+      int d = 2 * e + c;
+      ph[d] = (double)pos[d] + sd * noise_at(&ns, (uint64_t)d);
+    }
+  }
+  if (perceived)
+    for (int d = 0; d < 6; ++d) perceived[d] = ph[d];
+  /* entity order: player (0,1), predator (2,3), prey (4,5) */
+  double uyx, uyy, udx, udy, ax, ay;
+  unit2(ph[4] - ph[0], ph[5] - ph[1], &uyx, &uyy);
+  unit2(ph[2] - ph[0], ph[3] - ph[1], &udx, &udy);
+  unit2(uyx - pred_weight * udx, uyy - pred_weight * udy, &ax, &ay);
+  double nx = (double)pos[0] + ax - (double)pos[4];
+  double ny = (double)pos[1] + ay - (double)pos[5];
+  double cost = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+  return -sqrt(nx * nx + ny * ny) - cost;
+}
+
+void or_pp_means(const float* pos, int32_t n_trials, const float* lv0, int32_t L0,
+                 const float* lv1, int32_t L1, const float* lv2, int32_t L2,
+                 const uint32_t* cand_ids, int64_t n_ids, uint64_t seed,
+                 double obs_offset, double pred_weight, double* means) {
+  (void)L0;
+  for (int64_t k = 0; k < n_ids; ++k) {
+    uint32_t c = cand_ids[k];
+    uint32_t l2 = c % (uint32_t)L2;
+    uint32_t l1 = (c / (uint32_t)L2) % (uint32_t)L1;
+    uint32_t l0 = c / ((uint32_t)L2 * (uint32_t)L1);
+    double a[3] = {(double)lv0[l0], (double)lv1[l1], (double)lv2[l2]};
+    double sum = 0.0;
+    for (int32_t j = 0; j < n_trials; ++j)
+      sum += or_pp_outcome(pos + 6 * (size_t)j, a, seed, (uint32_t)j, c, obs_offset,
+                           pred_weight, NULL);
+    means[k] = sum / (double)n_trials;
+  }
+}
+
+void or_argmax(const double* v, int64_t n, int64_t* best, double* best_value, double* gap) {
+  int64_t b = 0;
+  for (int64_t i = 1; i < n; ++i)
+    if (v[i] > v[b]) b = i;
+  double second = -INFINITY;
+  for (int64_t i = 0; i < n; ++i)
+    if (i != b && v[i] > second) second = v[i];
+  *best = b;
+  *best_value = v[b];
+  *gap = (n > 1) ? v[b] - second : 0.0;
+}

@@ -1,0 +1,160 @@
+/*
+ * Oracle: a plain, slow FP64 CPU simulator of the cognitive-model hot path of
+ * "Distill: Domain-Specific Compilation for Cognitive Models" (arXiv 2110.15425).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing on the product path may link, import or
+ * call this library: only the test suite, the smoke check in __graft_entry__
+ * and the CPU-baseline leg of bench.py use it. It shares no code, header,
+ * constant table or helper with the CUDA library.
+ *
+ * Every model is written step by step in the order the paper (and the reading
+ * of it recorded in the design notes) describes, in double precision, with no
+ * blocking, fusion or reordering. Random draws come from this file's own
+ * Philox4x32-10 (Salmon et al., SC'11) and Box-Muller transform.
+ *
+ * Pinned by the tests under tests/test_oracle_*.py:
+ *   - Philox words: cross-checked bitwise against an independent
+ *     Philox4x32-10 (Triton's CPU interpreter) and statistical checks.
+ *   - Box-Muller: moments, KS test, radius/angle identities.
+ *   - DDM: closed-form choice probability and mean decision time.
+ *   - LCA: DDM equivalence mapping (Sec. 4.4, Fig. clones), noise-free fixed
+ *     point, closed-form leak-only crossing step, rectification invariant.
+ *   - Transfer network: integrator closed form, synchronous-update delay,
+ *     logistic range, stop-rule closed form.
+ *   - Grid search: noise-free geometric limits, perception variance,
+ *     candidate index layout, lowest-index argmax.
+ */
+#ifndef DISTILL_ORACLE_H
+#define DISTILL_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- RNG --- */
+
+/* One Philox4x32-10 block: out = Philox(ctr, key). Salmon et al. SC'11. */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Raw words of blocks block0 .. block0+nblocks-1 of the stream
+   key = (seed lo, seed hi), counter = (trial, cand, block, purpose).
+   out has 4*nblocks words. */
+void or_philox_words(uint64_t seed, uint32_t trial, uint32_t cand, uint32_t purpose,
+                     uint32_t block0, int64_t nblocks, uint32_t* out);
+
+/* u = ((w >> 8) + 1/2) * 2^-24, in (0, 1). */
+double or_uniform(uint32_t w);
+
+/* Box-Muller on (w0,w1) and (w2,w3): z[0..3]. */
+void or_box_muller(const uint32_t w[4], double z[4]);
+
+/* Normals d0 .. d0+n-1 of the noise stream (purpose 0) of (seed, trial, cand). */
+void or_normals(uint64_t seed, uint32_t trial, uint32_t cand, uint64_t d0, int64_t n,
+                double* out);
+
+/* ---------------------------------------------------------------- DDM --- */
+
+/* Drift-diffusion run to threshold (Sec. 4.4; config: batched DDM).
+   For each k in 0..n_ids-1, trial t = trial_ids[k] uses A[t], z[t]:
+     x_0 = x0;  x_j = x_{j-1} + (A dt + sigma sqrt(dt) eps_j)  (eps_j = normal j-1)
+   stop at the first j with |x_j| >= z. choice = 1 if x_j > 0 else 0; step = j.
+   No crossing within max_steps: choice = -1, step = max_steps.
+   x_final = x at the stop step; margin = min over j <= stop of ||x_j| - z|.
+   Any output pointer may be NULL. */
+void or_ddm_run(const float* A, const float* z, const uint32_t* trial_ids, int64_t n_ids,
+                uint64_t seed, double dt, double sigma, double x0, int32_t max_steps,
+                int8_t* choice, int32_t* step, double* x_final, double* margin);
+
+/* ---------------------------------------------------------------- LCA --- */
+
+/* Leaky competing accumulator (Sec. 4.4; Usher-McClelland form). Trial t uses
+   inputs I[t*N .. t*N+N-1]. All N units are updated synchronously:
+     x_i <- x_i + ((I_i - k x_i - beta sum_{j!=i} x_j) dt + sigma sqrt(dt) eps_i)
+     x_i <- max(0, x_i)                   when rectify != 0
+   eps_i of step j (1-based) is normal (j-1)*N + i.
+   one-sided (two_sided == 0): stop when max_i x_i >= threshold;
+     choice = argmax_i x_i (lowest index on exact ties).
+   two-sided (N == 1 only): stop when |x| >= threshold; choice = (x > 0).
+   Timeout: choice = -1, step = max_steps.
+   x_final: N values per trial (may be NULL); margin: min over j <= stop of
+   |max_i x_i - threshold| (one-sided) or ||x| - threshold| (two-sided). */
+void or_lca_run(int N, const float* I, const uint32_t* trial_ids, int64_t n_ids,
+                uint64_t seed, double leak, double inhibition, double sigma, double dt,
+                double threshold, int32_t max_steps, int rectify, int two_sided,
+                int8_t* choice, int32_t* step, double* x_final, double* margin);
+
+/* ------------------------------------------------------ transfer network --- */
+
+#define OR_MAX_LAYERS 16
+#define OR_MAX_PROJ 32
+
+typedef struct {
+  int n_layers;
+  int size[OR_MAX_LAYERS];
+  int is_input[OR_MAX_LAYERS];   /* 1: clamped input layer; 0: logistic layer */
+  double gain[OR_MAX_LAYERS];
+  double bias[OR_MAX_LAYERS];
+  double rate;                   /* time-averaging rate tau */
+  double noise_sd;               /* sd of the noise added to the state */
+  int n_proj;
+  int proj_sender[OR_MAX_PROJ];
+  int proj_receiver[OR_MAX_PROJ];
+  const float* proj_w[OR_MAX_PROJ]; /* [receiver size][sender size], row-major */
+  int stop_layer;
+  double stop_threshold;         /* stop when top1 - top2 > threshold (strict) */
+  int32_t max_steps;
+} or_net;
+
+/* Layered logistic time-averaging network (Sec. 2.2, 3.3; Botvinick Stroop).
+   cond_inputs: [n_cond][total input units] (input layers in layer order).
+   Trial t takes condition (t / cond_block) % n_cond.
+   s(0) = 0, y(0) = logistic(gain*(0 + bias)); step j = 1..max_steps, all
+   layers read the step j-1 outputs:
+     s <- (1 - rate) s + rate net + noise_sd eps,  y = 1 / (1 + exp(-gain (s + bias)))
+   eps of noisy unit u (logistic units numbered in layer order) at step j is
+   normal (j-1)*U + u, U = number of logistic units.
+   Stop at the first j where top1 - top2 of the stop layer > threshold:
+   choice = index of top1 (lowest index on exact ties), step = j.
+   Timeout: choice = -1, step = max_steps.
+   y_final: stop-layer outputs at the stop step ([n_ids][stop size], may be NULL).
+   margin: min over j <= stop of |(top1 - top2) - threshold|.
+   trace (may be NULL): outputs of every unit (all layers, in layer order) at
+   steps 0..trace_steps, [n_ids][trace_steps+1][total units]; the trace keeps
+   running past the stop step so closed forms can be checked at any j. */
+void or_transfer_run(const or_net* net, const float* cond_inputs, int n_cond, int cond_block,
+                     const uint32_t* trial_ids, int64_t n_ids, uint64_t seed,
+                     int8_t* choice, int32_t* step, double* y_final, double* margin,
+                     double* trace, int32_t trace_steps);
+
+/* ------------------------------------------------- predator-prey grid --- */
+
+/* One evaluation of the predator-prey model (Sec. 2.1, Fig. pp_eg) for
+   allocation a[0..2] (player, predator, prey) on trial `trial` of candidate
+   `cand`. pos = true positions (player xy, predator xy, prey xy).
+   Perceived X^_e = X_e + eps_{2e+c} / (obs_offset + a_e), eps from stream
+   (seed, trial, cand). u_prey = unit(Y^ - P^), u_pred = unit(D^ - P^),
+   act = unit(u_prey - pred_weight u_pred), unit(0) = 0.
+   outcome = -|P + act - Y| - sum_e a_e^2. perceived (may be NULL) gets X^. */
+double or_pp_outcome(const float pos[6], const double a[3], uint64_t seed, uint32_t trial,
+                     uint32_t cand, double obs_offset, double pred_weight, double* perceived);
+
+/* Per-candidate mean outcome over trials 0..n_trials-1 (summed in index order)
+   for candidates cand_ids[0..n_ids-1]. Candidate c has levels
+   (l0, l1, l2) with c = (l0*L1 + l1)*L2 + l2 and allocation
+   (lv0[l0], lv1[l1], lv2[l2]). pos: [n_trials][6]. */
+void or_pp_means(const float* pos, int32_t n_trials, const float* lv0, int32_t L0,
+                 const float* lv1, int32_t L1, const float* lv2, int32_t L2,
+                 const uint32_t* cand_ids, int64_t n_ids, uint64_t seed,
+                 double obs_offset, double pred_weight, double* means);
+
+/* argmax with lowest index on exact ties; gap = best - second best (0 on a tie;
+   0 when n == 1). */
+void or_argmax(const double* v, int64_t n, int64_t* best, double* best_value, double* gap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif
