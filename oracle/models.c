@@ -116,6 +116,10 @@ void or_lca_run(int N, const float* I, const uint32_t* trial_ids, int64_t n_ids,
         double d = fabs(x[best] - threshold);
         if (d < m) m = d;
         if (x[best] >= threshold) {
+          double second = -INFINITY;
+          for (int i = 0; i < N; ++i)
+            if (i != best && x[i] > second) second = x[i];
+          if (N > 1 && x[best] - second < m) m = x[best] - second;
           c = (int8_t)best;
           s = j;
           break;

@@ -44,7 +44,7 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 void or_philox_words(uint64_t seed, uint32_t trial, uint32_t cand, uint32_t purpose,
                      uint32_t block0, int64_t nblocks, uint32_t* out);
 
-/* u = ((w >> 8) + 1/2) * 2^-24, in (0, 1). */
+/* u = ((w >> 9) + 1/2) * 2^-23, in (0, 1); exact in binary32. */
 double or_uniform(uint32_t w);
 
 /* Box-Muller on (w0,w1) and (w2,w3): z[0..3]. */
@@ -79,7 +79,9 @@ void or_ddm_run(const float* A, const float* z, const uint32_t* trial_ids, int64
    two-sided (N == 1 only): stop when |x| >= threshold; choice = (x > 0).
    Timeout: choice = -1, step = max_steps.
    x_final: N values per trial (may be NULL); margin: min over j <= stop of
-   |max_i x_i - threshold| (one-sided) or ||x| - threshold| (two-sided). */
+   |max_i x_i - threshold| (one-sided) or ||x| - threshold| (two-sided); in the
+   one-sided case with N > 1 it also takes the gap between the largest and the
+   second largest x at the stop step, since the winner is decided there. */
 void or_lca_run(int N, const float* I, const uint32_t* trial_ids, int64_t n_ids,
                 uint64_t seed, double leak, double inhibition, double sigma, double dt,
                 double threshold, int32_t max_steps, int rectify, int two_sided,

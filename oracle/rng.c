@@ -56,8 +56,9 @@ void or_philox_words(uint64_t seed, uint32_t trial, uint32_t cand, uint32_t purp
 }
 
 double or_uniform(uint32_t w) {
-  /* top 24 bits plus one half, times 2^-24: strictly inside (0, 1) */
-  return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0);
+  /* top 23 bits plus one half, times 2^-23: strictly inside (0, 1), and
+     exactly representable in binary32 as well as binary64 */
+  return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0);
 }
 
 void or_box_muller(const uint32_t w[4], double z[4]) {

@@ -89,16 +89,20 @@ def test_philox_statistics(orc):
     chi2 = float(((counts - exp) ** 2 / exp).sum())
     # 255 dof: mean 255, sd ~22.6; 6 sd bound
     assert abs(chi2 - 255.0) < 6 * math.sqrt(2 * 255.0)
-    u = ((w >> np.uint64(8)).astype(np.float64) + 0.5) / 2.0**24
+    u = ((w >> np.uint64(9)).astype(np.float64) + 0.5) / 2.0**23
     r = np.corrcoef(u[:-1], u[1:])[0, 1]
     assert abs(r) < 5 / math.sqrt(n)
 
 
 def test_uniform_range_and_grid(orc):
-    assert orc.uniform(0) == 2.0**-25
-    assert orc.uniform(0xFFFFFFFF) == 1.0 - 2.0**-25
-    assert orc.uniform(0x000000FF) == 2.0**-25          # low 8 bits are dropped
-    assert orc.uniform(0x80000000) == 0.5 + 2.0**-25
+    assert orc.uniform(0) == 2.0**-24
+    assert orc.uniform(0xFFFFFFFF) == 1.0 - 2.0**-24
+    assert orc.uniform(0x000001FF) == 2.0**-24          # low 9 bits are dropped
+    assert orc.uniform(0x80000000) == 0.5 + 2.0**-24
+    # every value is exactly representable in binary32
+    for w in [0, 1 << 9, 0x7FFFFE00, 0xFFFFFFFF, 0x12345678]:
+        u = orc.uniform(w)
+        assert float(np.float32(u)) == u
 
 
 def test_box_muller_identities(orc):
