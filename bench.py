@@ -1,0 +1,650 @@
+#!/usr/bin/env python
+"""Benchmark of the cognitive-model hot path on GB300.
+
+One step = one pass of the whole hot path over one batch of synthetic input:
+  Stroop (4 x 1,000 trials), DDM (2^20 trials), LCA (262,144 trials at
+  N = 4, 8, 16), predator-prey grid search (27,000 candidates x 64 trials)
+  and the wide multitask network, launched together as one CUDA-graph batch
+  (each job on its own branch, so their tails overlap).
+value = trial-steps per second of that pass (a grid evaluation counts as one
+trial-step). Also reported: the plain one-launch-per-job form on the same
+GPU, the dominant kernel's roofline, an end-to-end number through the serving
+API with host buffers, served-mix p50/p99 latency, and the CPU oracle.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Multi-GPU: launched by torchrun, one process per GPU, weak scaling: rank r
+runs the same pass on its own trials (global ids r*n .. r*n + n - 1, so its
+noise differs) and its own predator-prey positions; no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "trial-steps/sec (hot-path pass: DDM, LCA, Stroop, wide Stroop, grid search)"
+UNIT = "trial-steps/s"
+WORKLOAD = ("hot-path pass: Stroop 4x1000 (weights seed 0) + DDM 2^20 + LCA 262144 x N{4,8,16} "
+            "+ predator-prey grid 27000 cand x 64 trials + wide Stroop 16384 (16+16 -> 256 -> 16)")
+# algorithmic lane-operations per DDM trial-step (Philox4x32-10 quarter block,
+# one uniform and half a Box-Muller pair, the compensated update and the test)
+DDM_OPS_PER_TRIAL_STEP = 32
+LANES_PER_SM = 128
+WIDE_TRIALS = 16384
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--profile-once", action="store_true",
+                    help="run warmup + 1 step only (for ncu launch lists)")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, local, world
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ step ---
+
+class Step:
+    """Device inputs/outputs and models of one hot-path pass (this rank's shard)."""
+
+    def __init__(self, B, W, torch, ctx, rank, world):
+        def shard_range(n, rank, world):
+            # weak scaling: every rank takes a full job of its own trials
+            return rank * n, rank * n + n
+        self.B, self.torch = B, torch
+        cuda = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+        self.jobs = []      # (name, kind, model, desc, outputs)
+        self.inputs_bytes = 0
+
+        def out_run(n, state=0):
+            return dict(choice=torch.zeros(max(n, 1), dtype=torch.int8, device="cuda"),
+                        step=torch.zeros(max(n, 1), dtype=torch.int32, device="cuda"))
+
+        # Stroop small
+        s = W.stroop_small()
+        lo, hi = shard_range(s["n_trials"], rank, world)
+        m = B.compose_network(ctx, s["layers"], s["projections"], rate=s["rate"],
+                              noise_sd=s["noise_sd"], stop_layer=s["stop_layer"],
+                              stop_threshold=s["stop_threshold"], max_steps=s["max_steps"])
+        cond = cuda(s["cond_inputs"])
+        d = B.run_desc(hi - lo, s["seed"], cond_inputs=cond, n_cond=4, cond_block=s["cond_block"],
+                       trial_offset=lo)
+        self.jobs.append(dict(name="stroop", model=m, desc=d, out=out_run(hi - lo), keep=[cond],
+                              host_in=[s["cond_inputs"]], n=hi - lo))
+        # DDM
+        w = W.ddm()
+        n = w["A"].shape[0]
+        lo, hi = shard_range(n, rank, world)
+        m = B.compose_ddm(ctx, dt=w["dt"], sigma=w["sigma"], max_steps=w["max_steps"])
+        hp = np.concatenate([w["A"], w["z"]])
+        p = cuda(hp)
+        d = B.run_desc(hi - lo, w["seed"], trial_params=p, trial_offset=lo)
+        self.jobs.append(dict(name="ddm", model=m, desc=d, out=out_run(hi - lo), keep=[p],
+                              host_in=[hp], n=hi - lo))
+        # LCA
+        for N in (4, 8, 16):
+            l = W.lca(N=N)
+            n = l["I"].shape[0]
+            lo, hi = shard_range(n, rank, world)
+            m = B.compose_lca(ctx, N, leak=l["leak"], inhibition=l["inhibition"], sigma=l["sigma"],
+                              dt=l["dt"], threshold=l["threshold"], max_steps=l["max_steps"])
+            hp = l["I"]
+            p = cuda(hp)
+            d = B.run_desc(hi - lo, l["seed"], trial_params=p, trial_offset=lo)
+            self.jobs.append(dict(name=f"lca{N}", model=m, desc=d, out=out_run(hi - lo), keep=[p],
+                                  host_in=[hp], n=hi - lo))
+        # wide Stroop (tensor cores); skipped when this build has no wide kernel
+        wd = W.stroop_wide(n_trials=WIDE_TRIALS)
+        try:
+            m = B.compose_network(ctx, wd["layers"], wd["projections"], rate=wd["rate"],
+                                  noise_sd=wd["noise_sd"], stop_layer=wd["stop_layer"],
+                                  stop_threshold=wd["stop_threshold"], max_steps=wd["max_steps"],
+                                  bf16_edges=(2,))
+            lo, hi = shard_range(WIDE_TRIALS, rank, world)
+            cond = cuda(wd["cond_inputs"])
+            d = B.run_desc(hi - lo, wd["seed"], cond_inputs=cond, n_cond=cond.shape[0],
+                           cond_block=1, trial_offset=lo)
+            probe = out_run(1)
+            B.dg_run(m, B.run_desc(1, wd["seed"], cond_inputs=cond, n_cond=cond.shape[0],
+                                   cond_block=1), probe["choice"], probe["step"])
+            self.jobs.append(dict(name="wide", model=m, desc=d, out=out_run(hi - lo), keep=[cond],
+                                  host_in=[wd["cond_inputs"]], n=hi - lo))
+        except B.DGError:
+            self.wide_missing = True
+        # predator-prey grid
+        g = W.predator_prey(pos_seed=3 + rank)
+        lo, hi = 0, 30 * 30 * 30
+        m = B.compose_predator_prey(ctx, obs_offset=g["obs_offset"], pred_weight=g["pred_weight"])
+        lv = [cuda(x) for x in g["levels"]]
+        pos = cuda(g["pos"])
+        d = B.grid_desc(lv, pos, g["seed"])
+        res = torch.zeros(3, dtype=torch.float64, device="cuda")
+        self.jobs.append(dict(name="grid", model=m, desc=d, grid=True,
+                              out=dict(result=res), keep=lv + [pos],
+                              host_in=[g["pos"]] + g["levels"], n=hi - lo,
+                              evals=(hi - lo) * g["pos"].shape[0]))
+        self.batch = None
+
+    def run_plain(self):
+        B = self.B
+        for j in self.jobs:
+            if j.get("grid"):
+                d = j["desc"]
+                d.mode = B.DG_MODE_PLAIN
+                B.dg_grid_search(j["model"], d, j["out"]["result"])
+                d.mode = B.DG_MODE_BATCHED
+            else:
+                d = j["desc"]
+                d.mode = B.DG_MODE_PLAIN
+                B.dg_run(j["model"], d, j["out"]["choice"], j["out"]["step"])
+                d.mode = B.DG_MODE_BATCHED
+
+    def launch(self, ctx):
+        B = self.B
+        if self.batch is None:
+            self.batch = B.dg_batch_create(ctx)
+            for j in self.jobs:
+                if j.get("grid"):
+                    B.dg_batch_add_grid(self.batch, j["model"], j["desc"], j["out"]["result"])
+                else:
+                    B.dg_batch_add_run(self.batch, j["model"], j["desc"], j["out"]["choice"],
+                                       j["out"]["step"])
+        B.dg_batch_launch(self.batch)
+
+    def trial_steps(self):
+        """Per-job trial-steps of the pass (from the step outputs)."""
+        self.torch.cuda.synchronize()
+        ts = {}
+        for j in self.jobs:
+            if j.get("grid"):
+                ts[j["name"]] = j["evals"]
+            else:
+                ts[j["name"]] = int(j["out"]["step"][:j["n"]].to(self.torch.int64).sum().item())
+        return ts
+
+    def kernels_per_step(self):
+        return len(self.jobs)
+
+
+# ---------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is None:
+            return
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        if not self.out:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------- CPU oracle ---
+
+def cpu_baseline(seconds_hint=True):
+    """The oracle as it stands, on this host's cores, over a bounded sample of
+    the same pass (a fixed fraction of every job). Returns (value, cores, sample)."""
+    import oracle
+    from paper_2110_15425_gb300 import workloads as W
+    threads = os.cpu_count() or 1
+    frac = 16
+    t0 = time.perf_counter()
+    steps = 0
+    s = W.stroop_small()
+    ids = np.arange(0, s["n_trials"], 8, dtype=np.uint32)
+    o = oracle.transfer_run(s["layers"], s["projections"], s["cond_inputs"], s["cond_block"],
+                            s["seed"], trial_ids=ids, threads=threads)
+    steps += int(o["step"].sum())
+    w = W.ddm()
+    ids = np.arange(0, w["A"].shape[0], frac, dtype=np.uint32)
+    o = oracle.ddm_run(w["A"], w["z"], w["seed"], trial_ids=ids, threads=threads)
+    steps += int(o["step"].sum())
+    for N in (4, 8, 16):
+        l = W.lca(N=N)
+        ids = np.arange(0, l["I"].shape[0], frac, dtype=np.uint32)
+        o = oracle.lca_run(l["I"], l["seed"], trial_ids=ids, threads=threads)
+        steps += int(o["step"].sum())
+    wd = W.stroop_wide(n_trials=WIDE_TRIALS)
+    ids = np.arange(0, WIDE_TRIALS, frac * 4, dtype=np.uint32)
+    o = oracle.transfer_run(wd["layers"], wd["projections"], wd["cond_inputs"], 1, wd["seed"],
+                            trial_ids=ids, threads=threads)
+    steps += int(o["step"].sum())
+    g = W.predator_prey()
+    ids = np.arange(0, 27000, frac, dtype=np.uint32)
+    oracle.pp_means(g["pos"], g["levels"], g["seed"], cand_ids=ids, threads=threads)
+    steps += ids.shape[0] * g["pos"].shape[0]
+    dt = time.perf_counter() - t0
+    sample = (f"every 8th Stroop trial, every {frac}th DDM/LCA trial and grid candidate, every "
+              f"{frac * 4}th wide trial: {steps} trial-steps in {dt:.1f} s")
+    return steps / dt, threads, sample
+
+
+# ------------------------------------------------------------- reference ---
+
+def run_reference(args):
+    rank, local, world = dist_env()
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        pass
+    sample = cores = None
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        v, cores, sample = cpu_baseline()
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * wall / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ main ---
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, local, world = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2110_15425_gb300 import binding as B
+    from paper_2110_15425_gb300 import workloads as W
+    try:
+        B.lib()
+    except RuntimeError:
+        from paper_2110_15425_gb300 import build as BB
+        BB.build()
+    ctx = B.dg_create(local)
+    step = Step(B, W, torch, ctx, rank, world)
+    pk, pk_kind = peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up: the first launch tunes shapes and captures the graph
+    for _ in range(max(3, args.warmup)):
+        step.launch(ctx)
+    ts = step.trial_steps()
+    total_ts = sum(ts.values())
+    l2_flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    K = 1 if args.profile_once else args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    barrier()
+    with ClockSampler(local) as clk:
+        for i in range(K):
+            l2_flush.zero_()
+            starts[i].record()
+            step.launch(ctx)
+            ends[i].record()
+        barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(step_ms) / K
+    if world > 1:
+        t = torch.tensor([ms, float(total_ts)], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        ms, all_ts = float(mx[0]), float(t[1])
+    else:
+        all_ts = float(total_ts)
+    if args.profile_once:
+        if rank == 0:
+            print(json.dumps({"profile_once": True, "ms": ms}))
+        return
+    value = all_ts / (ms / 1000.0)
+
+    # plain form: one launch per job, no refill, no graph, one stream
+    barrier()
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step.run_plain()
+    barrier()
+    plain_ms = []
+    for _ in range(3):
+        l2_flush.zero_()
+        pe0.record()
+        step.run_plain()
+        pe1.record()
+        torch.cuda.synchronize()
+        plain_ms.append(pe0.elapsed_time(pe1))
+    plain_ms = statistics.mean(plain_ms)
+    ts_plain = step.trial_steps()
+    plain_same = ts_plain == ts
+    # restore batched outputs for later checks
+    step.launch(ctx)
+
+    # per-job kernel times (each alone, batched form) and the dominant kernel
+    per_job = {}
+    ddm_ms = None
+    for j in step.jobs:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        times = []
+        for _ in range(3):
+            l2_flush.zero_()
+            e0.record()
+            if j.get("grid"):
+                B.dg_grid_search(j["model"], j["desc"], j["out"]["result"])
+            else:
+                B.dg_run(j["model"], j["desc"], j["out"]["choice"], j["out"]["step"])
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        t_ms = statistics.mean(times)
+        per_job[j["name"]] = {"ms": round(t_ms, 4), "trial_steps": ts[j["name"]],
+                              "trial_steps_per_s": ts[j["name"]] / (t_ms / 1000.0)}
+        if j["name"] == "grid":
+            per_job["grid"]["candidates_per_s"] = j["n"] / (t_ms / 1000.0)
+        if j["name"] == "ddm":
+            ddm_ms = t_ms
+    dominant = max(per_job, key=lambda k: per_job[k]["ms"])
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    peak_ops = sms * LANES_PER_SM * sm_max * 1e6
+    ddm_ops = ts["ddm"] * DDM_OPS_PER_TRIAL_STEP
+    achieved = ddm_ops / (ddm_ms / 1000.0)
+    roofline = {"bound": "alu", "kernel": "ddm_batched", "achieved": achieved / 1e12,
+                "peak": peak_ops / 1e12, "unit": "Tlane-op/s", "frac": achieved / peak_ops,
+                "traffic": None,
+                "peak_source": f"{sms} SMs x {LANES_PER_SM} FP32/INT32 lanes x {sm_max:.0f} MHz "
+                               f"({pk_kind} max SM clock)",
+                "ops_per_trial_step": DDM_OPS_PER_TRIAL_STEP, "dominant_in_pass": dominant}
+
+    # end to end through the serving API with pinned host buffers
+    e2e = None
+    serving = None
+    if not args.no_serving:
+        e2e = e2e_serving(B, torch, ctx, step, all_ts, world, rank)
+        if world == 1:
+            serving = served_mix(B, W, torch, ctx, step)
+
+    gpu_launches = step.kernels_per_step() * K
+    clocks = clk.summary()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = cpu_baseline()
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "flushed between timed steps (512 MB write)",
+                       "parallelism": f"dp{world} (independent passes)" if world > 1 else "1 GPU",
+                       "wide_member": "missing" if getattr(step, "wide_missing", False) else "on"},
+            "plain_form": {"ms_per_step": plain_ms, "value": all_ts / (plain_ms / 1000.0),
+                           "speedup_batched_vs_plain": plain_ms / ms,
+                           "same_trial_steps_as_batched": plain_same},
+            "per_job": per_job,
+            "grid_candidates_per_s": per_job["grid"]["candidates_per_s"],
+            "roofline": roofline, "e2e": e2e, "serving": serving, "gpu_launches": gpu_launches,
+            "clocks": clocks, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    for j in step.jobs:
+        B.dg_model_free(j["model"])
+    B.dg_destroy(ctx)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _pinned(torch, a):
+    t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    return t, t.numpy()
+
+
+def e2e_serving(B, torch, ctx, step, all_ts, world, rank):
+    """The pass through dg_submit/dg_wait: host inputs copied in, outputs
+    copied back, every step."""
+    host_jobs = []
+    h2d = d2h = 0
+    for j in step.jobs:
+        job = B.dg_job()
+        job.model = j["model"].value
+        keep = []
+        if j.get("grid"):
+            d = j["desc"]
+            job.is_grid = 1
+            job.grid = B.dg_grid_desc.from_buffer_copy(d)
+            pos_t, pos = _pinned(torch, j["host_in"][0])
+            keep.append(pos_t)
+            job.grid.positions = pos.ctypes.data
+            for i in range(3):
+                lt, lv = _pinned(torch, j["host_in"][1 + i])
+                keep.append(lt)
+                job.grid.levels[i] = lv.ctypes.data
+                h2d += lv.nbytes
+            h2d += pos.nbytes
+            rt, res = _pinned(torch, np.zeros(3, np.float64))
+            keep.append(rt)
+            job.grid_result = res.ctypes.data
+            d2h += 24
+        else:
+            d = j["desc"]
+            job.run = B.dg_run_desc.from_buffer_copy(d)
+            pt, hp = _pinned(torch, j["host_in"][0])
+            keep.append(pt)
+            if d.trial_params:
+                job.run.trial_params = hp.ctypes.data
+            else:
+                job.run.cond_inputs = hp.ctypes.data
+            h2d += hp.nbytes
+            ct, ch = _pinned(torch, np.zeros(max(1, j["n"]), np.int8))
+            st, sp = _pinned(torch, np.zeros(max(1, j["n"]), np.int32))
+            keep += [ct, st]
+            job.choice = ch.ctypes.data
+            job.step = sp.ctypes.data
+            d2h += j["n"] * 5
+        host_jobs.append((job, keep))
+
+    def one():
+        tickets = [B.dg_submit(ctx, jb) for jb, _ in host_jobs]
+        for t in tickets:
+            B.dg_wait(ctx, t, 600000)
+
+    one()
+    one()
+    times = []
+    for _ in range(3):
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        one()
+        times.append(time.perf_counter() - t0)
+    sec = statistics.mean(times)
+    if world > 1:
+        t = torch.tensor([sec], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        sec = float(t[0])
+    return {"value": all_ts / sec, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": 1000 * sec,
+            "api": "dg_submit/dg_wait (serving loop, pinned host buffers)"}
+
+
+def served_mix(B, W, torch, ctx, step, n_jobs=48, seed=7):
+    """Served mix: Poisson arrivals of jobs drawn uniformly from the five
+    workloads, trial counts log-uniform in [1e3, 1e6], admitted under the
+    150 GB budget; arrival rate 0.7x the measured capacity."""
+    rng = np.random.default_rng(seed)
+    kinds = ["stroop", "ddm", "lca", "grid", "wide"]
+    models = {j["name"]: j["model"] for j in step.jobs}
+    have_wide = "wide" in models
+    jobs = []
+    for i in range(n_jobs):
+        k = kinds[rng.integers(0, 5 if have_wide else 4)]
+        n = int(round(10 ** rng.uniform(3, 6)))
+        jobs.append((k, n, int(rng.integers(0, 1 << 31))))
+    prepared = []
+    for k, n, sd in jobs:
+        job = B.dg_job()
+        keep = []
+        if k == "grid":
+            L = int(min(30, max(2, round((n / 64) ** (1 / 3)))))
+            g = W.predator_prey(levels=L, noise_seed=sd)
+            job.model = models["grid"].value
+            job.is_grid = 1
+            pt, pos = _pinned(torch, g["pos"])
+            keep.append(pt)
+            job.grid.positions = pos.ctypes.data
+            job.grid.n_trials = 64
+            job.grid.seed = sd
+            for i in range(3):
+                lt, lv = _pinned(torch, g["levels"][i])
+                keep.append(lt)
+                job.grid.levels[i] = lv.ctypes.data
+                job.grid.n_levels[i] = L
+            rt, res = _pinned(torch, np.zeros(3, np.float64))
+            keep += [rt, res]
+            job.grid_result = res.ctypes.data
+        else:
+            if k == "stroop":
+                s = W.stroop_small()
+                job.model = models["stroop"].value
+                ht, h = _pinned(torch, s["cond_inputs"])
+                job.run.cond_inputs = h.ctypes.data
+                job.run.n_cond, job.run.cond_block = 4, max(1, n // 4)
+            elif k == "wide":
+                wd = W.stroop_wide(n_trials=n)
+                job.model = models["wide"].value
+                ht, h = _pinned(torch, wd["cond_inputs"])
+                job.run.cond_inputs = h.ctypes.data
+                job.run.n_cond, job.run.cond_block = 256, 1
+            elif k == "ddm":
+                w = W.ddm(n_trials=n, param_seed=sd)
+                job.model = models["ddm"].value
+                ht, h = _pinned(torch, np.concatenate([w["A"], w["z"]]))
+                job.run.trial_params = h.ctypes.data
+            else:
+                l = W.lca(n_trials=n, N=8, input_seed=sd)
+                job.model = models["lca8"].value
+                ht, h = _pinned(torch, l["I"])
+                job.run.trial_params = h.ctypes.data
+            keep.append(ht)
+            job.run.n_trials = n
+            job.run.seed = sd
+            ct, ch = _pinned(torch, np.zeros(n, np.int8))
+            st, sp = _pinned(torch, np.zeros(n, np.int32))
+            keep += [ct, st, sp]
+            job.choice = ch.ctypes.data
+            job.step = sp.ctypes.data
+        prepared.append((k, n, job, keep))
+    # capacity: run all jobs back to back once (also warms the allocator)
+    t0 = time.perf_counter()
+    for k, n, job, keep in prepared:
+        B.dg_wait(ctx, B.dg_submit(ctx, job), 600000)
+    serial = time.perf_counter() - t0
+    rate = 0.7 * n_jobs / serial
+    gaps = rng.exponential(1.0 / rate, n_jobs)
+    tickets = []
+    t_start = time.perf_counter()
+    next_t = t_start
+    for (k, n, job, keep), g in zip(prepared, gaps):
+        next_t += g
+        while time.perf_counter() < next_t:
+            time.sleep(min(0.0005, max(0.0, next_t - time.perf_counter())))
+        tickets.append(B.dg_submit(ctx, job))
+    lat = []
+    total_steps = 0
+    for (k, n, job, keep), t in zip(prepared, tickets):
+        r = B.dg_wait(ctx, t, 600000)
+        lat.append(r.t_done - r.t_submit)
+        # keep[-1] is the job's host step array
+        total_steps += job.grid.n_levels[0] ** 3 * 64 if k == "grid" else int(keep[-1].sum())
+    wall = time.perf_counter() - t_start
+    lat.sort()
+    return {"jobs": n_jobs, "arrival_rate_per_s": rate, "wall_s": wall,
+            "p50_ms": 1000 * lat[len(lat) // 2], "p99_ms": 1000 * lat[min(len(lat) - 1,
+                                                                      int(math.ceil(0.99 * len(lat))) - 1)],
+            "jobs_per_s": n_jobs / wall, "trial_steps_per_s": total_steps / wall,
+            "serial_s": serial, "mix": "stroop/ddm/lca8/grid" + ("/wide" if have_wide else "")}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,291 @@
+/*
+ * distill_gpu.h - C ABI of a GB300 (sm_103a) library that runs the data-parallel
+ * hot path of the cognitive models compiled by Distill (arXiv 2110.15425):
+ * many independent stochastic trials of a PsyNeuLink-style composition, and
+ * the grid search of an optimization-control mechanism.
+ *
+ * The calls follow the paper's statement of the problem:
+ *   - compose a model graph of nodes (mechanisms) and edges (projections)
+ *     (Sec. 2.1);
+ *   - run it for a number of trials, iterating each trial until its end
+ *     condition (Sec. 2.2, Listing 1);
+ *   - let the Control node simulate every allocation of a grid and pick the
+ *     best one (Sec. 2.1, Sec. 3.6).
+ * Dynamic structures become static ones with integer ids (Sec. 3.3), and the
+ * sanitization run of Sec. 2.2 becomes compose-time shape validation.
+ *
+ * Conventions (every entry point):
+ *   - Returns dg_status; nothing throws across the ABI. On an error the
+ *     outputs are left unwritten and dg_last_error() describes the failure.
+ *   - "device" pointers are CUDA global-memory addresses (e.g. a torch
+ *     tensor's data_ptr()); "host" pointers are ordinary CPU memory.
+ *   - Inputs and outputs are owned by the caller. A model owns the device
+ *     copies of its weights from dg_compose until dg_model_free.
+ *   - Work on a `stream` (a cudaStream_t, NULL = legacy default stream) is
+ *     asynchronous and ordered on that stream; outputs are valid once the
+ *     stream has reached that point.
+ *   - Random draws: Philox4x32-10 keyed by (seed lo, seed hi) with counter
+ *     (trial, candidate, block, 0). Normal d of a (trial, candidate) stream
+ *     is lane d&3 of the Box-Muller output of block d>>2; the uniform of word
+ *     w is ((w >> 9) + 1/2) 2^-23. Results depend only on (inputs, seed), never
+ *     on launch shape, so any trial can be replayed alone.
+ */
+#ifndef DISTILL_GPU_H
+#define DISTILL_GPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DG_OK = 0,
+  DG_E_ARG = -1,          /* null pointer, bad enum value, size out of range */
+  DG_E_SHAPE = -2,        /* model graph or sizes fail compose-time validation */
+  DG_E_BUDGET = -3,       /* request larger than the context's HBM budget */
+  DG_E_CUDA = -4,         /* a CUDA call failed (message has the CUDA error) */
+  DG_E_TIMEOUT = -5,      /* dg_wait ran out of time, or a device wait gave up */
+  DG_E_UNSUPPORTED = -6,  /* valid graph that no kernel implements */
+  DG_E_STATE = -7         /* call not valid in the object's current state */
+} dg_status;
+
+typedef enum {
+  DG_INPUT = 0,             /* clamped input layer: y = the trial's input values */
+  DG_TRANSFER_LOGISTIC = 1, /* time-averaging logistic layer (Sec. 2.1, 5 Stroop) */
+  DG_DDM = 2,               /* drift-diffusion integrator (Sec. 4.4) */
+  DG_LCA = 3,               /* leaky competing accumulator (Sec. 4.4, 5 Multitasking) */
+  DG_PP_OBSERVE = 4,        /* Obs nodes: noisy view of 3 entity positions (Sec. 2.1) */
+  DG_PP_ACTION = 5,         /* Action node: one unit step (Sec. 2.1) */
+  DG_PP_OBJECTIVE = 6       /* Objective node: -distance to prey - allocation cost (Sec. 2.1) */
+} dg_mech_kind;
+
+/* dg_mechanism.flags (DG_LCA only) */
+#define DG_LCA_NO_RECTIFY 1 /* do not clamp accumulators at 0 */
+#define DG_LCA_TWO_SIDED 2  /* size 1 only: stop at |x| >= threshold, choice = (x > 0) */
+
+/* dg_projection.dtype: precision of the device copy of the weights */
+#define DG_F32 0
+#define DG_BF16 1 /* round-to-nearest-even bfloat16; only the wide hidden->response edge */
+
+/* dg_run_desc.mode */
+#define DG_MODE_BATCHED 0 /* persistent kernel, trials refilled as others finish, autotuned */
+#define DG_MODE_PLAIN 1   /* one thread per trial, one launch, no refill (comparison form) */
+
+typedef struct {
+  int32_t kind;       /* dg_mech_kind */
+  int32_t size;       /* number of units */
+  double gain, bias;  /* TRANSFER_LOGISTIC: y = 1 / (1 + exp(-gain (s + bias))) */
+  double rate;        /* TRANSFER_LOGISTIC: s <- (1 - rate) s + rate net + noise eps */
+  double noise;       /* TRANSFER_LOGISTIC: sd added to s each step;
+                         DDM, LCA: sigma, scaled by sqrt(dt) */
+  double dt;          /* DDM, LCA: Euler step */
+  double leak;        /* LCA: k */
+  double inhibition;  /* LCA: beta (lateral inhibition) */
+  double start;       /* DDM: x0 */
+  double offset;      /* PP_OBSERVE: perception sd = 1 / (offset + allocation) */
+  double weight;      /* PP_ACTION: act = unit(unit(prey - player) - weight unit(predator - player)) */
+  int32_t flags;      /* DG_LCA_* */
+  int32_t reserved;
+} dg_mechanism;
+
+typedef struct {
+  int32_t sender;        /* index into the mechanism array */
+  int32_t receiver;
+  const float* weights;  /* host, FP32 [receiver size][sender size] row-major; copied at compose */
+  int32_t dtype;         /* DG_F32 or DG_BF16 */
+  int32_t reserved;
+} dg_projection;
+
+typedef struct {
+  int32_t mech;          /* mechanism whose outputs decide the end of a trial */
+  int32_t max_steps;     /* iterations per trial at most (>= 1) */
+  double threshold;      /* LCA: max_i x_i >= threshold; TRANSFER: top1 - top2 > threshold;
+                            DDM: unused (per-trial threshold) */
+} dg_stop;
+
+typedef struct dg_ctx dg_ctx;
+typedef struct dg_model dg_model;
+
+/* Per-trial work of dg_run. */
+typedef struct {
+  int64_t n_trials;           /* >= 0; at most 2^31 - 1 */
+  int64_t trial_offset;       /* global id of trial 0 of this call (>= 0, offset + n_trials
+                                 <= 2^32): the random stream and the condition of local trial t
+                                 are those of trial offset + t, so a job split across calls or
+                                 GPUs, or resumed at any trial, reproduces the whole job */
+  uint64_t seed;              /* Philox key */
+  const float* trial_params;  /* device. DDM: [2][n_trials] (row 0 drift A, row 1 threshold z);
+                                 LCA: [n_trials][N] inputs I; TRANSFER: unused (NULL) */
+  const float* cond_inputs;   /* device. TRANSFER: [n_cond][input units of all DG_INPUT
+                                 layers in mechanism order]; else unused */
+  int32_t n_cond;             /* TRANSFER: global trial g takes condition (g / cond_block) % n_cond */
+  int32_t cond_block;
+  int32_t mode;               /* DG_MODE_* */
+  int32_t reserved;
+} dg_run_desc;
+
+/* Control grid of dg_grid_search (predator-prey models). */
+typedef struct {
+  int32_t n_levels[3];        /* levels per control signal (player, predator, prey) */
+  int32_t n_trials;           /* noisy trials per candidate, 1 .. 1024 */
+  const float* levels[3];     /* device, allocation values of each signal */
+  const float* positions;     /* device, [n_trials][6]: player xy, predator xy, prey xy */
+  uint64_t seed;
+  int32_t mode;               /* DG_MODE_* */
+  int32_t reserved;
+  int64_t cand_begin;         /* evaluate candidates cand_begin .. cand_begin + cand_count - 1 */
+  int64_t cand_count;         /* (0 = all); cand_means[i] is candidate cand_begin + i, and
+                                 best_index is a global candidate index */
+} dg_grid_desc;
+
+typedef struct {
+  int64_t best_index;         /* c = (l0 * L1 + l1) * L2 + l2; lowest index on exact ties */
+  double best_value;          /* FP64 mean outcome of the best candidate */
+  double runner_up_gap;       /* best_value - second best value (0 on a tie) */
+} dg_grid_result;
+
+/* ---------------------------------------------------------------- context --- */
+
+/* Create a context on CUDA device `device`. hbm_budget_bytes bounds the device
+   memory the serving loop may hold for admitted jobs (0 = 150 GB). */
+dg_status dg_create(dg_ctx** out, int device, size_t hbm_budget_bytes);
+dg_status dg_destroy(dg_ctx* ctx);
+
+/* Thread-local description of the last error on the calling thread; never NULL. */
+const char* dg_last_error(void);
+
+/* Library version, e.g. "distill-gpu 0.1 sm_103a". */
+const char* dg_version(void);
+
+/* ---------------------------------------------------------------- compose --- */
+
+/* Validate a model graph (Sec. 2.2 sanitization) and lay it out statically
+   (Sec. 3.3). Recognised graphs:
+     - DDM:      one DG_DDM mechanism of size 1; no projections.
+     - LCA:      one DG_LCA mechanism, size 1..16 (optionally fed by one DG_INPUT of
+                 the same size through an identity projection with NULL weights).
+     - TRANSFER: DG_INPUT and DG_TRANSFER_LOGISTIC layers; every projection runs
+                 from an earlier mechanism to a logistic layer; the stop mechanism is
+                 a logistic layer of size 2..16. Up to 32 logistic units run on the
+                 small-network kernel; the wide form (two one-hot input layers ->
+                 hidden of 64..256 units, multiple of 64 -> response of 16 units with a
+                 DG_BF16 hidden->response projection) runs on the tensor-core kernel.
+     - PREDATOR_PREY: DG_INPUT(6) -> DG_PP_OBSERVE(6) -> DG_PP_ACTION(2) ->
+                 DG_PP_OBJECTIVE(1), chained by projections with NULL weights.
+   Weights are copied to the device (synchronously) before return.
+   Errors: DG_E_ARG (null/invalid values), DG_E_SHAPE (graph not valid),
+   DG_E_UNSUPPORTED (valid but outside the kernels' limits), DG_E_CUDA. */
+dg_status dg_compose(dg_ctx* ctx, const dg_mechanism* mechs, int32_t n_mech,
+                     const dg_projection* projs, int32_t n_proj, const dg_stop* stop,
+                     dg_model** out);
+dg_status dg_model_free(dg_model* model);
+
+/* Model kind (0 DDM, 1 LCA, 2 TRANSFER small, 3 TRANSFER wide, 4 PREDATOR_PREY)
+   and the number of floats dg_run writes per trial into final_state. */
+dg_status dg_model_info(const dg_model* model, int32_t* kind, int32_t* state_size);
+
+/* -------------------------------------------------------------------- run --- */
+
+/* Run desc->n_trials independent trials of a DDM, LCA or TRANSFER model, each
+   until its stop condition or stop.max_steps (Sec. 2.2, Listing 1).
+   Outputs (device, caller-owned, n_trials entries):
+     choice: DDM 1 = upper bound, 0 = lower; LCA winner index; TRANSFER index
+             of the largest stop-layer output; -1 = no decision by max_steps.
+     step:   iteration at which the trial ended (1-based), max_steps on timeout.
+     final_state (may be NULL): [n_trials][state_size] FP32 state at the end
+             (DDM x; LCA x_0..x_{N-1}; TRANSFER stop-layer outputs).
+   Errors: DG_E_ARG, DG_E_UNSUPPORTED (PREDATOR_PREY model), DG_E_CUDA. */
+dg_status dg_run(dg_model* model, const dg_run_desc* desc, int8_t* choice, int32_t* step,
+                 float* final_state, void* stream);
+
+/* Predator-prey grid search (Sec. 2.1, 3.6): simulate every candidate
+   allocation over desc->n_trials noisy trials, average the outcomes in FP64,
+   and take the argmax (lowest index on exact ties).
+   result: device pointer to one dg_grid_result.
+   cand_means (may be NULL): device, FP64 [L0 L1 L2] mean outcome per candidate.
+   Errors: DG_E_ARG, DG_E_UNSUPPORTED (not a PREDATOR_PREY model), DG_E_CUDA. */
+dg_status dg_grid_search(dg_model* model, const dg_grid_desc* desc, dg_grid_result* result,
+                         double* cand_means, void* stream);
+
+/* Argmax over n FP64 values (device), lowest index on exact ties, into a
+   device dg_grid_result. n >= 1. */
+dg_status dg_argmax_f64(dg_ctx* ctx, const double* values, int64_t n, dg_grid_result* result,
+                        void* stream);
+
+/* ------------------------------------------------------ RNG replay (parity) --- */
+
+/* Raw Philox4x32-10 words of blocks block0 .. block0+nblocks-1 of
+   counter (trial, cand, block, purpose), key (seed lo, seed hi).
+   out: device, 4*nblocks uint32. */
+dg_status dg_philox_words(uint64_t seed, uint32_t trial, uint32_t cand, uint32_t purpose,
+                          uint32_t block0, int64_t nblocks, uint32_t* out, void* stream);
+
+/* Normals d0 .. d0+n-1 of the noise stream of (seed, trial, cand), FP32, as the
+   kernels draw them. out: device, n floats. */
+dg_status dg_normals(uint64_t seed, uint32_t trial, uint32_t cand, uint64_t d0, int64_t n,
+                     float* out, void* stream);
+
+/* ---------------------------------------------------------------- batching --- */
+
+/* A batch is a fixed set of runs and grid searches launched together: the
+   first dg_batch_launch captures them as parallel branches of one CUDA graph
+   (each on its own forked stream, so their tails overlap on the device);
+   later launches replay that graph. Pointers and sizes are fixed when added. */
+typedef struct dg_batch dg_batch;
+dg_status dg_batch_create(dg_ctx* ctx, dg_batch** out);
+dg_status dg_batch_add_run(dg_batch* b, dg_model* model, const dg_run_desc* desc,
+                           int8_t* choice, int32_t* step, float* final_state);
+dg_status dg_batch_add_grid(dg_batch* b, dg_model* model, const dg_grid_desc* desc,
+                            dg_grid_result* result, double* cand_means);
+dg_status dg_batch_launch(dg_batch* b, void* stream);
+dg_status dg_batch_free(dg_batch* b);
+
+/* ---------------------------------------------------------------- serving --- */
+
+/* A job for the serving loop. Inputs and outputs are HOST memory (pinned memory
+   makes the copies asynchronous); the loop copies inputs to device memory it
+   owns, runs the job, and copies the outputs back. */
+typedef struct {
+  dg_model* model;
+  int32_t is_grid;            /* 0: dg_run job; 1: dg_grid_search job */
+  int32_t reserved;
+  dg_run_desc run;            /* trial_params / cond_inputs are HOST pointers here */
+  dg_grid_desc grid;          /* levels / positions are HOST pointers here */
+  int8_t* choice;             /* host outputs of a run job (final_state may be NULL) */
+  int32_t* step;
+  float* final_state;
+  dg_grid_result* grid_result;  /* host output of a grid job */
+  double* cand_means;           /* host, may be NULL */
+} dg_job;
+
+typedef struct {
+  int32_t status;             /* dg_status of the job */
+  int32_t reserved;
+  double t_submit, t_admit, t_done;  /* seconds on the host's steady clock */
+  uint64_t device_bytes;      /* device memory the job held */
+} dg_job_result;
+
+/* Queue a job; returns at once with a ticket. The serving loop admits queued
+   jobs in arrival order while the HBM budget has room, runs admitted jobs
+   concurrently (each on its own stream, continuous batching), and frees a
+   job's memory when its results are on the host.
+   Errors: DG_E_ARG; DG_E_BUDGET if the job alone exceeds the budget. */
+dg_status dg_submit(dg_ctx* ctx, const dg_job* job, uint64_t* ticket);
+
+/* Wait up to timeout_ms (< 0: no limit) for a ticket. DG_E_TIMEOUT if it is
+   not done by then (the job keeps running; wait again later). On DG_OK the
+   job's host outputs are written and *result describes it. A ticket can be
+   waited for successfully once. */
+dg_status dg_wait(dg_ctx* ctx, uint64_t ticket, int32_t timeout_ms, dg_job_result* result);
+
+/* Serving counters: jobs queued, running, done; device bytes in use. */
+dg_status dg_serve_stats(dg_ctx* ctx, int64_t* queued, int64_t* running, int64_t* done,
+                         uint64_t* bytes_in_use);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -1,0 +1,100 @@
+// Device building blocks shared by every kernel of the library: counter-based
+// random numbers and warp-level trial scheduling.
+//
+// Random draws (Sec. 3.6 asks that every evaluation draw reproducible,
+// independent numbers; the paper restores a per-evaluation PRNG state on each
+// call, which costs ~7.5 kB per GPU thread). Here the generator is
+// Philox4x32-10 (Salmon et al., SC'11) with no state at all: block b of the
+// stream of (seed, trial, candidate) is Philox(counter = (trial, candidate,
+// b, 0), key = (seed lo, seed hi)). Normal d of the stream is lane d & 3 of
+// the Box-Muller transform of block d >> 2.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dg {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// One Philox4x32-10 block. Each round multiplies words 0 and 2 by the two
+// round multipliers, then mixes the high halves with words 1 and 3 and the
+// key; the key advances by the two Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 noise_block(uint32_t k0, uint32_t k1, uint32_t trial,
+                                             uint32_t cand, uint32_t block) {
+  return philox(make_uint4(trial, cand, block, 0u), k0, k1);
+}
+
+// u = ((w >> 9) + 1/2) 2^-23: the 24-bit odd numerator is exact in binary32,
+// so the fma below is exact.
+__device__ __forceinline__ float u01(uint32_t w) {
+  return fmaf(__uint2float_rn(w >> 9), 0x1p-23f, 0x1p-24f);
+}
+
+// Box-Muller (1958): radius from the first word, angle from the second.
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& z0, float& z1) {
+  const float r = sqrtf(-2.0f * logf(u01(wa)));
+  float s, c;
+  sincospif(2.0f * u01(wb), &s, &c);
+  z0 = r * c;
+  z1 = r * s;
+}
+
+__device__ __forceinline__ float4 normals4(uint4 w) {
+  float4 z;
+  box_muller(w.x, w.y, z.x, z.y);
+  box_muller(w.z, w.w, z.z, z.w);
+  return z;
+}
+
+__device__ __forceinline__ float pick4(const float4& z, uint32_t lane) {
+  const float a = (lane & 1u) ? z.y : z.x;
+  const float b = (lane & 1u) ? z.w : z.z;
+  return (lane & 2u) ? b : a;
+}
+
+// Error-free sum (Knuth's TwoSum): x + inc = s + err exactly. The state is
+// carried as x + c, so FP32 drift over thousands of steps stays at the level
+// of the increments' own rounding.
+__device__ __forceinline__ void comp_add(float& x, float& c, float inc) {
+  const float s = x + inc;
+  const float bp = s - x;
+  const float err = (x - (s - bp)) + (inc - bp);
+  x = s;
+  c += err;
+}
+
+// Warp-aggregated fetch of trial ids from a global cursor: every lane of the
+// warp must call it; lanes with `need` get consecutive new ids (or -1 when no
+// lane needs one). One atomic per warp per call.
+__device__ __forceinline__ long long fetch_trial(unsigned long long* cursor, bool need) {
+  const unsigned mask = __ballot_sync(kFull, need);
+  if (mask == 0u) return -1;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(cursor, (unsigned long long)__popc(mask));
+  base = __shfl_sync(kFull, base, leader);
+  if (!need) return -1;
+  return (long long)(base + (unsigned long long)__popc(mask & ((1u << lane) - 1u)));
+}
+
+__device__ __forceinline__ float logistic(float gain, float bias, float s) {
+  return 1.0f / (1.0f + expf(-gain * (s + bias)));
+}
+
+}  // namespace dg

@@ -1,0 +1,153 @@
+// Internal interface between the host runtime (runtime.cpp) and the kernel
+// translation units. Plain structs of device pointers and scalars; no torch.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dg {
+
+// Launch shape chosen by the runtime (autotuned for the batched kernels).
+struct LaunchCfg {
+  int block = 256;   // threads per block
+  int grid = 0;      // blocks; 0 = one per SM times occupancy
+  int tpt = 1;       // threads per trial (LCA)
+};
+
+// ------------------------------------------------------------------ DDM ---
+struct DdmParams {
+  const float* A;      // [n] drift
+  const float* z;      // [n] threshold
+  int64_t n;
+  uint32_t trial0;     // global id of local trial 0 (RNG counter)
+  uint32_t k0, k1;     // Philox key
+  float dt;            // Euler step (FP32 copy)
+  float diffusion;     // sigma * sqrt(dt), rounded once from FP64
+  float x0;
+  int max_steps;
+  int8_t* choice;
+  int32_t* step;
+  float* xout;         // may be null
+  unsigned long long* cursor;  // batched form: global trial cursor (zeroed per launch)
+};
+cudaError_t launch_ddm(const DdmParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
+int ddm_max_blocks_per_sm(int block);
+
+// ------------------------------------------------------------------ LCA ---
+struct LcaParams {
+  const float* I;      // [n][N]
+  int64_t n;
+  uint32_t trial0;
+  int N;
+  uint32_t k0, k1;
+  float dt, diffusion, leak, inhibition, threshold;
+  int max_steps;
+  int rectify, two_sided;
+  int8_t* choice;
+  int32_t* step;
+  float* xout;         // [n][N], may be null
+  unsigned long long* cursor;
+};
+cudaError_t launch_lca(const LcaParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
+bool lca_tpt_supported(int N, int tpt);
+int lca_max_blocks_per_sm(int N, int tpt, int block);
+
+// ---------------------------------------------------- small logistic network ---
+constexpr int kNetMaxUnits = 32;     // logistic units
+constexpr int kNetMaxInputs = 64;    // input units
+constexpr int kNetMaxEdges = 512;    // weighted edges between logistic units
+
+// Static layout of a small network (Sec. 3.3): units numbered in mechanism
+// order; edges from logistic units listed as (dst, src, w); the input part of
+// each unit's net input is a dense [U][n_in] matrix applied once per trial.
+struct NetLayout {
+  int U;                         // logistic units
+  int n_in;                      // input units
+  int n_edges;
+  int stop_off, stop_size;       // stop layer among logistic units
+  float rate, noise;
+  float stop_threshold;
+  int max_steps;
+  float gain[kNetMaxUnits];
+  float bias[kNetMaxUnits];
+  int16_t edge_dst[kNetMaxEdges];
+  int16_t edge_src[kNetMaxEdges];
+  float edge_w[kNetMaxEdges];
+};
+
+struct NetParams {
+  const NetLayout* layout;       // device copy
+  const float* w_in;             // device [U][n_in]
+  const float* cond;             // device [n_cond][n_in]
+  int n_cond, cond_block;
+  int64_t n;
+  uint32_t trial0;
+  uint32_t k0, k1;
+  int U, n_in, stop_size;        // host copies for launch sizing
+  int8_t* choice;
+  int32_t* step;
+  float* yout;                   // [n][stop_size], may be null
+  unsigned long long* cursor;
+};
+cudaError_t launch_net(const NetParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
+
+// --------------------------------------------------- wide network (tensor cores) ---
+struct WideParams {
+  const float* w_stim;           // [H][S] FP32
+  const float* w_task;           // [H][T] FP32
+  const uint16_t* w_resp_bf16;   // [R][H] bfloat16 bits (K-major rows for the MMA B operand)
+  const float* w_resp_f32;       // [R][H] FP32 copy of the same bf16 values (plain kernel)
+  const float* cond;             // [n_cond][S + T] one-hot rows
+  int n_cond, cond_block;
+  int S, T, H, R;
+  float bias_h, bias_r, gain_h, gain_r, rate, noise, stop_threshold;
+  int max_steps;
+  int64_t n;
+  uint32_t trial0;
+  uint32_t k0, k1;
+  int8_t* choice;
+  int32_t* step;
+  float* yout;                   // [n][R], may be null
+  unsigned long long* cursor;
+  int* status;                   // device status word (bounded mbarrier waits)
+};
+cudaError_t launch_wide(const WideParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
+
+// ------------------------------------------------------- predator-prey grid ---
+struct TopTwo {                  // running argmax with lowest-index ties
+  double v1;
+  long long i1;
+  double v2;
+};
+
+constexpr int kMaxGridBlocks = 4096;  // size of the per-block argmax partials scratch
+
+struct GridParams {
+  const float* lv[3];
+  int L[3];
+  const float* pos;              // [n_trials][6]
+  int n_trials;
+  uint32_t k0, k1;
+  float offset, weight;
+  long long cand0;               // global index of local candidate 0
+  long long n_cand;              // candidates evaluated by this launch
+  double* means;                 // [n_cand] local, may be null
+  TopTwo* partials;              // scratch, one per block
+  unsigned int* ticket;          // scratch, zeroed per launch
+  void* result;                  // dg_grid_result*
+};
+cudaError_t launch_grid(const GridParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
+int grid_blocks(int mode, long long n_cand, int n_trials);
+
+cudaError_t launch_argmax(const double* v, long long n, TopTwo* partials, unsigned int* ticket,
+                          void* result, cudaStream_t s);
+
+// ------------------------------------------------------------ RNG replay ---
+cudaError_t launch_philox_words(uint64_t seed, uint32_t trial, uint32_t cand, uint32_t purpose,
+                                uint32_t block0, int64_t nblocks, uint32_t* out, cudaStream_t s);
+cudaError_t launch_normals(uint64_t seed, uint32_t trial, uint32_t cand, uint64_t d0, int64_t n,
+                           float* out, cudaStream_t s);
+
+int num_sms();
+
+}  // namespace dg

@@ -1,0 +1,278 @@
+// Optimization-control grid search of the predator-prey model (Sec. 2.1,
+// Fig. pp_eg; parallel evaluation of Sec. 3.6).
+//
+// Candidate c = (l0 L1 + l1) L2 + l2 allocates attention a = (lv0[l0], lv1[l1],
+// lv2[l2]) to (player, predator, prey). Trial j of candidate c:
+//   perceived X^_e = X_e + eps_{2e+coord} / (offset + a_e)   (stream (seed, j, c))
+//   act = unit(unit(Y^ - P^) - weight unit(D^ - P^)),  unit(0) = 0
+//   outcome = -|P + act - Y| - sum_e a_e^2                      (true P, Y)
+// mean_c = FP64 mean of the outcomes; best = argmax_c mean_c, lowest c on ties.
+//
+// Batched form: one warp per candidate (trials spread over the lanes), FP64
+// shuffle reduction, running top-2 per warp, block merge, then the last block
+// to finish merges the per-block partials (no second launch, no atomics on
+// the values). Plain form (the paper's mapping): one thread per candidate
+// with a sequential FP64 sum, then a separate argmax launch.
+#include <cfloat>
+#include <climits>
+
+#include "dg_device.cuh"
+#include "dg_internal.h"
+
+namespace dg {
+
+namespace {
+
+struct GridResultDev {
+  long long best_index;
+  double best_value;
+  double gap;
+};
+
+__device__ __forceinline__ TopTwo top_init() { return TopTwo{-DBL_MAX, LLONG_MAX, -DBL_MAX}; }
+
+// Merge two running top-2 summaries: best value with lowest index on ties,
+// and the largest value among the rest.
+__device__ __forceinline__ TopTwo top_merge(TopTwo a, TopTwo b) {
+  const bool b_wins = (b.v1 > a.v1) || (b.v1 == a.v1 && b.i1 < a.i1);
+  TopTwo r;
+  if (b_wins) {
+    r.v1 = b.v1;
+    r.i1 = b.i1;
+    r.v2 = fmax(a.v1, b.v2);
+  } else {
+    r.v1 = a.v1;
+    r.i1 = a.i1;
+    r.v2 = fmax(b.v1, a.v2);
+  }
+  return r;
+}
+
+__device__ __forceinline__ TopTwo top_shfl(TopTwo t, int src, unsigned mask = kFull) {
+  TopTwo r;
+  r.v1 = __shfl_sync(mask, t.v1, src);
+  r.i1 = __shfl_sync(mask, t.i1, src);
+  r.v2 = __shfl_sync(mask, t.v2, src);
+  return r;
+}
+
+__device__ __forceinline__ TopTwo top_warp(TopTwo t) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t = top_merge(t, top_shfl(t, (threadIdx.x & 31) ^ o));
+  return t;
+}
+
+__device__ __forceinline__ void unit2(float vx, float vy, float& ox, float& oy) {
+  const float n2 = vx * vx + vy * vy;
+  if (n2 > 0.f) {
+    const float r = rsqrtf(n2);
+    ox = vx * r;
+    oy = vy * r;
+  } else {
+    ox = 0.f;
+    oy = 0.f;
+  }
+}
+
+__device__ __forceinline__ float pp_outcome(const GridParams& p, const float* pos, int j,
+                                            uint32_t c, float sd0, float sd1, float sd2,
+                                            float cost) {
+  const float4 z = normals4(noise_block(p.k0, p.k1, (uint32_t)j, c, 0u));
+  const uint4 w1 = noise_block(p.k0, p.k1, (uint32_t)j, c, 1u);
+  float z4, z5;
+  box_muller(w1.x, w1.y, z4, z5);
+  const float* X = pos + 6 * j;
+  const float phx = fmaf(sd0, z.x, X[0]), phy = fmaf(sd0, z.y, X[1]);
+  const float dhx = fmaf(sd1, z.z, X[2]), dhy = fmaf(sd1, z.w, X[3]);
+  const float yhx = fmaf(sd2, z4, X[4]), yhy = fmaf(sd2, z5, X[5]);
+  float uyx, uyy, udx, udy, ax, ay;
+  unit2(yhx - phx, yhy - phy, uyx, uyy);
+  unit2(dhx - phx, dhy - phy, udx, udy);
+  unit2(fmaf(-p.weight, udx, uyx), fmaf(-p.weight, udy, uyy), ax, ay);
+  const float nx = (X[0] + ax) - X[4];
+  const float ny = (X[1] + ay) - X[5];
+  return -sqrtf(nx * nx + ny * ny) - cost;
+}
+
+// c: global candidate index
+__device__ __forceinline__ void cand_alloc(const GridParams& p, const float* lv, long long c,
+                                           float& a0, float& a1, float& a2) {
+  const int l2 = (int)(c % p.L[2]);
+  const int l1 = (int)((c / p.L[2]) % p.L[1]);
+  const int l0 = (int)(c / ((long long)p.L[2] * p.L[1]));
+  a0 = lv[l0];
+  a1 = lv[p.L[0] + l1];
+  a2 = lv[p.L[0] + p.L[1] + l2];
+}
+
+// Stage positions and level values in shared memory.
+__device__ __forceinline__ void stage(const GridParams& p, float* pos, float* lv) {
+  for (int i = threadIdx.x; i < 6 * p.n_trials; i += blockDim.x) pos[i] = __ldg(p.pos + i);
+  for (int i = threadIdx.x; i < p.L[0]; i += blockDim.x) lv[i] = __ldg(p.lv[0] + i);
+  for (int i = threadIdx.x; i < p.L[1]; i += blockDim.x) lv[p.L[0] + i] = __ldg(p.lv[1] + i);
+  for (int i = threadIdx.x; i < p.L[2]; i += blockDim.x)
+    lv[p.L[0] + p.L[1] + i] = __ldg(p.lv[2] + i);
+  __syncthreads();
+}
+
+// Block-wide merge of per-warp summaries, publication of the block's summary,
+// and the final merge by whichever block finishes last.
+__device__ void finish_argmax(TopTwo mine, TopTwo* partials, unsigned int* ticket,
+                              void* result) {
+  __shared__ TopTwo warp_best[32];
+  __shared__ bool last;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  mine = top_warp(mine);
+  if (lane == 0) warp_best[warp] = mine;
+  __syncthreads();
+  if (warp == 0) {
+    TopTwo t = lane < nw ? warp_best[lane] : top_init();
+    t = top_warp(t);
+    if (lane == 0) {
+      partials[blockIdx.x] = t;
+      __threadfence();
+      last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  TopTwo t = top_init();
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    TopTwo q;
+    q.v1 = __ldcg(&partials[b].v1);
+    q.i1 = __ldcg(&partials[b].i1);
+    q.v2 = __ldcg(&partials[b].v2);
+    t = top_merge(t, q);
+  }
+  t = top_warp(t);
+  __syncthreads();
+  if (lane == 0) warp_best[warp] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    TopTwo r = warp_best[0];
+    for (int w = 1; w < nw; ++w) r = top_merge(r, warp_best[w]);
+    GridResultDev* out = reinterpret_cast<GridResultDev*>(result);
+    out->best_index = r.i1;
+    out->best_value = r.v1;
+    out->gap = (r.v2 == -DBL_MAX) ? 0.0 : r.v1 - r.v2;
+  }
+}
+
+__global__ void __launch_bounds__(256) grid_batched(GridParams p) {
+  extern __shared__ float sm[];
+  float* pos = sm;
+  float* lv = sm + 6 * p.n_trials;
+  stage(p, pos, lv);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  TopTwo best = top_init();
+  const double inv = 1.0 / (double)p.n_trials;
+  for (long long c = (long long)blockIdx.x * wpb + warp; c < p.n_cand;
+       c += (long long)gridDim.x * wpb) {
+    const long long cg = p.cand0 + c;
+    float a0, a1, a2;
+    cand_alloc(p, lv, cg, a0, a1, a2);
+    const float sd0 = 1.0f / (p.offset + a0), sd1 = 1.0f / (p.offset + a1),
+                sd2 = 1.0f / (p.offset + a2);
+    const float cost = a0 * a0 + a1 * a1 + a2 * a2;
+    double acc = 0.0;
+    for (int j = lane; j < p.n_trials; j += 32)
+      acc += (double)pp_outcome(p, pos, j, (uint32_t)cg, sd0, sd1, sd2, cost);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
+    const double mean = __shfl_sync(kFull, acc, 0) * inv;
+    if (lane == 0) {
+      if (p.means) p.means[c] = mean;
+      best = top_merge(best, TopTwo{mean, cg, -DBL_MAX});
+    }
+  }
+  finish_argmax(best, p.partials, p.ticket, p.result);
+}
+
+__global__ void __launch_bounds__(256) grid_plain(GridParams p) {
+  extern __shared__ float sm[];
+  float* pos = sm;
+  float* lv = sm + 6 * p.n_trials;
+  stage(p, pos, lv);
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.n_cand) return;
+  const long long cg = p.cand0 + c;
+  float a0, a1, a2;
+  cand_alloc(p, lv, cg, a0, a1, a2);
+  const float sd0 = 1.0f / (p.offset + a0), sd1 = 1.0f / (p.offset + a1),
+              sd2 = 1.0f / (p.offset + a2);
+  const float cost = a0 * a0 + a1 * a1 + a2 * a2;
+  double acc = 0.0;
+  for (int j = 0; j < p.n_trials; ++j)
+    acc += (double)pp_outcome(p, pos, j, (uint32_t)cg, sd0, sd1, sd2, cost);
+  p.means[c] = acc / (double)p.n_trials;
+}
+
+__global__ void __launch_bounds__(256) argmax_kernel(const double* v, long long n,
+                                                     long long base, TopTwo* partials,
+                                                     unsigned int* ticket, void* result) {
+  TopTwo best = top_init();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    best = top_merge(best, TopTwo{v[i], base + i, -DBL_MAX});
+  finish_argmax(best, partials, ticket, result);
+}
+
+size_t grid_smem(const GridParams& p) {
+  return sizeof(float) * (6 * (size_t)p.n_trials + p.L[0] + p.L[1] + p.L[2]);
+}
+
+}  // namespace
+
+int grid_blocks(int mode, long long n_cand, int n_trials) {
+  (void)n_trials;
+  if (mode == 1) return (int)((n_cand + 255) / 256);
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, grid_batched, 256, 0);
+  if (nb < 1) nb = 1;
+  long long g = (long long)num_sms() * nb;
+  const long long need = (n_cand + 7) / 8;
+  return (int)(g < need ? g : need);
+}
+
+cudaError_t launch_grid(const GridParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s) {
+  const size_t smem = grid_smem(p);  // <= 6 * 1024 + 3 * 4096 floats (runtime limits)
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(grid_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(grid_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr = true;
+  }
+  if (p.n_cand <= 0) return cudaSuccess;
+  if (mode == 1) {
+    const long long grid = (p.n_cand + 255) / 256;
+    grid_plain<<<(unsigned)grid, 256, smem, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int ab = (int)((p.n_cand + 255) / 256);
+    if (ab > 1024) ab = 1024;
+    if (ab < 1) ab = 1;
+    argmax_kernel<<<ab, 256, 0, s>>>(p.means, p.n_cand, p.cand0, p.partials, p.ticket,
+                                     p.result);
+    return cudaGetLastError();
+  }
+  const int block = (cfg.block == 128 || cfg.block == 256) ? cfg.block : 256;
+  int grid = cfg.grid > 0 ? cfg.grid : grid_blocks(0, p.n_cand, p.n_trials);
+  if (grid > kMaxGridBlocks) grid = kMaxGridBlocks;  // one argmax partial per block
+  const long long need = (p.n_cand + block / 32 - 1) / (block / 32);
+  if (grid > need) grid = (int)need;
+  grid_batched<<<grid, block, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_argmax(const double* v, long long n, TopTwo* partials, unsigned int* ticket,
+                          void* result, cudaStream_t s) {
+  long long g = (n + 255) / 256;
+  if (g > 1024) g = 1024;
+  if (g < 1) g = 1;
+  argmax_kernel<<<(unsigned)g, 256, 0, s>>>(v, n, 0, partials, ticket, result);
+  return cudaGetLastError();
+}
+
+}  // namespace dg

@@ -1,0 +1,284 @@
+// Leaky competing accumulator trials (Sec. 4.4, the LCA of the Multitasking
+// model in Sec. 5), Usher-McClelland form, synchronous update:
+//   x_i <- x_i + ((I_i - k x_i - beta sum_{j != i} x_j) dt + sigma sqrt(dt) eps_i)
+//   x_i <- max(0, x_i)                         (unless DG_LCA_NO_RECTIFY)
+// stop when max_i x_i >= threshold (winner = lowest index among maxima), or,
+// two-sided with N = 1, when |x| >= threshold (the DDM mapping of Sec. 4.4).
+// eps_i of step j (1-based) is normal (j-1) N + i of the (seed, trial, 0) stream.
+//
+// A trial is held by a group of TPT lanes (threads per trial), each holding
+// N / TPT accumulators in registers; the sum and the max go through shuffles
+// inside the group. Batched form: persistent grid, groups refill from a global
+// trial cursor. Plain form: one thread per trial, one launch.
+#include "dg_device.cuh"
+#include "dg_internal.h"
+
+namespace dg {
+
+namespace {
+
+template <int N, int TPT>
+struct Lca {
+  static constexpr int NU = N / TPT;  // accumulators per lane
+
+  // Normals of this lane's units for step index k (0-based).
+  static __device__ __forceinline__ void noise(const LcaParams& p, uint32_t trial, int k, int g,
+                                               float (&e)[NU]) {
+    if constexpr (NU % 4 == 0) {
+      const uint32_t b0 = (uint32_t)k * (uint32_t)(N / 4) + (uint32_t)(g * (NU / 4));
+#pragma unroll
+      for (int b = 0; b < NU / 4; ++b) {
+        const float4 z = normals4(noise_block(p.k0, p.k1, trial, 0u, b0 + (uint32_t)b));
+        e[4 * b + 0] = z.x;
+        e[4 * b + 1] = z.y;
+        e[4 * b + 2] = z.z;
+        e[4 * b + 3] = z.w;
+      }
+    } else {
+      static_assert(TPT == 1, "split trials need whole Philox blocks per lane");
+      const uint32_t d0 = (uint32_t)k * (uint32_t)N;
+      float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < NU; ++i) {
+        const uint32_t d = d0 + (uint32_t)i;
+        if (i == 0 || (d & 3u) == 0u) z = normals4(noise_block(p.k0, p.k1, trial, 0u, d >> 2));
+        e[i] = pick4(z, d & 3u);
+      }
+    }
+  }
+
+  // S = sum of the N accumulators in one fixed order for every layout: a
+  // balanced pairwise tree over units in index order when N is a power of
+  // two (each lane reduces its contiguous chunk, then lanes combine with
+  // ascending shuffle distances, which continues the same tree), else a
+  // sequential sum (those N run with one lane per trial only).
+  static __device__ __forceinline__ float chunk_sum(const float (&x)[NU]) {
+    if constexpr ((N & (N - 1)) == 0) {
+      float t[NU];
+#pragma unroll
+      for (int i = 0; i < NU; ++i) t[i] = x[i];
+#pragma unroll
+      for (int w = 1; w < NU; w <<= 1)
+#pragma unroll
+        for (int i = 0; i + w < NU; i += 2 * w) t[i] = t[i] + t[i + w];
+      return t[0];
+    } else {
+      float s = 0.f;
+#pragma unroll
+      for (int i = 0; i < NU; ++i) s += x[i];
+      return s;
+    }
+  }
+
+  static __device__ __forceinline__ float group_sum(float v, unsigned gmask) {
+#pragma unroll
+    for (int o = 1; o < TPT; o <<= 1) v += __shfl_xor_sync(gmask, v, o);
+    return v;
+  }
+
+  static __device__ __forceinline__ void group_argmax(float& v, int& i, unsigned gmask) {
+#pragma unroll
+    for (int o = TPT / 2; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(gmask, v, o);
+      const int oi = __shfl_xor_sync(gmask, i, o);
+      if (ov > v || (ov == v && oi < i)) {
+        v = ov;
+        i = oi;
+      }
+    }
+  }
+
+  // One step of one trial. Returns true when the trial has ended at this step.
+  static __device__ __forceinline__ bool step(const LcaParams& p, uint32_t trial, int k, int g,
+                                              unsigned gmask, float (&x)[NU], const float (&I)[NU],
+                                              int8_t& choice) {
+    float e[NU];
+    noise(p, trial, k, g, e);
+    const float S = group_sum(chunk_sum(x), gmask);
+#pragma unroll
+    for (int i = 0; i < NU; ++i) {
+      const float drive = (I[i] - p.leak * x[i]) - p.inhibition * (S - x[i]);
+      float v = x[i] + fmaf(drive, p.dt, p.diffusion * e[i]);
+      if (p.rectify) v = fmaxf(v, 0.f);
+      x[i] = v;
+    }
+    if (N == 1 && p.two_sided) {
+      if (fabsf(x[0]) >= p.threshold) {
+        choice = x[0] > 0.f ? 1 : 0;
+        return true;
+      }
+      return false;
+    }
+    float m = x[0];
+    int mi = g * NU;
+#pragma unroll
+    for (int i = 1; i < NU; ++i)
+      if (x[i] > m) {
+        m = x[i];
+        mi = g * NU + i;
+      }
+    group_argmax(m, mi, gmask);
+    if (m >= p.threshold) {
+      choice = (int8_t)mi;
+      return true;
+    }
+    return false;
+  }
+
+  static __device__ __forceinline__ void load(const LcaParams& p, long long t, int g,
+                                              float (&x)[NU], float (&I)[NU]) {
+    const float* src = p.I + (size_t)t * N + g * NU;
+#pragma unroll
+    for (int i = 0; i < NU; ++i) {
+      I[i] = __ldg(src + i);
+      x[i] = 0.f;
+    }
+  }
+
+  static __device__ __forceinline__ void store(const LcaParams& p, long long t, int g, int8_t c,
+                                               int st, const float (&x)[NU]) {
+    if (g == 0) {
+      p.choice[t] = c;
+      p.step[t] = st;
+    }
+    if (p.xout) {
+      float* dst = p.xout + (size_t)t * N + g * NU;
+#pragma unroll
+      for (int i = 0; i < NU; ++i) dst[i] = x[i];
+    }
+  }
+};
+
+template <int N, int TPT>
+__global__ void __launch_bounds__(256) lca_batched(LcaParams p) {
+  using L = Lca<N, TPT>;
+  const int lane = threadIdx.x & 31;
+  const int g = lane % TPT;
+  const int root = lane - g;
+  const unsigned gmask = (TPT == 32 ? kFull : ((1u << TPT) - 1u)) << root;
+  float x[L::NU], I[L::NU];
+  long long t = fetch_trial(p.cursor, g == 0);
+  t = __shfl_sync(kFull, t, root);
+  bool active = t >= 0 && t < p.n;
+  int k = 0;
+  if (active) L::load(p, t, g, x, I);
+  while (__any_sync(kFull, active)) {
+    bool finished = false;
+    if (active) {
+      int8_t c = -1;
+      const bool hit = L::step(p, p.trial0 + (uint32_t)t, k, g, gmask, x, I, c);
+      ++k;
+      if (hit || k >= p.max_steps) {
+        L::store(p, t, g, hit ? c : (int8_t)-1, hit ? k : p.max_steps, x);
+        finished = true;
+      }
+    }
+    long long nt = fetch_trial(p.cursor, finished && g == 0);
+    nt = __shfl_sync(kFull, nt, root);
+    if (finished) {
+      t = nt;
+      active = t < p.n;
+      k = 0;
+      if (active) L::load(p, t, g, x, I);
+    }
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) lca_plain(LcaParams p) {
+  using L = Lca<N, 1>;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.n) return;
+  const int lane = threadIdx.x & 31;
+  const unsigned gmask = 1u << lane;
+  float x[L::NU], I[L::NU];
+  L::load(p, t, 0, x, I);
+  for (int k = 0; k < p.max_steps; ++k) {
+    int8_t c = -1;
+    if (L::step(p, p.trial0 + (uint32_t)t, k, 0, gmask, x, I, c)) {
+      L::store(p, t, 0, c, k + 1, x);
+      return;
+    }
+  }
+  L::store(p, t, 0, (int8_t)-1, p.max_steps, x);
+}
+
+template <int N, int TPT>
+void* batched_fn() {
+  return (void*)lca_batched<N, TPT>;
+}
+
+template <int N>
+cudaError_t launch_n(const LcaParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s) {
+  if (mode == 1) {
+    const int block = 256;
+    const long long grid = (p.n + block - 1) / block;
+    lca_plain<N><<<(unsigned)grid, block, 0, s>>>(p);
+    return cudaGetLastError();
+  }
+  const int block = cfg.block;
+  int grid = cfg.grid;
+  if (grid <= 0) grid = num_sms() * lca_max_blocks_per_sm(N, cfg.tpt, block);
+  const long long need = (p.n * cfg.tpt + block - 1) / block;
+  if (grid > need) grid = (int)need;
+  if (grid < 1) grid = 1;
+  switch (cfg.tpt) {
+    case 1: lca_batched<N, 1><<<grid, block, 0, s>>>(p); break;
+    case 2:
+      if constexpr (N % 8 == 0) { lca_batched<N, 2><<<grid, block, 0, s>>>(p); break; }
+      return cudaErrorInvalidValue;
+    case 4:
+      if constexpr (N % 16 == 0) { lca_batched<N, 4><<<grid, block, 0, s>>>(p); break; }
+      return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+void* kernel_for(int N, int tpt) {
+  switch (tpt) {
+    case 1:
+      switch (N) {
+#define DG_CASE(n) case n: return batched_fn<n, 1>();
+        DG_CASE(1) DG_CASE(2) DG_CASE(3) DG_CASE(4) DG_CASE(5) DG_CASE(6) DG_CASE(7) DG_CASE(8)
+        DG_CASE(9) DG_CASE(10) DG_CASE(11) DG_CASE(12) DG_CASE(13) DG_CASE(14) DG_CASE(15)
+        DG_CASE(16)
+#undef DG_CASE
+      }
+      return nullptr;
+    case 2:
+      if (N == 8) return batched_fn<8, 2>();
+      if (N == 16) return batched_fn<16, 2>();
+      return nullptr;
+    case 4:
+      if (N == 16) return batched_fn<16, 4>();
+      return nullptr;
+  }
+  return nullptr;
+}
+
+}  // namespace
+
+bool lca_tpt_supported(int N, int tpt) { return kernel_for(N, tpt) != nullptr; }
+
+int lca_max_blocks_per_sm(int N, int tpt, int block) {
+  void* fn = kernel_for(N, tpt);
+  if (!fn) return 0;
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0);
+  return nb;
+}
+
+cudaError_t launch_lca(const LcaParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s) {
+  if (p.n <= 0) return cudaSuccess;
+  switch (p.N) {
+#define DG_CASE(n) case n: return launch_n<n>(p, mode, cfg, s);
+    DG_CASE(1) DG_CASE(2) DG_CASE(3) DG_CASE(4) DG_CASE(5) DG_CASE(6) DG_CASE(7) DG_CASE(8)
+    DG_CASE(9) DG_CASE(10) DG_CASE(11) DG_CASE(12) DG_CASE(13) DG_CASE(14) DG_CASE(15)
+    DG_CASE(16)
+#undef DG_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace dg

@@ -1,0 +1,1369 @@
+// Host runtime of the C ABI in include/distill_gpu.h: compose-time validation
+// and static layout (Sec. 2.2 sanitization, Sec. 3.3 static structures),
+// launch dispatch, per-stream scratch, the launch-shape autotuner, CUDA-graph
+// batches and the continuous-batching serving loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "distill_gpu.h"
+#include "dg_internal.h"
+
+// ----------------------------------------------------------------- errors ---
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+dg_status fail(dg_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define DG_CUDA(x)                                                                   \
+  do {                                                                               \
+    cudaError_t e_ = (x);                                                            \
+    if (e_ != cudaSuccess) return fail(DG_E_CUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
+  } while (0)
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+enum ModelKind { K_DDM = 0, K_LCA = 1, K_NET = 2, K_WIDE = 3, K_PP = 4 };
+
+// Per-stream scratch: trial cursor, argmax ticket, per-block argmax partials,
+// device status word, and a growable FP64 buffer for the plain grid search.
+constexpr size_t kMaxPartials = dg::kMaxGridBlocks;
+constexpr size_t kScratchHead = 256;
+constexpr size_t kScratchBytes = kScratchHead + kMaxPartials * sizeof(dg::TopTwo);
+
+struct Scratch {
+  unsigned char* base = nullptr;
+  double* means = nullptr;
+  size_t means_cap = 0;
+  unsigned long long* cursor() { return reinterpret_cast<unsigned long long*>(base); }
+  unsigned int* ticket() { return reinterpret_cast<unsigned int*>(base + 8); }
+  int* status() { return reinterpret_cast<int*>(base + 16); }
+  dg::TopTwo* partials() { return reinterpret_cast<dg::TopTwo*>(base + kScratchHead); }
+};
+
+struct Server;
+
+}  // namespace
+
+struct dg_ctx {
+  int device = 0;
+  size_t budget = 0;
+  std::mutex mu;
+  std::unordered_map<cudaStream_t, Scratch> scratch;
+  std::map<std::string, dg::LaunchCfg> tuned;
+  std::string tune_file;
+  bool autotune = true;
+  std::unique_ptr<Server> server;
+  std::mutex server_mu;
+};
+
+struct dg_model {
+  dg_ctx* ctx = nullptr;
+  int kind = 0;
+  int max_steps = 1;
+  // DDM
+  float dt = 0.f, diffusion = 0.f, x0 = 0.f;
+  // LCA
+  int N = 0;
+  float leak = 0.f, inhibition = 0.f, threshold = 0.f;
+  int rectify = 1, two_sided = 0;
+  // small network
+  dg::NetLayout layout{};
+  dg::NetLayout* d_layout = nullptr;
+  float* d_w_in = nullptr;
+  // wide network
+  int S = 0, T = 0, H = 0, R = 0;
+  float bias_h = 0, bias_r = 0, gain_h = 1, gain_r = 1, rate = 0, noise = 0, stop_thr = 0;
+  float* d_w_stim = nullptr;
+  float* d_w_task = nullptr;
+  uint16_t* d_w_resp_bf16 = nullptr;
+  float* d_w_resp_f32 = nullptr;
+  // predator-prey
+  float offset = 0.f, weight = 0.f;
+  int state_size = 0;
+  int n_inputs = 0;  // TRANSFER: input units per condition row
+};
+
+namespace {
+
+// ------------------------------------------------------------ scratch ---
+
+dg_status get_scratch(dg_ctx* ctx, cudaStream_t s, Scratch** out) {
+  std::lock_guard<std::mutex> g(ctx->mu);
+  auto it = ctx->scratch.find(s);
+  if (it == ctx->scratch.end()) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+      return fail(DG_E_STATE,
+                  "first use of a stream must not be inside stream capture (scratch allocation)");
+    Scratch sc;
+    DG_CUDA(cudaMalloc(&sc.base, kScratchBytes));
+    DG_CUDA(cudaMemset(sc.base, 0, kScratchBytes));
+    it = ctx->scratch.emplace(s, sc).first;
+  }
+  *out = &it->second;
+  return DG_OK;
+}
+
+dg_status scratch_means(dg_ctx* ctx, Scratch* sc, size_t n, cudaStream_t s) {
+  if (sc->means_cap >= n) return DG_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    return fail(DG_E_STATE, "plain grid search needs a means buffer; run once before capture");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  DG_CUDA(cudaStreamSynchronize(s));
+  if (sc->means) cudaFree(sc->means);
+  sc->means = nullptr;
+  DG_CUDA(cudaMalloc(&sc->means, n * sizeof(double)));
+  sc->means_cap = n;
+  return DG_OK;
+}
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+// Set on the serving thread: never time launch shapes there (tuning
+// synchronizes); use tuned shapes when known, defaults otherwise.
+thread_local bool t_no_tune = false;
+
+// ---------------------------------------------------------- autotuner ---
+
+void load_tune_file(dg_ctx* ctx) {
+  if (ctx->tune_file.empty()) return;
+  FILE* f = fopen(ctx->tune_file.c_str(), "r");
+  if (!f) return;
+  char key[256];
+  int b, g, t;
+  while (fscanf(f, "%255s %d %d %d", key, &b, &g, &t) == 4) {
+    dg::LaunchCfg c;
+    c.block = b;
+    c.grid = g;
+    c.tpt = t;
+    ctx->tuned[key] = c;
+  }
+  fclose(f);
+}
+
+void save_tune_file(dg_ctx* ctx) {
+  if (ctx->tune_file.empty()) return;
+  FILE* f = fopen(ctx->tune_file.c_str(), "w");
+  if (!f) return;
+  for (auto& kv : ctx->tuned)
+    fprintf(f, "%s %d %d %d\n", kv.first.c_str(), kv.second.block, kv.second.grid, kv.second.tpt);
+  fclose(f);
+}
+
+int log2_bucket(long long n) {
+  int b = 0;
+  while ((1ll << b) < n && b < 62) ++b;
+  return b;
+}
+
+// Launch `fn(cfg)` for each candidate shape, time each (best of 2) with
+// events on the stream, keep the fastest. All candidates compute identical
+// outputs (results depend only on inputs and seed), so the outputs left by
+// the last run are the job's outputs.
+template <class F>
+dg_status autotune(dg_ctx* ctx, const std::string& key, const std::vector<dg::LaunchCfg>& cands,
+                   cudaStream_t s, F&& fn, dg::LaunchCfg* chosen, bool* ran) {
+  *ran = false;
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) {
+      *chosen = it->second;
+      return DG_OK;
+    }
+  }
+  if (!ctx->autotune || t_no_tune || capturing(s) || cands.size() == 1) {
+    *chosen = cands.front();
+    return DG_OK;
+  }
+  cudaEvent_t a, b;
+  DG_CUDA(cudaEventCreate(&a));
+  DG_CUDA(cudaEventCreate(&b));
+  float best_ms = 1e30f;
+  dg::LaunchCfg best = cands.front();
+  for (const auto& c : cands) {
+    float ms_best = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(a, s);
+      dg_status st = fn(c);
+      if (st != DG_OK) {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return st;
+      }
+      cudaEventRecord(b, s);
+      if (cudaEventSynchronize(b) != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      ms_best = std::min(ms_best, ms);
+    }
+    if (ms_best < best_ms) {
+      best_ms = ms_best;
+      best = c;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  // leave the job's outputs from the chosen shape
+  dg_status st = fn(best);
+  if (st != DG_OK) return st;
+  *ran = true;
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->tuned[key] = best;
+    save_tune_file(ctx);
+  }
+  *chosen = best;
+  return DG_OK;
+}
+
+// Run a batched launch with the tuned shape for `key` (tuning it first when
+// it is unknown and the stream is not being captured).
+template <class F>
+dg_status run_tuned(dg_ctx* ctx, const std::string& key, const std::vector<dg::LaunchCfg>& cands,
+                    cudaStream_t s, F&& go) {
+  dg::LaunchCfg c;
+  bool ran = false;
+  dg_status st = autotune(ctx, key, cands, s, go, &c, &ran);
+  if (st != DG_OK) return st;
+  return ran ? DG_OK : go(c);
+}
+
+std::vector<dg::LaunchCfg> ddm_candidates() {
+  std::vector<dg::LaunchCfg> v;
+  for (int block : {256, 128}) {
+    const int occ = dg::ddm_max_blocks_per_sm(block);
+    for (int div : {1, 2}) {
+      dg::LaunchCfg c;
+      c.block = block;
+      c.grid = dg::num_sms() * std::max(1, occ / div);
+      v.push_back(c);
+    }
+  }
+  return v;
+}
+
+// DG_LCA_TPT=<1|2|4> restricts the threads-per-trial layouts the tuner may
+// pick (used to exercise every layout).
+int forced_tpt() {
+  const char* e = getenv("DG_LCA_TPT");
+  return e ? atoi(e) : 0;
+}
+
+std::vector<dg::LaunchCfg> lca_candidates(int N) {
+  std::vector<dg::LaunchCfg> v;
+  const int only = forced_tpt();
+  for (int tpt : {1, 2, 4}) {
+    if (!dg::lca_tpt_supported(N, tpt) || (only && tpt != only)) continue;
+    for (int block : {256, 128}) {
+      dg::LaunchCfg c;
+      c.block = block;
+      c.tpt = tpt;
+      c.grid = dg::num_sms() * std::max(1, dg::lca_max_blocks_per_sm(N, tpt, block));
+      v.push_back(c);
+    }
+  }
+  return v;
+}
+
+std::vector<dg::LaunchCfg> grid_candidates(long long n_cand) {
+  std::vector<dg::LaunchCfg> v;
+  const int full = dg::grid_blocks(0, n_cand, 64);
+  for (int per_warp : {0, 2, 3, 4}) {
+    dg::LaunchCfg c;
+    c.block = 256;
+    if (per_warp == 0) {
+      c.grid = full;
+    } else {
+      long long g = (n_cand + 8LL * per_warp - 1) / (8LL * per_warp);
+      if (g > (long long)kMaxPartials) continue;
+      c.grid = (int)g;
+    }
+    v.push_back(c);
+  }
+  return v;
+}
+
+// ---------------------------------------------------------- run paths ---
+
+dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t* step,
+                     float* fs, cudaStream_t s) {
+  if (d->n_trials == 0) return DG_OK;
+  Scratch* sc = nullptr;
+  dg_status st = get_scratch(m->ctx, s, &sc);
+  if (st != DG_OK) return st;
+  const uint32_t k0 = (uint32_t)d->seed, k1 = (uint32_t)(d->seed >> 32);
+  const int mode = d->mode;
+  const std::string bucket = std::to_string(log2_bucket(d->n_trials));
+
+  if (m->kind == K_DDM) {
+    dg::DdmParams p{};
+    p.A = d->trial_params;
+    p.z = d->trial_params + d->n_trials;
+    p.n = d->n_trials;
+    p.trial0 = (uint32_t)d->trial_offset;
+    p.k0 = k0;
+    p.k1 = k1;
+    p.dt = m->dt;
+    p.diffusion = m->diffusion;
+    p.x0 = m->x0;
+    p.max_steps = m->max_steps;
+    p.choice = choice;
+    p.step = step;
+    p.xout = fs;
+    p.cursor = sc->cursor();
+    auto go = [&](const dg::LaunchCfg& c) -> dg_status {
+      if (mode == DG_MODE_BATCHED) DG_CUDA(cudaMemsetAsync(sc->cursor(), 0, 8, s));
+      DG_CUDA(dg::launch_ddm(p, mode, c, s));
+      return DG_OK;
+    };
+    if (mode == DG_MODE_PLAIN) return go(dg::LaunchCfg{});
+    return run_tuned(m->ctx, "ddm/" + bucket, ddm_candidates(), s, go);
+  }
+  if (m->kind == K_LCA) {
+    dg::LcaParams p{};
+    p.I = d->trial_params;
+    p.n = d->n_trials;
+    p.trial0 = (uint32_t)d->trial_offset;
+    p.N = m->N;
+    p.k0 = k0;
+    p.k1 = k1;
+    p.dt = m->dt;
+    p.diffusion = m->diffusion;
+    p.leak = m->leak;
+    p.inhibition = m->inhibition;
+    p.threshold = m->threshold;
+    p.max_steps = m->max_steps;
+    p.rectify = m->rectify;
+    p.two_sided = m->two_sided;
+    p.choice = choice;
+    p.step = step;
+    p.xout = fs;
+    p.cursor = sc->cursor();
+    auto go = [&](const dg::LaunchCfg& c) -> dg_status {
+      if (mode == DG_MODE_BATCHED) DG_CUDA(cudaMemsetAsync(sc->cursor(), 0, 8, s));
+      DG_CUDA(dg::launch_lca(p, mode, c, s));
+      return DG_OK;
+    };
+    if (mode == DG_MODE_PLAIN) return go(dg::LaunchCfg{});
+    auto cands = lca_candidates(m->N);
+    if (cands.empty()) return fail(DG_E_UNSUPPORTED, "dg_run: no LCA layout for N=%d", m->N);
+    return run_tuned(m->ctx,
+                     "lca" + std::to_string(m->N) + "/" + bucket + "/t" +
+                         std::to_string(forced_tpt()),
+                     cands, s, go);
+  }
+  if (m->kind == K_NET) {
+    dg::NetParams p{};
+    p.layout = m->d_layout;
+    p.w_in = m->d_w_in;
+    p.cond = d->cond_inputs;
+    p.n_cond = d->n_cond;
+    p.cond_block = d->cond_block;
+    p.n = d->n_trials;
+    p.trial0 = (uint32_t)d->trial_offset;
+    p.k0 = k0;
+    p.k1 = k1;
+    p.U = m->layout.U;
+    p.n_in = m->layout.n_in;
+    p.stop_size = m->layout.stop_size;
+    p.choice = choice;
+    p.step = step;
+    p.yout = fs;
+    p.cursor = mode == DG_MODE_BATCHED ? sc->cursor() : nullptr;
+    if (mode == DG_MODE_BATCHED) DG_CUDA(cudaMemsetAsync(sc->cursor(), 0, 8, s));
+    DG_CUDA(dg::launch_net(p, mode, dg::LaunchCfg{}, s));
+    return DG_OK;
+  }
+  if (m->kind == K_WIDE) {
+    dg::WideParams p{};
+    p.w_stim = m->d_w_stim;
+    p.w_task = m->d_w_task;
+    p.w_resp_bf16 = m->d_w_resp_bf16;
+    p.w_resp_f32 = m->d_w_resp_f32;
+    p.cond = d->cond_inputs;
+    p.n_cond = d->n_cond;
+    p.cond_block = d->cond_block;
+    p.S = m->S;
+    p.T = m->T;
+    p.H = m->H;
+    p.R = m->R;
+    p.bias_h = m->bias_h;
+    p.bias_r = m->bias_r;
+    p.gain_h = m->gain_h;
+    p.gain_r = m->gain_r;
+    p.rate = m->rate;
+    p.noise = m->noise;
+    p.stop_threshold = m->stop_thr;
+    p.max_steps = m->max_steps;
+    p.n = d->n_trials;
+    p.trial0 = (uint32_t)d->trial_offset;
+    p.k0 = k0;
+    p.k1 = k1;
+    p.choice = choice;
+    p.step = step;
+    p.yout = fs;
+    p.cursor = sc->cursor();
+    p.status = sc->status();
+    if (mode == DG_MODE_BATCHED) DG_CUDA(cudaMemsetAsync(sc->cursor(), 0, 8, s));
+    cudaError_t e = dg::launch_wide(p, mode, dg::LaunchCfg{}, s);
+    if (e == cudaErrorNotSupported)
+      return fail(DG_E_UNSUPPORTED, "wide network kernel not available in this build");
+    DG_CUDA(e);
+    return DG_OK;
+  }
+  return fail(DG_E_UNSUPPORTED, "dg_run: predator-prey models run through dg_grid_search");
+}
+
+dg_status check_run_args(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t* step) {
+  if (!m || !d) return fail(DG_E_ARG, "dg_run: null model or desc");
+  if (d->n_trials < 0 || d->n_trials > INT32_MAX)
+    return fail(DG_E_ARG, "dg_run: n_trials %lld out of range [0, 2^31-1]", (long long)d->n_trials);
+  if (d->mode != DG_MODE_BATCHED && d->mode != DG_MODE_PLAIN)
+    return fail(DG_E_ARG, "dg_run: unknown mode %d", d->mode);
+  if (d->trial_offset < 0 || d->trial_offset + d->n_trials > (1ll << 32))
+    return fail(DG_E_ARG, "dg_run: trial_offset + n_trials must lie in [0, 2^32]");
+  if (m->kind == K_PP)
+    return fail(DG_E_UNSUPPORTED, "dg_run: predator-prey models run through dg_grid_search");
+  if (d->n_trials == 0) return DG_OK;
+  if (!choice || !step) return fail(DG_E_ARG, "dg_run: null choice or step output");
+  if ((m->kind == K_DDM || m->kind == K_LCA) && !d->trial_params)
+    return fail(DG_E_ARG, "dg_run: trial_params required for DDM and LCA models");
+  if (m->kind == K_NET || m->kind == K_WIDE) {
+    if (!d->cond_inputs) return fail(DG_E_ARG, "dg_run: cond_inputs required");
+    if (d->n_cond < 1 || d->cond_block < 1)
+      return fail(DG_E_ARG, "dg_run: n_cond and cond_block must be >= 1");
+  }
+  return DG_OK;
+}
+
+size_t run_param_floats(const dg_model* m, const dg_run_desc* d) {
+  if (m->kind == K_DDM) return 2 * (size_t)d->n_trials;
+  if (m->kind == K_LCA) return (size_t)d->n_trials * m->N;
+  return 0;
+}
+
+size_t run_cond_floats(const dg_model* m, const dg_run_desc* d) {
+  if (m->kind == K_NET || m->kind == K_WIDE) return (size_t)d->n_cond * m->n_inputs;
+  return 0;
+}
+
+// ------------------------------------------------------------- grid ---
+
+dg_status check_grid_args(dg_model* m, const dg_grid_desc* d, dg_grid_result* result) {
+  if (!m || !d || !result) return fail(DG_E_ARG, "dg_grid_search: null model, desc or result");
+  if (m->kind != K_PP)
+    return fail(DG_E_UNSUPPORTED, "dg_grid_search: model is not a predator-prey model");
+  for (int i = 0; i < 3; ++i)
+    if (d->n_levels[i] < 1 || d->n_levels[i] > 4096)
+      return fail(DG_E_ARG, "dg_grid_search: n_levels[%d] = %d out of [1, 4096]", i,
+                  d->n_levels[i]);
+  if (d->n_trials < 1 || d->n_trials > 1024)
+    return fail(DG_E_ARG, "dg_grid_search: n_trials %d out of [1, 1024]", d->n_trials);
+  if (!d->positions || !d->levels[0] || !d->levels[1] || !d->levels[2])
+    return fail(DG_E_ARG, "dg_grid_search: null positions or levels");
+  if (d->mode != DG_MODE_BATCHED && d->mode != DG_MODE_PLAIN)
+    return fail(DG_E_ARG, "dg_grid_search: unknown mode %d", d->mode);
+  const long long n = (long long)d->n_levels[0] * d->n_levels[1] * d->n_levels[2];
+  if (n > 0xFFFFFFFFll) return fail(DG_E_ARG, "dg_grid_search: more than 2^32 candidates");
+  if (d->cand_begin < 0 || d->cand_count < 0 || d->cand_begin + d->cand_count > n ||
+      (d->cand_count == 0 && d->cand_begin != 0))
+    return fail(DG_E_ARG, "dg_grid_search: candidate range [%lld, +%lld) outside [0, %lld)",
+                (long long)d->cand_begin, (long long)d->cand_count, n);
+  return DG_OK;
+}
+
+dg_status grid_device(dg_model* m, const dg_grid_desc* d, dg_grid_result* result, double* means,
+                      cudaStream_t s) {
+  Scratch* sc = nullptr;
+  dg_status st = get_scratch(m->ctx, s, &sc);
+  if (st != DG_OK) return st;
+  dg::GridParams p{};
+  for (int i = 0; i < 3; ++i) {
+    p.lv[i] = d->levels[i];
+    p.L[i] = d->n_levels[i];
+  }
+  p.pos = d->positions;
+  p.n_trials = d->n_trials;
+  p.k0 = (uint32_t)d->seed;
+  p.k1 = (uint32_t)(d->seed >> 32);
+  p.offset = m->offset;
+  p.weight = m->weight;
+  const long long total = (long long)d->n_levels[0] * d->n_levels[1] * d->n_levels[2];
+  p.cand0 = d->cand_begin;
+  p.n_cand = d->cand_count ? d->cand_count : total;
+  p.means = means;
+  p.partials = sc->partials();
+  p.ticket = sc->ticket();
+  p.result = result;
+  if (d->mode == DG_MODE_PLAIN && !means) {
+    st = scratch_means(m->ctx, sc, (size_t)p.n_cand, s);
+    if (st != DG_OK) return st;
+    p.means = sc->means;
+  }
+  auto go = [&](const dg::LaunchCfg& c) -> dg_status {
+    DG_CUDA(cudaMemsetAsync(sc->ticket(), 0, 4, s));
+    DG_CUDA(dg::launch_grid(p, d->mode, c, s));
+    return DG_OK;
+  };
+  if (d->mode == DG_MODE_PLAIN) return go(dg::LaunchCfg{});
+  const std::string key = "grid/" + std::to_string(log2_bucket(p.n_cand)) + "/" +
+                          std::to_string(log2_bucket(p.n_trials));
+  return run_tuned(m->ctx, key, grid_candidates(p.n_cand), s, go);
+}
+
+// ------------------------------------------------------------ serving ---
+
+struct JobRec {
+  uint64_t id = 0;
+  dg_job job{};
+  dg_status status = DG_OK;
+  int state = 0;  // 0 queued, 1 running, 2 done
+  size_t bytes = 0;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  int slot = -1;
+  void* dmem = nullptr;
+};
+
+struct Server {
+  dg_ctx* ctx;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> queue;
+  std::unordered_map<uint64_t, std::shared_ptr<JobRec>> jobs;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  std::vector<uint64_t> slot_job;  // 0 = free
+  size_t in_use = 0;
+  uint64_t next_id = 1;
+  int64_t n_running = 0, n_done = 0;
+  bool stop = false;
+  std::thread th;
+
+  explicit Server(dg_ctx* c, int slots) : ctx(c) {
+    cudaSetDevice(ctx->device);
+    // Job memory comes from the stream-ordered allocator: allocation and
+    // release are ordered on the job's stream and never synchronize the
+    // device, so admitted jobs keep overlapping. The pool keeps freed memory
+    // for reuse instead of returning it to the driver.
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    for (int i = 0; i < slots; ++i) {
+      cudaStream_t s;
+      cudaEvent_t e;
+      cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+      cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+      streams.push_back(s);
+      events.push_back(e);
+      slot_job.push_back(0);
+    }
+    th = std::thread([this] { loop(); });
+  }
+
+  ~Server() {
+    {
+      std::lock_guard<std::mutex> g(mu);
+      stop = true;
+    }
+    cv_work.notify_all();
+    if (th.joinable()) th.join();
+    for (auto s : streams) cudaStreamSynchronize(s);
+    for (auto& kv : jobs)
+      if (kv.second->dmem) cudaFree(kv.second->dmem);
+    cudaDeviceSynchronize();
+    for (auto s : streams) cudaStreamDestroy(s);
+    for (auto e : events) cudaEventDestroy(e);
+  }
+
+  static size_t job_bytes(const dg_job& j) {
+    size_t b = 1024;  // alignment slack
+    if (j.is_grid) {
+      const size_t nc = j.grid.cand_count ? (size_t)j.grid.cand_count
+                                          : (size_t)j.grid.n_levels[0] * j.grid.n_levels[1] *
+                                                j.grid.n_levels[2];
+      b += 6 * sizeof(float) * (size_t)j.grid.n_trials;
+      b += sizeof(float) * ((size_t)j.grid.n_levels[0] + j.grid.n_levels[1] + j.grid.n_levels[2]);
+      b += sizeof(dg_grid_result) + sizeof(double) * nc;
+    } else {
+      const size_t n = (size_t)j.run.n_trials;
+      b += sizeof(float) * (run_param_floats(j.model, &j.run) + run_cond_floats(j.model, &j.run));
+      b += n * (sizeof(int8_t) + sizeof(int32_t));
+      if (j.final_state) b += n * sizeof(float) * (size_t)j.model->state_size;
+    }
+    return b + 16 * 256;
+  }
+
+  // Enqueue a job's copies and kernels on its slot's stream.
+  dg_status launch(JobRec& r, cudaStream_t s) {
+    DG_CUDA(cudaMallocAsync(&r.dmem, r.bytes, s));
+    unsigned char* p = reinterpret_cast<unsigned char*>(r.dmem);
+    auto take = [&](size_t bytes) {
+      unsigned char* q = p;
+      p += (bytes + 255) / 256 * 256;
+      return q;
+    };
+    const dg_job& j = r.job;
+    if (j.is_grid) {
+      dg_grid_desc d = j.grid;
+      const size_t nc = d.cand_count ? (size_t)d.cand_count
+                                     : (size_t)d.n_levels[0] * d.n_levels[1] * d.n_levels[2];
+      float* pos = (float*)take(6 * sizeof(float) * d.n_trials);
+      DG_CUDA(cudaMemcpyAsync(pos, j.grid.positions, 6 * sizeof(float) * d.n_trials,
+                              cudaMemcpyHostToDevice, s));
+      d.positions = pos;
+      for (int i = 0; i < 3; ++i) {
+        float* lv = (float*)take(sizeof(float) * d.n_levels[i]);
+        DG_CUDA(cudaMemcpyAsync(lv, j.grid.levels[i], sizeof(float) * d.n_levels[i],
+                                cudaMemcpyHostToDevice, s));
+        d.levels[i] = lv;
+      }
+      dg_grid_result* res = (dg_grid_result*)take(sizeof(dg_grid_result));
+      double* means = (double*)take(sizeof(double) * nc);
+      dg_status st = grid_device(j.model, &d, res, means, s);
+      if (st != DG_OK) return st;
+      DG_CUDA(cudaMemcpyAsync(j.grid_result, res, sizeof(dg_grid_result),
+                              cudaMemcpyDeviceToHost, s));
+      if (j.cand_means)
+        DG_CUDA(cudaMemcpyAsync(j.cand_means, means, sizeof(double) * nc,
+                                cudaMemcpyDeviceToHost, s));
+      return DG_OK;
+    }
+    dg_run_desc d = j.run;
+    const size_t n = (size_t)d.n_trials;
+    const size_t pf = run_param_floats(j.model, &d), cf = run_cond_floats(j.model, &d);
+    if (pf) {
+      float* tp = (float*)take(pf * sizeof(float));
+      DG_CUDA(cudaMemcpyAsync(tp, j.run.trial_params, pf * sizeof(float), cudaMemcpyHostToDevice, s));
+      d.trial_params = tp;
+    }
+    if (cf) {
+      float* ci = (float*)take(cf * sizeof(float));
+      DG_CUDA(cudaMemcpyAsync(ci, j.run.cond_inputs, cf * sizeof(float), cudaMemcpyHostToDevice, s));
+      d.cond_inputs = ci;
+    }
+    int8_t* ch = (int8_t*)take(n);
+    int32_t* stp = (int32_t*)take(n * sizeof(int32_t));
+    float* fs = j.final_state ? (float*)take(n * sizeof(float) * j.model->state_size) : nullptr;
+    dg_status st = run_device(j.model, &d, ch, stp, fs, s);
+    if (st != DG_OK) return st;
+    DG_CUDA(cudaMemcpyAsync(j.choice, ch, n, cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaMemcpyAsync(j.step, stp, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (fs)
+      DG_CUDA(cudaMemcpyAsync(j.final_state, fs, n * sizeof(float) * j.model->state_size,
+                              cudaMemcpyDeviceToHost, s));
+    return DG_OK;
+  }
+
+  void finish(JobRec& r, dg_status st) {
+    if (r.dmem) {
+      // the job's stream has passed its completion event, so this is ordered
+      // after every use of the memory
+      cudaFreeAsync(r.dmem, r.slot >= 0 ? streams[r.slot] : nullptr);
+      r.dmem = nullptr;
+    }
+    in_use -= r.bytes;
+    r.status = st;
+    r.state = 2;
+    r.t_done = now_s();
+    if (r.slot >= 0) slot_job[r.slot] = 0;
+    r.slot = -1;
+    --n_running;
+    ++n_done;
+  }
+
+  void loop() {
+    cudaSetDevice(ctx->device);
+    t_no_tune = true;
+    std::unique_lock<std::mutex> lk(mu);
+    while (true) {
+      bool progress = false;
+      // retire finished jobs
+      for (size_t i = 0; i < streams.size(); ++i) {
+        if (!slot_job[i]) continue;
+        cudaError_t q = cudaEventQuery(events[i]);
+        if (q == cudaErrorNotReady) continue;
+        auto& r = *jobs[slot_job[i]];
+        finish(r, q == cudaSuccess ? DG_OK : DG_E_CUDA);
+        progress = true;
+      }
+      if (progress) cv_done.notify_all();
+      // admit queued jobs in arrival order while memory and slots allow;
+      // the launches themselves happen without the lock
+      std::vector<std::shared_ptr<JobRec>> admitted;
+      while (!queue.empty()) {
+        auto rp = jobs[queue.front()];
+        if (in_use + rp->bytes > ctx->budget) break;
+        int slot = -1;
+        for (size_t i = 0; i < streams.size(); ++i)
+          if (!slot_job[i]) {
+            slot = (int)i;
+            break;
+          }
+        if (slot < 0) break;
+        queue.pop_front();
+        rp->slot = slot;
+        rp->state = 1;
+        rp->t_admit = now_s();
+        in_use += rp->bytes;
+        ++n_running;
+        slot_job[slot] = rp->id;
+        admitted.push_back(rp);
+      }
+      if (!admitted.empty()) {
+        progress = true;
+        lk.unlock();
+        std::vector<std::pair<std::shared_ptr<JobRec>, dg_status>> failed;
+        for (auto& rp : admitted) {
+          cudaStream_t s = streams[rp->slot];
+          dg_status st = launch(*rp, s);
+          if (st == DG_OK && cudaEventRecord(events[rp->slot], s) != cudaSuccess) st = DG_E_CUDA;
+          if (st != DG_OK) {
+            cudaStreamSynchronize(s);
+            failed.emplace_back(rp, st);
+          }
+        }
+        lk.lock();
+        for (auto& f : failed) finish(*f.first, f.second);
+        if (!failed.empty()) cv_done.notify_all();
+      }
+      if (stop) break;
+      if (!progress) {
+        if (n_running > 0)
+          cv_work.wait_for(lk, std::chrono::microseconds(50));
+        else
+          cv_work.wait_for(lk, std::chrono::milliseconds(5));
+      }
+    }
+  }
+};
+
+Server* server_of(dg_ctx* ctx) {
+  std::lock_guard<std::mutex> g(ctx->server_mu);
+  if (!ctx->server) {
+    int slots = 16;
+    if (const char* e = getenv("DG_SERVE_SLOTS")) slots = std::max(1, atoi(e));
+    ctx->server.reset(new Server(ctx, slots));
+  }
+  return ctx->server.get();
+}
+
+// ------------------------------------------------------------ compose ---
+
+uint16_t to_bf16(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);  // inf / nan
+  const uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;  // round to nearest even
+  return (uint16_t)(u >> 16);
+}
+
+float from_bf16(uint16_t h) {
+  uint32_t u = (uint32_t)h << 16;
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+}
+
+template <class T>
+dg_status upload(T** dst, const std::vector<T>& v) {
+  DG_CUDA(cudaMalloc(dst, std::max<size_t>(1, v.size()) * sizeof(T)));
+  if (!v.empty()) DG_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return DG_OK;
+}
+
+dg_status compose_transfer(dg_model* m, const dg_mechanism* mechs, int n_mech,
+                           const dg_projection* projs, int n_proj, const dg_stop* stop) {
+  std::vector<int> noff(n_mech, -1), ioff(n_mech, -1);
+  int U = 0, n_in = 0, n_logistic = 0;
+  for (int i = 0; i < n_mech; ++i) {
+    if (mechs[i].kind == DG_INPUT) {
+      ioff[i] = n_in;
+      n_in += mechs[i].size;
+    } else {
+      noff[i] = U;
+      U += mechs[i].size;
+      ++n_logistic;
+    }
+  }
+  if (n_logistic == 0) return fail(DG_E_SHAPE, "compose: no logistic layer");
+  if (stop->mech < 0 || stop->mech >= n_mech || mechs[stop->mech].kind != DG_TRANSFER_LOGISTIC)
+    return fail(DG_E_SHAPE, "compose: stop mechanism must be a logistic layer");
+  if (mechs[stop->mech].size < 2 || mechs[stop->mech].size > 16)
+    return fail(DG_E_SHAPE, "compose: stop layer needs 2..16 units");
+  double rate = -1, noise = -1;
+  for (int i = 0; i < n_mech; ++i) {
+    if (mechs[i].kind != DG_TRANSFER_LOGISTIC) continue;
+    if (!(mechs[i].rate > 0.0 && mechs[i].rate <= 1.0))
+      return fail(DG_E_ARG, "compose: mechanism %d rate must be in (0, 1]", i);
+    if (!(mechs[i].noise >= 0.0)) return fail(DG_E_ARG, "compose: mechanism %d noise < 0", i);
+    if (rate < 0) {
+      rate = mechs[i].rate;
+      noise = mechs[i].noise;
+    } else if (rate != mechs[i].rate || noise != mechs[i].noise) {
+      return fail(DG_E_UNSUPPORTED, "compose: all logistic layers must share rate and noise");
+    }
+  }
+  for (int p = 0; p < n_proj; ++p) {
+    const auto& e = projs[p];
+    if (e.sender < 0 || e.sender >= n_mech || e.receiver < 0 || e.receiver >= n_mech)
+      return fail(DG_E_SHAPE, "compose: projection %d has an invalid endpoint", p);
+    if (mechs[e.receiver].kind != DG_TRANSFER_LOGISTIC)
+      return fail(DG_E_SHAPE, "compose: projection %d must end at a logistic layer", p);
+    if (!e.weights) return fail(DG_E_ARG, "compose: projection %d has no weights", p);
+    if (e.dtype != DG_F32 && e.dtype != DG_BF16)
+      return fail(DG_E_ARG, "compose: projection %d has unknown dtype", p);
+  }
+  m->max_steps = stop->max_steps;
+  m->state_size = mechs[stop->mech].size;
+  m->n_inputs = n_in;
+  m->rate = (float)rate;
+  m->noise = (float)noise;
+  m->stop_thr = (float)stop->threshold;
+
+  // wide form: stim, task (inputs) -> hidden -> response (BF16 edge)
+  int n_inputs = 0;
+  for (int i = 0; i < n_mech; ++i) n_inputs += mechs[i].kind == DG_INPUT;
+  if (n_inputs == 2 && n_logistic == 2 && n_proj == 3) {
+    int in0 = -1, in1 = -1, hid = -1, resp = stop->mech;
+    for (int i = 0; i < n_mech; ++i) {
+      if (mechs[i].kind == DG_INPUT) (in0 < 0 ? in0 : in1) = i;
+      else if (i != resp) hid = i;
+    }
+    const dg_projection *ps = nullptr, *pt = nullptr, *pr = nullptr;
+    for (int p = 0; p < n_proj; ++p) {
+      if (projs[p].sender == in0 && projs[p].receiver == hid) ps = &projs[p];
+      if (projs[p].sender == in1 && projs[p].receiver == hid) pt = &projs[p];
+      if (projs[p].sender == hid && projs[p].receiver == resp) pr = &projs[p];
+    }
+    const int H = hid >= 0 ? mechs[hid].size : 0;
+    if (ps && pt && pr && pr->dtype == DG_BF16 && H >= 64 && H <= 256 && H % 64 == 0 &&
+        mechs[resp].size == 16) {
+      m->kind = K_WIDE;
+      m->S = mechs[in0].size;
+      m->T = mechs[in1].size;
+      m->H = H;
+      m->R = 16;
+      m->bias_h = (float)mechs[hid].bias;
+      m->gain_h = (float)mechs[hid].gain;
+      m->bias_r = (float)mechs[resp].bias;
+      m->gain_r = (float)mechs[resp].gain;
+      std::vector<float> ws(ps->weights, ps->weights + (size_t)H * m->S);
+      std::vector<float> wt(pt->weights, pt->weights + (size_t)H * m->T);
+      std::vector<uint16_t> wr(16 * (size_t)H);
+      std::vector<float> wrf(16 * (size_t)H);
+      for (size_t i = 0; i < wr.size(); ++i) {
+        wr[i] = to_bf16(pr->weights[i]);
+        wrf[i] = from_bf16(wr[i]);
+      }
+      dg_status st;
+      if ((st = upload(&m->d_w_stim, ws)) != DG_OK) return st;
+      if ((st = upload(&m->d_w_task, wt)) != DG_OK) return st;
+      if ((st = upload(&m->d_w_resp_bf16, wr)) != DG_OK) return st;
+      if ((st = upload(&m->d_w_resp_f32, wrf)) != DG_OK) return st;
+      return DG_OK;
+    }
+  }
+  for (int p = 0; p < n_proj; ++p)
+    if (projs[p].dtype != DG_F32)
+      return fail(DG_E_UNSUPPORTED, "compose: BF16 weights only on the wide network's response edge");
+
+  if (U > dg::kNetMaxUnits || n_in > dg::kNetMaxInputs)
+    return fail(DG_E_UNSUPPORTED, "compose: small-network kernel takes <= %d logistic and <= %d input units",
+                dg::kNetMaxUnits, dg::kNetMaxInputs);
+  m->kind = K_NET;
+  dg::NetLayout& L = m->layout;
+  memset(&L, 0, sizeof L);
+  L.U = U;
+  L.n_in = n_in;
+  L.rate = (float)rate;
+  L.noise = (float)noise;
+  L.stop_off = noff[stop->mech];
+  L.stop_size = mechs[stop->mech].size;
+  L.stop_threshold = (float)stop->threshold;
+  L.max_steps = stop->max_steps;
+  for (int i = 0; i < n_mech; ++i)
+    if (noff[i] >= 0)
+      for (int u = 0; u < mechs[i].size; ++u) {
+        L.gain[noff[i] + u] = (float)mechs[i].gain;
+        L.bias[noff[i] + u] = (float)mechs[i].bias;
+      }
+  std::vector<float> w_in((size_t)U * std::max(1, n_in), 0.f);
+  int ne = 0;
+  for (int p = 0; p < n_proj; ++p) {
+    const auto& e = projs[p];
+    const int rs = mechs[e.receiver].size, ss = mechs[e.sender].size;
+    for (int i = 0; i < rs; ++i)
+      for (int j = 0; j < ss; ++j) {
+        const float w = e.weights[(size_t)i * ss + j];
+        const int dst = noff[e.receiver] + i;
+        if (mechs[e.sender].kind == DG_INPUT) {
+          w_in[(size_t)dst * n_in + ioff[e.sender] + j] += w;
+        } else {
+          if (ne >= dg::kNetMaxEdges)
+            return fail(DG_E_UNSUPPORTED, "compose: more than %d edges between logistic units",
+                        dg::kNetMaxEdges);
+          L.edge_dst[ne] = (int16_t)dst;
+          L.edge_src[ne] = (int16_t)(noff[e.sender] + j);
+          L.edge_w[ne] = w;
+          ++ne;
+        }
+      }
+  }
+  L.n_edges = ne;
+  dg_status st;
+  if ((st = upload(&m->d_w_in, w_in)) != DG_OK) return st;
+  DG_CUDA(cudaMalloc(&m->d_layout, sizeof(dg::NetLayout)));
+  DG_CUDA(cudaMemcpy(m->d_layout, &L, sizeof L, cudaMemcpyHostToDevice));
+  return DG_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI ===
+
+extern "C" {
+
+const char* dg_last_error(void) { return g_err.c_str(); }
+
+const char* dg_version(void) { return "distill-gpu 0.1 sm_103a"; }
+
+dg_status dg_create(dg_ctx** out, int device, size_t hbm_budget_bytes) {
+  if (!out) return fail(DG_E_ARG, "dg_create: null out");
+  int n = 0;
+  DG_CUDA(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return fail(DG_E_ARG, "dg_create: device %d of %d", device, n);
+  DG_CUDA(cudaSetDevice(device));
+  DG_CUDA(cudaFree(nullptr));  // create the primary context
+  dg_ctx* c = new dg_ctx;
+  c->device = device;
+  c->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)150 * 1000 * 1000 * 1000;
+  if (const char* e = getenv("DG_AUTOTUNE")) c->autotune = atoi(e) != 0;
+  if (const char* e = getenv("DG_AUTOTUNE_CACHE")) c->tune_file = e;
+  load_tune_file(c);
+  *out = c;
+  return DG_OK;
+}
+
+dg_status dg_destroy(dg_ctx* ctx) {
+  if (!ctx) return fail(DG_E_ARG, "dg_destroy: null ctx");
+  ctx->server.reset();
+  // streams that own scratch may already be destroyed (serving slots, batch
+  // branches): wait for the whole device instead of per stream
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : ctx->scratch) {
+    cudaFree(kv.second.base);
+    if (kv.second.means) cudaFree(kv.second.means);
+  }
+  delete ctx;
+  return DG_OK;
+}
+
+dg_status dg_compose(dg_ctx* ctx, const dg_mechanism* mechs, int32_t n_mech,
+                     const dg_projection* projs, int32_t n_proj, const dg_stop* stop,
+                     dg_model** out) {
+  if (!ctx || !mechs || !stop || !out || n_mech < 1 || n_proj < 0 || (n_proj > 0 && !projs))
+    return fail(DG_E_ARG, "dg_compose: null or empty arguments");
+  if (stop->max_steps < 1) return fail(DG_E_ARG, "dg_compose: stop.max_steps must be >= 1");
+  for (int i = 0; i < n_mech; ++i) {
+    if (mechs[i].kind < DG_INPUT || mechs[i].kind > DG_PP_OBJECTIVE)
+      return fail(DG_E_ARG, "dg_compose: mechanism %d has unknown kind %d", i, mechs[i].kind);
+    if (mechs[i].size < 1) return fail(DG_E_SHAPE, "dg_compose: mechanism %d has size < 1", i);
+  }
+  DG_CUDA(cudaSetDevice(ctx->device));
+  std::unique_ptr<dg_model> m(new dg_model);
+  m->ctx = ctx;
+  int counts[7] = {0};
+  for (int i = 0; i < n_mech; ++i) counts[mechs[i].kind]++;
+  const int integrators = counts[DG_DDM] + counts[DG_LCA];
+  const int pp = counts[DG_PP_OBSERVE] + counts[DG_PP_ACTION] + counts[DG_PP_OBJECTIVE];
+
+  if (integrators > 0) {
+    if (integrators != 1 || counts[DG_TRANSFER_LOGISTIC] || pp || counts[DG_INPUT] > 1)
+      return fail(DG_E_SHAPE, "dg_compose: an integrator model has one DDM or LCA (and at most one input)");
+    int im = -1, in = -1;
+    for (int i = 0; i < n_mech; ++i) {
+      if (mechs[i].kind == DG_DDM || mechs[i].kind == DG_LCA) im = i;
+      else in = i;
+    }
+    const dg_mechanism& g = mechs[im];
+    if (in >= 0) {
+      if (mechs[in].size != g.size)
+        return fail(DG_E_SHAPE, "dg_compose: input size %d != integrator size %d", mechs[in].size, g.size);
+      if (n_proj != 1 || projs[0].sender != in || projs[0].receiver != im || projs[0].weights)
+        return fail(DG_E_SHAPE, "dg_compose: input feeds the integrator by one identity projection (NULL weights)");
+    } else if (n_proj != 0) {
+      return fail(DG_E_SHAPE, "dg_compose: integrator model without input takes no projections");
+    }
+    if (stop->mech != im) return fail(DG_E_SHAPE, "dg_compose: stop must name the integrator");
+    if (!(g.dt > 0.0) || !(g.noise >= 0.0))
+      return fail(DG_E_ARG, "dg_compose: integrator needs dt > 0 and noise >= 0");
+    m->dt = (float)g.dt;
+    m->diffusion = (float)(g.noise * std::sqrt(g.dt));
+    m->max_steps = stop->max_steps;
+    if (g.kind == DG_DDM) {
+      if (g.size != 1) return fail(DG_E_SHAPE, "dg_compose: DDM has size 1");
+      m->kind = K_DDM;
+      m->x0 = (float)g.start;
+      m->state_size = 1;
+    } else {
+      if (g.size > 16) return fail(DG_E_UNSUPPORTED, "dg_compose: LCA size %d > 16", g.size);
+      if ((g.flags & DG_LCA_TWO_SIDED) && g.size != 1)
+        return fail(DG_E_SHAPE, "dg_compose: two-sided LCA needs size 1");
+      if (!(stop->threshold > 0.0)) return fail(DG_E_ARG, "dg_compose: LCA threshold must be > 0");
+      m->kind = K_LCA;
+      m->N = g.size;
+      m->leak = (float)g.leak;
+      m->inhibition = (float)g.inhibition;
+      m->threshold = (float)stop->threshold;
+      m->rectify = (g.flags & DG_LCA_NO_RECTIFY) ? 0 : 1;
+      m->two_sided = (g.flags & DG_LCA_TWO_SIDED) ? 1 : 0;
+      m->state_size = g.size;
+    }
+    *out = m.release();
+    return DG_OK;
+  }
+
+  if (pp > 0) {
+    if (n_mech != 4 || counts[DG_INPUT] != 1 || counts[DG_PP_OBSERVE] != 1 ||
+        counts[DG_PP_ACTION] != 1 || counts[DG_PP_OBJECTIVE] != 1)
+      return fail(DG_E_SHAPE, "dg_compose: predator-prey model is input -> observe -> action -> objective");
+    int idx[7] = {-1, -1, -1, -1, -1, -1, -1};
+    for (int i = 0; i < n_mech; ++i) idx[mechs[i].kind] = i;
+    if (mechs[idx[DG_INPUT]].size != 6 || mechs[idx[DG_PP_OBSERVE]].size != 6 ||
+        mechs[idx[DG_PP_ACTION]].size != 2 || mechs[idx[DG_PP_OBJECTIVE]].size != 1)
+      return fail(DG_E_SHAPE, "dg_compose: predator-prey sizes are 6, 6, 2, 1");
+    const int chain[4] = {idx[DG_INPUT], idx[DG_PP_OBSERVE], idx[DG_PP_ACTION], idx[DG_PP_OBJECTIVE]};
+    if (n_proj != 3) return fail(DG_E_SHAPE, "dg_compose: predator-prey model has 3 projections");
+    for (int k = 0; k < 3; ++k) {
+      bool found = false;
+      for (int p = 0; p < n_proj; ++p)
+        if (projs[p].sender == chain[k] && projs[p].receiver == chain[k + 1] && !projs[p].weights)
+          found = true;
+      if (!found) return fail(DG_E_SHAPE, "dg_compose: predator-prey projection %d -> %d missing", chain[k], chain[k + 1]);
+    }
+    const double off = mechs[idx[DG_PP_OBSERVE]].offset;
+    if (!(off > 0.0)) return fail(DG_E_ARG, "dg_compose: observation offset must be > 0");
+    m->kind = K_PP;
+    m->offset = (float)off;
+    m->weight = (float)mechs[idx[DG_PP_ACTION]].weight;
+    m->max_steps = stop->max_steps;
+    *out = m.release();
+    return DG_OK;
+  }
+
+  dg_status st = compose_transfer(m.get(), mechs, n_mech, projs, n_proj, stop);
+  if (st != DG_OK) {
+    dg_model_free(m.release());
+    return st;
+  }
+  *out = m.release();
+  return DG_OK;
+}
+
+dg_status dg_model_free(dg_model* m) {
+  if (!m) return fail(DG_E_ARG, "dg_model_free: null model");
+  cudaFree(m->d_layout);
+  cudaFree(m->d_w_in);
+  cudaFree(m->d_w_stim);
+  cudaFree(m->d_w_task);
+  cudaFree(m->d_w_resp_bf16);
+  cudaFree(m->d_w_resp_f32);
+  delete m;
+  return DG_OK;
+}
+
+dg_status dg_model_info(const dg_model* m, int32_t* kind, int32_t* state_size) {
+  if (!m) return fail(DG_E_ARG, "dg_model_info: null model");
+  if (kind) *kind = m->kind;
+  if (state_size) *state_size = m->state_size;
+  return DG_OK;
+}
+
+dg_status dg_run(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t* step,
+                 float* final_state, void* stream) {
+  dg_status st = check_run_args(m, d, choice, step);
+  if (st != DG_OK) return st;
+  DG_CUDA(cudaSetDevice(m->ctx->device));
+  return run_device(m, d, choice, step, final_state, (cudaStream_t)stream);
+}
+
+dg_status dg_grid_search(dg_model* m, const dg_grid_desc* d, dg_grid_result* result,
+                         double* cand_means, void* stream) {
+  dg_status st = check_grid_args(m, d, result);
+  if (st != DG_OK) return st;
+  DG_CUDA(cudaSetDevice(m->ctx->device));
+  return grid_device(m, d, result, cand_means, (cudaStream_t)stream);
+}
+
+dg_status dg_argmax_f64(dg_ctx* ctx, const double* values, int64_t n, dg_grid_result* result,
+                        void* stream) {
+  if (!ctx || !values || !result || n < 1) return fail(DG_E_ARG, "dg_argmax_f64: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch* sc = nullptr;
+  dg_status st = get_scratch(ctx, s, &sc);
+  if (st != DG_OK) return st;
+  DG_CUDA(cudaMemsetAsync(sc->ticket(), 0, 4, s));
+  DG_CUDA(dg::launch_argmax(values, n, sc->partials(), sc->ticket(), result, s));
+  return DG_OK;
+}
+
+dg_status dg_philox_words(uint64_t seed, uint32_t trial, uint32_t cand, uint32_t purpose,
+                          uint32_t block0, int64_t nblocks, uint32_t* out, void* stream) {
+  if (nblocks < 0 || (nblocks > 0 && !out)) return fail(DG_E_ARG, "dg_philox_words: bad arguments");
+  if (((uintptr_t)out & 15u) != 0) return fail(DG_E_ARG, "dg_philox_words: out must be 16-byte aligned");
+  DG_CUDA(dg::launch_philox_words(seed, trial, cand, purpose, block0, nblocks, out,
+                                  (cudaStream_t)stream));
+  return DG_OK;
+}
+
+dg_status dg_normals(uint64_t seed, uint32_t trial, uint32_t cand, uint64_t d0, int64_t n,
+                     float* out, void* stream) {
+  if (n < 0 || (n > 0 && !out)) return fail(DG_E_ARG, "dg_normals: bad arguments");
+  DG_CUDA(dg::launch_normals(seed, trial, cand, d0, n, out, (cudaStream_t)stream));
+  return DG_OK;
+}
+
+// ---------------------------------------------------------------- batch ---
+
+struct dg_batch {
+  dg_ctx* ctx;
+  struct Op {
+    dg_model* m;
+    bool grid;
+    dg_run_desc run;
+    dg_grid_desc gd;
+    int8_t* choice;
+    int32_t* step;
+    float* fs;
+    dg_grid_result* res;
+    double* means;
+  };
+  std::vector<Op> ops;
+  std::vector<cudaStream_t> side;
+  cudaStream_t cap = nullptr;  // private capture stream (the legacy stream cannot be captured)
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t exec = nullptr;
+};
+
+dg_status dg_batch_create(dg_ctx* ctx, dg_batch** out) {
+  if (!ctx || !out) return fail(DG_E_ARG, "dg_batch_create: null argument");
+  dg_batch* b = new dg_batch;
+  b->ctx = ctx;
+  *out = b;
+  return DG_OK;
+}
+
+dg_status dg_batch_add_run(dg_batch* b, dg_model* m, const dg_run_desc* d, int8_t* choice,
+                           int32_t* step, float* final_state) {
+  if (!b) return fail(DG_E_ARG, "dg_batch_add_run: null batch");
+  if (b->exec) return fail(DG_E_STATE, "dg_batch_add_run: batch already launched");
+  dg_status st = check_run_args(m, d, choice, step);
+  if (st != DG_OK) return st;
+  dg_batch::Op op{};
+  op.m = m;
+  op.grid = false;
+  op.run = *d;
+  op.choice = choice;
+  op.step = step;
+  op.fs = final_state;
+  b->ops.push_back(op);
+  return DG_OK;
+}
+
+dg_status dg_batch_add_grid(dg_batch* b, dg_model* m, const dg_grid_desc* d,
+                            dg_grid_result* result, double* cand_means) {
+  if (!b) return fail(DG_E_ARG, "dg_batch_add_grid: null batch");
+  if (b->exec) return fail(DG_E_STATE, "dg_batch_add_grid: batch already launched");
+  dg_status st = check_grid_args(m, d, result);
+  if (st != DG_OK) return st;
+  dg_batch::Op op{};
+  op.m = m;
+  op.grid = true;
+  op.gd = *d;
+  op.res = result;
+  op.means = cand_means;
+  b->ops.push_back(op);
+  return DG_OK;
+}
+
+static dg_status batch_op(dg_batch::Op& op, cudaStream_t s) {
+  if (op.grid) return grid_device(op.m, &op.gd, op.res, op.means, s);
+  return run_device(op.m, &op.run, op.choice, op.step, op.fs, s);
+}
+
+dg_status dg_batch_launch(dg_batch* b, void* stream) {
+  if (!b) return fail(DG_E_ARG, "dg_batch_launch: null batch");
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_CUDA(cudaSetDevice(b->ctx->device));
+  if (b->exec) {
+    DG_CUDA(cudaGraphLaunch(b->exec, s));
+    return DG_OK;
+  }
+  if (b->ops.empty()) return DG_OK;
+  // one forked stream per op; scratch and tuned shapes prepared outside capture
+  for (size_t i = 0; i < b->ops.size(); ++i) {
+    cudaStream_t side;
+    DG_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    b->side.push_back(side);
+    cudaEvent_t e;
+    DG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    b->join.push_back(e);
+    dg_status st = batch_op(b->ops[i], side);  // tunes shapes, allocates scratch
+    if (st != DG_OK) return st;
+  }
+  for (auto side : b->side) DG_CUDA(cudaStreamSynchronize(side));
+  DG_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+  DG_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  cudaStream_t cs = b->cap;
+  DG_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  dg_status st = DG_OK;
+  if (cudaEventRecord(b->fork, cs) != cudaSuccess) st = fail(DG_E_CUDA, "batch: fork record");
+  for (size_t i = 0; i < b->ops.size() && st == DG_OK; ++i) {
+    if (cudaStreamWaitEvent(b->side[i], b->fork, 0) != cudaSuccess) {
+      st = fail(DG_E_CUDA, "batch: fork wait");
+      break;
+    }
+    st = batch_op(b->ops[i], b->side[i]);
+    if (st != DG_OK) break;
+    if (cudaEventRecord(b->join[i], b->side[i]) != cudaSuccess ||
+        cudaStreamWaitEvent(cs, b->join[i], 0) != cudaSuccess)
+      st = fail(DG_E_CUDA, "batch: join");
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t ec = cudaStreamEndCapture(cs, &g);
+  if (st != DG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (ec != cudaSuccess) return fail(DG_E_CUDA, "batch: end capture: %s", cudaGetErrorString(ec));
+  ec = cudaGraphInstantiate(&b->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ec != cudaSuccess) return fail(DG_E_CUDA, "batch: instantiate: %s", cudaGetErrorString(ec));
+  DG_CUDA(cudaGraphLaunch(b->exec, s));
+  return DG_OK;
+}
+
+dg_status dg_batch_free(dg_batch* b) {
+  if (!b) return fail(DG_E_ARG, "dg_batch_free: null batch");
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto s : b->side) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  for (auto e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+  return DG_OK;
+}
+
+// -------------------------------------------------------------- serving ---
+
+dg_status dg_submit(dg_ctx* ctx, const dg_job* job, uint64_t* ticket) {
+  if (!ctx || !job || !ticket || !job->model) return fail(DG_E_ARG, "dg_submit: null argument");
+  dg_status st;
+  if (job->is_grid) {
+    if (!job->grid_result) return fail(DG_E_ARG, "dg_submit: grid job needs grid_result");
+    st = check_grid_args(job->model, &job->grid, job->grid_result);
+  } else {
+    st = check_run_args(job->model, &job->run, job->choice, job->step);
+  }
+  if (st != DG_OK) return st;
+  Server* sv = server_of(ctx);
+  auto r = std::make_shared<JobRec>();
+  r->job = *job;
+  r->bytes = Server::job_bytes(*job);
+  if (r->bytes > ctx->budget)
+    return fail(DG_E_BUDGET, "dg_submit: job needs %zu bytes, budget is %zu", r->bytes, ctx->budget);
+  r->t_submit = now_s();
+  {
+    std::lock_guard<std::mutex> g(sv->mu);
+    r->id = sv->next_id++;
+    sv->jobs[r->id] = r;
+    sv->queue.push_back(r->id);
+  }
+  sv->cv_work.notify_all();
+  *ticket = r->id;
+  return DG_OK;
+}
+
+dg_status dg_wait(dg_ctx* ctx, uint64_t ticket, int32_t timeout_ms, dg_job_result* result) {
+  if (!ctx) return fail(DG_E_ARG, "dg_wait: null ctx");
+  Server* sv = server_of(ctx);
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->jobs.find(ticket);
+  if (it == sv->jobs.end()) return fail(DG_E_ARG, "dg_wait: unknown ticket %llu", (unsigned long long)ticket);
+  std::shared_ptr<JobRec> r = it->second;
+  auto done = [&] { return r->state == 2; };
+  if (timeout_ms < 0) {
+    sv->cv_done.wait(lk, done);
+  } else if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done)) {
+    return fail(DG_E_TIMEOUT, "dg_wait: ticket %llu not done after %d ms",
+                (unsigned long long)ticket, timeout_ms);
+  }
+  if (result) {
+    result->status = r->status;
+    result->t_submit = r->t_submit;
+    result->t_admit = r->t_admit;
+    result->t_done = r->t_done;
+    result->device_bytes = r->bytes;
+  }
+  sv->jobs.erase(ticket);
+  if (r->status != DG_OK) return fail((dg_status)r->status, "job %llu failed", (unsigned long long)ticket);
+  return DG_OK;
+}
+
+dg_status dg_serve_stats(dg_ctx* ctx, int64_t* queued, int64_t* running, int64_t* done,
+                         uint64_t* bytes_in_use) {
+  if (!ctx) return fail(DG_E_ARG, "dg_serve_stats: null ctx");
+  Server* sv = server_of(ctx);
+  std::lock_guard<std::mutex> g(sv->mu);
+  if (queued) *queued = (int64_t)sv->queue.size();
+  if (running) *running = sv->n_running;
+  if (done) *done = sv->n_done;
+  if (bytes_in_use) *bytes_in_use = sv->in_use;
+  return DG_OK;
+}
+
+}  // extern "C"

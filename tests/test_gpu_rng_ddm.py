@@ -1,0 +1,116 @@
+"""GPU parity: Philox words, normals and the DDM kernels against the oracle."""
+import numpy as np
+import pytest
+
+from gpu_util import FLOAT_RTOL, compare_decisions, dev, host, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2110_15425_gb300 import binding as B
+    torch.cuda.init()
+    c = B.dg_create(0)
+    yield c
+    B.dg_destroy(c)
+
+
+@pytest.mark.parametrize("seed,trial,cand,purpose,block0,n", [
+    (0, 0, 0, 0, 0, 1000), (11, 5, 0, 0, 2000, 333), ((7 << 32) | 99, 123456, 26999, 0, 0, 64),
+    (0xFFFFFFFFFFFFFFFF, 0xFFFFFFFF, 0xFFFFFFFF, 3, 0xFFFFFFF0, 16)])
+def test_philox_words_bitwise(orc, seed, trial, cand, purpose, block0, n):
+    import torch
+    from paper_2110_15425_gb300 import binding as B
+    out = torch.zeros(4 * n, dtype=torch.int32, device="cuda")
+    B.dg_philox_words(seed, trial, cand, purpose, block0, n, out)
+    got = host(out).view(np.uint32)
+    ref = orc.philox_words(seed, trial, cand, purpose, block0, n)
+    assert np.array_equal(got, ref)
+
+
+def test_normals_match_oracle(orc):
+    import torch
+    from paper_2110_15425_gb300 import binding as B
+    n = 1 << 16
+    out = torch.zeros(n, dtype=torch.float32, device="cuda")
+    B.dg_normals(42, 7, 3, 5, n, out)
+    got = host(out).astype(np.float64)
+    ref = orc.normals(42, 7, 3, 5, n)
+    err = np.abs(got - ref)
+    assert err.max() < 2e-6 * max(1.0, np.abs(ref).max()), err.max()
+    assert np.max(err / np.maximum(np.abs(ref), 1.0)) < 1e-6
+
+
+def _ddm_run(ctx, A, z, seed, mode, max_steps=10000, dt=1e-3, sigma=1.0):
+    import torch
+    from paper_2110_15425_gb300 import binding as B
+    n = A.shape[0]
+    model = B.compose_ddm(ctx, dt=dt, sigma=sigma, max_steps=max_steps)
+    try:
+        params = dev(np.concatenate([A, z]).astype(np.float32))
+        choice = torch.zeros(max(n, 1), dtype=torch.int8, device="cuda")
+        step = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
+        xs = torch.zeros(max(n, 1), dtype=torch.float32, device="cuda")
+        B.dg_run(model, B.run_desc(n, seed, trial_params=params, mode=mode), choice, step, xs)
+        return host(choice)[:n], host(step)[:n], host(xs)[:n]
+    finally:
+        B.dg_model_free(model)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("n", [1, 37, 5000])
+def test_ddm_parity_small(ctx, orc, threads, mode, n):
+    from paper_2110_15425_gb300 import workloads as W
+    w = W.ddm(n_trials=n, param_seed=5)
+    c, s, x = _ddm_run(ctx, w["A"], w["z"], w["seed"], mode)
+    ref = orc.ddm_run(w["A"], w["z"], w["seed"], threads=threads)
+    excl = compare_decisions(c, s, ref, f"ddm mode={mode}")
+    assert excl <= max(2, n // 200)
+    keep = ref["margin"] >= 1e-5
+    assert rel_err(x[keep], ref["x"][keep], w["z"][keep]) < FLOAT_RTOL
+
+
+@pytest.mark.parametrize("max_steps", [1, 2, 7, 13])
+def test_ddm_short_caps(ctx, orc, max_steps):
+    from paper_2110_15425_gb300 import workloads as W
+    w = W.ddm(n_trials=300, param_seed=6)
+    w["A"][:10] = 50.0  # crosses within the first steps
+    for mode in (0, 1):
+        c, s, x = _ddm_run(ctx, w["A"], w["z"], 3, mode, max_steps=max_steps)
+        ref = orc.ddm_run(w["A"], w["z"], 3, max_steps=max_steps)
+        compare_decisions(c, s, ref, f"cap {max_steps}")
+        assert np.all(s <= max_steps)
+
+
+def test_ddm_empty(ctx):
+    c, s, x = _ddm_run(ctx, np.zeros(0, np.float32), np.zeros(0, np.float32), 1, 0)
+    assert c.size == 0
+
+
+def test_ddm_plain_equals_batched(ctx):
+    from paper_2110_15425_gb300 import workloads as W
+    w = W.ddm(n_trials=20000, param_seed=7)
+    a = _ddm_run(ctx, w["A"], w["z"], 9, 0)
+    b = _ddm_run(ctx, w["A"], w["z"], 9, 1)
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+
+
+def test_ddm_full_size_sampled(ctx, orc, threads):
+    """2^20 trials in the benchmark's launch configuration; 4096 sampled
+    trials replayed by the oracle."""
+    from paper_2110_15425_gb300 import workloads as W
+    w = W.ddm()
+    c, s, x = _ddm_run(ctx, w["A"], w["z"], w["seed"], 0)
+    rng = np.random.default_rng(0)
+    ids = np.sort(rng.choice(w["A"].shape[0], 4096, replace=False)).astype(np.uint32)
+    ref = orc.ddm_run(w["A"], w["z"], w["seed"], trial_ids=ids, threads=threads)
+    compare_decisions(c[ids], s[ids], ref, "ddm full")
+    keep = ref["margin"] >= 1e-5
+    assert rel_err(x[ids][keep], ref["x"][keep], w["z"][ids][keep]) < FLOAT_RTOL
+    # properties at any size: decisions are +-1 or timeouts; steps in range
+    assert set(np.unique(c)).issubset({-1, 0, 1})
+    assert s.min() >= 1 and s.max() <= 10000
+    assert np.all(s[c == -1] == 10000)
