@@ -214,6 +214,28 @@ dg_status dg_grid_search(dg_model* model, const dg_grid_desc* desc, dg_grid_resu
 dg_status dg_argmax_f64(dg_ctx* ctx, const double* values, int64_t n, dg_grid_result* result,
                         void* stream);
 
+/* Allocation-free dg_grid_search. The paper has no counterpart: this entry
+   point exists for callers that may not allocate device memory themselves or
+   let a library do it behind their back - code that runs while someone else's
+   CUDA graph capture is open (cudaMalloc is not a stream operation and breaks
+   the capture), frameworks whose own allocator owns the whole device budget,
+   and latency-bound loops where a device allocation would stall other work.
+   dg_grid_search allocates its scratch (argmax ticket, per-block partials,
+   and for the plain form without cand_means a per-candidate means buffer) on
+   first use of each stream; this call uses a fixed array in the library's own
+   device memory instead (280 KiB, present on every GPU that loads the library
+   until the process exits) and calls no allocator.
+   Same arguments, outputs and results as dg_grid_search, with these limits:
+     - DG_MODE_PLAIN without cand_means evaluates at most 32768 candidates
+       per call (DG_E_ARG beyond that);
+     - the first call on a device looks up the array's device address; make
+       that first call before any stream capture on that device;
+     - every call shares the one array and it keeps the last call's contents
+       (the call clears what must start at zero), so calls that may overlap
+       on the GPU, e.g. on two streams without ordering, race: order them. */
+dg_status dg_grid_search_noalloc(dg_model* model, const dg_grid_desc* desc,
+                                 dg_grid_result* result, double* cand_means, void* stream);
+
 /* ------------------------------------------------------ RNG replay (parity) --- */
 
 /* Raw Philox4x32-10 words of blocks block0 .. block0+nblocks-1 of

@@ -958,6 +958,40 @@ dg_status compose_transfer(dg_model* m, const dg_mechanism* mechs, int n_mech,
 
 }  // namespace
 
+namespace dg {
+
+// Validate a grid search and fill its kernel parameters without touching any
+// scratch or allocating anything; the caller supplies partials, ticket and,
+// for the plain form without cand_means, the means buffer.
+dg_status grid_params_noalloc(dg_model* m, const dg_grid_desc* d, dg_grid_result* result,
+                              double* cand_means, GridParams* p) {
+  dg_status st = check_grid_args(m, d, result);
+  if (st != DG_OK) return st;
+  *p = GridParams{};
+  for (int i = 0; i < 3; ++i) {
+    p->lv[i] = d->levels[i];
+    p->L[i] = d->n_levels[i];
+  }
+  p->pos = d->positions;
+  p->n_trials = d->n_trials;
+  p->k0 = (uint32_t)d->seed;
+  p->k1 = (uint32_t)(d->seed >> 32);
+  p->offset = m->offset;
+  p->weight = m->weight;
+  const long long total = (long long)d->n_levels[0] * d->n_levels[1] * d->n_levels[2];
+  p->cand0 = d->cand_begin;
+  p->n_cand = d->cand_count ? d->cand_count : total;
+  p->means = cand_means;
+  p->result = result;
+  return DG_OK;
+}
+
+dg_status set_error(dg_status s, const char* msg) { return fail(s, "%s", msg); }
+
+int model_device(const dg_model* m) { return m->ctx->device; }
+
+}  // namespace dg
+
 // ===================================================================== ABI ===
 
 extern "C" {
