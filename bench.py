@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--profile-once", action="store_true",
                     help="run warmup + 1 step only (for ncu launch lists)")
+    ap.add_argument("--only", default=None,
+                    choices=["ddm", "lca4", "lca8", "lca16", "grid", "stroop", "wide"],
+                    help="one job of this kind, default launch shape, 1 warm + 1 timed launch "
+                         "(the small case for per-kernel ncu captures)")
+    ap.add_argument("--n", type=int, default=0, help="trials (or candidates) for --only")
     return ap.parse_args()
 
 
@@ -259,7 +264,7 @@ def cpu_baseline(seconds_hint=True):
     import oracle
     from paper_2110_15425_gb300 import workloads as W
     threads = os.cpu_count() or 1
-    frac = 16
+    frac = 4
     t0 = time.perf_counter()
     steps = 0
     s = W.stroop_small()
@@ -321,10 +326,66 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ main ---
 
+def run_only(args):
+    """One job of one kind: the small case for single-kernel profiles."""
+    os.environ["DG_AUTOTUNE"] = "0"
+    import torch
+    from paper_2110_15425_gb300 import binding as B
+    from paper_2110_15425_gb300 import workloads as W
+    ctx = B.dg_create(0)
+    cuda = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    k = args.only
+    if k == "grid":
+        L = max(2, round(args.n ** (1 / 3))) if args.n else 30
+        g = W.predator_prey(levels=L)
+        m = B.compose_predator_prey(ctx)
+        lv = [cuda(x) for x in g["levels"]]
+        pos = cuda(g["pos"])
+        res = torch.zeros(3, dtype=torch.float64, device="cuda")
+        go = lambda: B.dg_grid_search(m, B.grid_desc(lv, pos, g["seed"]), res)  # noqa: E731
+    else:
+        if k == "ddm":
+            w = W.ddm(n_trials=args.n or (1 << 20))
+            m = B.compose_ddm(ctx)
+            p = cuda(np.concatenate([w["A"], w["z"]]))
+            d = B.run_desc(w["A"].shape[0], w["seed"], trial_params=p)
+        elif k.startswith("lca"):
+            w = W.lca(n_trials=args.n or 262144, N=int(k[3:]))
+            m = B.compose_lca(ctx, w["N"])
+            p = cuda(w["I"])
+            d = B.run_desc(w["I"].shape[0], w["seed"], trial_params=p)
+        else:
+            w = W.stroop_small() if k == "stroop" else W.stroop_wide(n_trials=args.n or WIDE_TRIALS)
+            m = B.compose_network(ctx, w["layers"], w["projections"], rate=w["rate"],
+                                  noise_sd=w["noise_sd"], stop_layer=w["stop_layer"],
+                                  stop_threshold=w["stop_threshold"], max_steps=w["max_steps"],
+                                  bf16_edges=(2,) if k == "wide" else ())
+            p = cuda(w["cond_inputs"])
+            d = B.run_desc(w["n_trials"], w["seed"], cond_inputs=p, n_cond=p.shape[0],
+                           cond_block=w["cond_block"])
+        n = d.n_trials
+        ch = torch.zeros(n, dtype=torch.int8, device="cuda")
+        st = torch.zeros(n, dtype=torch.int32, device="cuda")
+        go = lambda: B.dg_run(m, d, ch, st)  # noqa: E731
+    go()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    go()
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"only": k, "n": args.n, "ms": e0.elapsed_time(e1)}))
+    B.dg_model_free(m)
+    B.dg_destroy(ctx)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.only:
+        run_only(args)
         return
     rank, local, world = dist_env()
     import torch

@@ -23,11 +23,11 @@ constexpr unsigned kFull = 0xffffffffu;
 __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    // one 32x32 -> 64-bit multiply gives both halves of each product
+    const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53ull;
+    const unsigned long long p1 = (unsigned long long)c.z * 0xCD9E8D57ull;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
   }
@@ -45,13 +45,30 @@ __device__ __forceinline__ float u01(uint32_t w) {
   return fmaf(__uint2float_rn(w >> 9), 0x1p-23f, 0x1p-24f);
 }
 
-// Box-Muller (1958): radius from the first word, angle from the second.
+// -ln(u) for u in (0, 1). The hardware log2 approximation has a small
+// absolute error, which is a large relative error when u is close to 1 and
+// ln(u) is tiny; there the Taylor series of -ln(1 - v) = v + v^2/2 + v^3/3 +
+// ... in v = 1 - u (exact in binary32 for u >= 1/2) is used instead: for
+// v < 2^-6 five terms leave a relative truncation error below 2e-10.
+__device__ __forceinline__ float neg_log_u01(float u) {
+  const float v = 1.0f - u;
+  const float series =
+      v * fmaf(v, fmaf(v, fmaf(v, fmaf(v, 0.2f, 0.25f), 1.0f / 3.0f), 0.5f), 1.0f);
+  const float hw = -0.69314718055994531f * __log2f(u);
+  return v < 0x1p-6f ? series : hw;
+}
+
+// Box-Muller (1958): radius sqrt(-2 ln u_a) from the first word, angle
+// 2 pi u_b from the second. The angle is taken as 2 pi (u_b - 1/2) in
+// (-pi, pi) (u_b - 1/2 is exact), which flips the sign of both sine and
+// cosine, so the hardware sine/cosine see a reduced argument.
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& z0, float& z1) {
-  const float r = sqrtf(-2.0f * logf(u01(wa)));
+  const float y = 2.0f * neg_log_u01(u01(wa));
+  const float r = y * rsqrtf(y);
   float s, c;
-  sincospif(2.0f * u01(wb), &s, &c);
-  z0 = r * c;
-  z1 = r * s;
+  __sincosf(6.28318530717958648f * (u01(wb) - 0.5f), &s, &c);
+  z0 = -r * c;
+  z1 = -r * s;
 }
 
 __device__ __forceinline__ float4 normals4(uint4 w) {
@@ -94,7 +111,7 @@ __device__ __forceinline__ long long fetch_trial(unsigned long long* cursor, boo
 }
 
 __device__ __forceinline__ float logistic(float gain, float bias, float s) {
-  return 1.0f / (1.0f + expf(-gain * (s + bias)));
+  return __fdividef(1.0f, 1.0f + __expf(-gain * (s + bias)));
 }
 
 }  // namespace dg

@@ -29,6 +29,7 @@ struct DdmParams {
   int32_t* step;
   float* xout;         // may be null
   unsigned long long* cursor;  // batched form: global trial cursor (zeroed per launch)
+  const unsigned int* perm;    // batched form: order in which trials are handed out (or null)
 };
 cudaError_t launch_ddm(const DdmParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
 int ddm_max_blocks_per_sm(int block);
@@ -47,6 +48,7 @@ struct LcaParams {
   int32_t* step;
   float* xout;         // [n][N], may be null
   unsigned long long* cursor;
+  const unsigned int* perm;    // batched form: hand-out order (or null)
 };
 cudaError_t launch_lca(const LcaParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
 bool lca_tpt_supported(int N, int tpt);
@@ -141,6 +143,23 @@ int grid_blocks(int mode, long long n_cand, int n_trials);
 
 cudaError_t launch_argmax(const double* v, long long n, TopTwo* partials, unsigned int* ticket,
                           void* result, cudaStream_t s);
+
+// ------------------------------------------- longest-expected-first order ---
+constexpr int kSchedBuckets = 1024;
+
+struct SchedParams {
+  int kind;                      // 0 DDM, 1 LCA
+  const float* a;                // DDM: A[n]; LCA: I[n][N]
+  const float* b;                // DDM: z[n]
+  int N;
+  long long n;
+  float dt, sigma2, leak, threshold;
+  int max_steps;
+  unsigned int* hist;            // [kSchedBuckets] scratch
+  unsigned int* cursor;          // [kSchedBuckets] scratch
+  unsigned int* perm;            // [n] output
+};
+cudaError_t launch_sched(const SchedParams& s, cudaStream_t st);
 
 // ------------------------------------------------------------ RNG replay ---
 cudaError_t launch_philox_words(uint64_t seed, uint32_t trial, uint32_t cand, uint32_t purpose,

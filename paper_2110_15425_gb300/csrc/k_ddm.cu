@@ -28,11 +28,11 @@ __device__ __forceinline__ void ddm_begin(const DdmParams& p, long long t, DdmLa
   s.c = 0.0f;
 }
 
-// Up to four steps k .. k+3 of one trial from one Philox block. Returns the
-// 1-based sub-step at which the trial crossed a bound, or 0.
-__device__ __forceinline__ int ddm_four_steps(const DdmParams& p, uint32_t trial, int k,
+// Up to four steps k .. k+3 of one trial with the four normals of its Philox
+// block k / 4. Returns the 1-based sub-step at which the trial crossed a
+// bound, or 0.
+__device__ __forceinline__ int ddm_four_steps(const DdmParams& p, const float4& e, int k,
                                               DdmLane& s) {
-  const float4 e = normals4(noise_block(p.k0, p.k1, trial, 0u, (uint32_t)(k >> 2)));
   const float ev[4] = {e.x, e.y, e.z, e.w};
   int hit = 0;
 #pragma unroll
@@ -45,6 +45,10 @@ __device__ __forceinline__ int ddm_four_steps(const DdmParams& p, uint32_t trial
   return hit;
 }
 
+__device__ __forceinline__ float4 ddm_noise(const DdmParams& p, long long t, int k) {
+  return normals4(noise_block(p.k0, p.k1, p.trial0 + (uint32_t)t, 0u, (uint32_t)(k >> 2)));
+}
+
 __device__ __forceinline__ void ddm_write(const DdmParams& p, long long t, int hit, int k,
                                           const DdmLane& s) {
   const float xs = s.x + s.c;
@@ -53,29 +57,46 @@ __device__ __forceinline__ void ddm_write(const DdmParams& p, long long t, int h
   if (p.xout) p.xout[t] = xs;
 }
 
+// Next trial of this lane: f is the value fetched from the cursor.
+__device__ __forceinline__ long long ddm_trial(const DdmParams& p, long long f) {
+  return p.perm ? (long long)__ldg(p.perm + f) : f;
+}
+
 __global__ void __launch_bounds__(256) ddm_batched(DdmParams p) {
-  long long t = fetch_trial(p.cursor, true);
-  bool active = t >= 0 && t < p.n;
+  long long f = fetch_trial(p.cursor, true);
+  bool active = f >= 0 && f < p.n;
+  long long t = active ? ddm_trial(p, f) : 0;
   DdmLane s;
   int k = 0;
-  if (active) ddm_begin(p, t, s);
+  float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (active) {
+    ddm_begin(p, t, s);
+    e = ddm_noise(p, t, 0);
+  }
   while (__any_sync(kFull, active)) {
     bool finished = false;
     if (active) {
-      const int hit = ddm_four_steps(p, p.trial0 + (uint32_t)t, k, s);
+      // the next block's normals do not depend on the state, so they are
+      // computed alongside this block's four sequential updates
+      const float4 en = ddm_noise(p, t, k + 4);
+      const int hit = ddm_four_steps(p, e, k, s);
       if (hit || k + 4 >= p.max_steps) {
         ddm_write(p, t, hit, k, s);
         finished = true;
       } else {
         k += 4;
+        e = en;
       }
     }
-    const long long nt = fetch_trial(p.cursor, finished);
+    f = fetch_trial(p.cursor, finished);
     if (finished) {
-      t = nt;
-      active = t < p.n;
+      active = f < p.n;
       k = 0;
-      if (active) ddm_begin(p, t, s);
+      if (active) {
+        t = ddm_trial(p, f);
+        ddm_begin(p, t, s);
+        e = ddm_noise(p, t, 0);
+      }
     }
   }
 }
@@ -86,7 +107,7 @@ __global__ void __launch_bounds__(256) ddm_plain(DdmParams p) {
   DdmLane s;
   ddm_begin(p, t, s);
   for (int k = 0;; k += 4) {
-    const int hit = ddm_four_steps(p, p.trial0 + (uint32_t)t, k, s);
+    const int hit = ddm_four_steps(p, ddm_noise(p, t, k), k, s);
     if (hit || k + 4 >= p.max_steps) {
       ddm_write(p, t, hit, k, s);
       return;

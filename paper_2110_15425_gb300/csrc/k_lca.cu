@@ -157,9 +157,10 @@ __global__ void __launch_bounds__(256) lca_batched(LcaParams p) {
   const int root = lane - g;
   const unsigned gmask = (TPT == 32 ? kFull : ((1u << TPT) - 1u)) << root;
   float x[L::NU], I[L::NU];
-  long long t = fetch_trial(p.cursor, g == 0);
-  t = __shfl_sync(kFull, t, root);
-  bool active = t >= 0 && t < p.n;
+  long long f = fetch_trial(p.cursor, g == 0);
+  f = __shfl_sync(kFull, f, root);
+  bool active = f >= 0 && f < p.n;
+  long long t = active ? (p.perm ? (long long)__ldg(p.perm + f) : f) : 0;
   int k = 0;
   if (active) L::load(p, t, g, x, I);
   while (__any_sync(kFull, active)) {
@@ -173,13 +174,15 @@ __global__ void __launch_bounds__(256) lca_batched(LcaParams p) {
         finished = true;
       }
     }
-    long long nt = fetch_trial(p.cursor, finished && g == 0);
-    nt = __shfl_sync(kFull, nt, root);
+    f = fetch_trial(p.cursor, finished && g == 0);
+    f = __shfl_sync(kFull, f, root);
     if (finished) {
-      t = nt;
-      active = t < p.n;
+      active = f < p.n;
       k = 0;
-      if (active) L::load(p, t, g, x, I);
+      if (active) {
+        t = p.perm ? (long long)__ldg(p.perm + f) : f;
+        L::load(p, t, g, x, I);
+      }
     }
   }
 }

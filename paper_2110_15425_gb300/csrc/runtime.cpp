@@ -55,19 +55,26 @@ double now_s() {
 
 enum ModelKind { K_DDM = 0, K_LCA = 1, K_NET = 2, K_WIDE = 3, K_PP = 4 };
 
-// Per-stream scratch: trial cursor, argmax ticket, per-block argmax partials,
-// device status word, and a growable FP64 buffer for the plain grid search.
+// Per-stream scratch: trial cursor, argmax ticket, device status word, the
+// histogram and bucket cursors of the trial-order sort, per-block argmax
+// partials; plus growable buffers for the trial order and for the plain grid
+// search's means.
 constexpr size_t kMaxPartials = dg::kMaxGridBlocks;
-constexpr size_t kScratchHead = 256;
+constexpr size_t kSortOff = 256;
+constexpr size_t kScratchHead = kSortOff + 2 * dg::kSchedBuckets * sizeof(unsigned int) + 256;
 constexpr size_t kScratchBytes = kScratchHead + kMaxPartials * sizeof(dg::TopTwo);
 
 struct Scratch {
   unsigned char* base = nullptr;
   double* means = nullptr;
   size_t means_cap = 0;
+  unsigned int* perm = nullptr;
+  size_t perm_cap = 0;
   unsigned long long* cursor() { return reinterpret_cast<unsigned long long*>(base); }
   unsigned int* ticket() { return reinterpret_cast<unsigned int*>(base + 8); }
   int* status() { return reinterpret_cast<int*>(base + 16); }
+  unsigned int* hist() { return reinterpret_cast<unsigned int*>(base + kSortOff); }
+  unsigned int* bucket_cursor() { return hist() + dg::kSchedBuckets; }
   dg::TopTwo* partials() { return reinterpret_cast<dg::TopTwo*>(base + kScratchHead); }
 };
 
@@ -92,7 +99,7 @@ struct dg_model {
   int kind = 0;
   int max_steps = 1;
   // DDM
-  float dt = 0.f, diffusion = 0.f, x0 = 0.f;
+  float dt = 0.f, diffusion = 0.f, x0 = 0.f, sigma = 0.f;
   // LCA
   int N = 0;
   float leak = 0.f, inhibition = 0.f, threshold = 0.f;
@@ -152,6 +159,29 @@ dg_status scratch_means(dg_ctx* ctx, Scratch* sc, size_t n, cudaStream_t s) {
 bool capturing(cudaStream_t s) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+dg_status scratch_perm(dg_ctx* ctx, Scratch* sc, size_t n, cudaStream_t s) {
+  if (sc->perm_cap >= n) return DG_OK;
+  if (capturing(s))
+    return fail(DG_E_STATE, "trial-order buffer must grow; run this size once before capture");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  DG_CUDA(cudaStreamSynchronize(s));
+  if (sc->perm) cudaFree(sc->perm);
+  sc->perm = nullptr;
+  DG_CUDA(cudaMalloc(&sc->perm, n * sizeof(unsigned int)));
+  sc->perm_cap = n;
+  return DG_OK;
+}
+
+// Longest-expected-first hand-out order (DG_LPT=0 turns it off). Small jobs
+// skip it: their launch is not long enough for the order to matter.
+bool lpt_enabled(long long n) {
+  static const int on = [] {
+    const char* e = getenv("DG_LPT");
+    return e ? atoi(e) : 1;
+  }();
+  return on && n >= 4096;
 }
 
 // Set on the serving thread: never time launch shapes there (tuning
@@ -264,16 +294,19 @@ dg_status run_tuned(dg_ctx* ctx, const std::string& key, const std::vector<dg::L
   return ran ? DG_OK : go(c);
 }
 
+// Launch shapes: fewer resident trials per SM make each trial advance
+// faster (the longest trials set a persistent launch's end) at the price of
+// less latency hiding; the tuner measures where the balance lies.
 std::vector<dg::LaunchCfg> ddm_candidates() {
   std::vector<dg::LaunchCfg> v;
-  for (int block : {256, 128}) {
-    const int occ = dg::ddm_max_blocks_per_sm(block);
-    for (int div : {1, 2}) {
-      dg::LaunchCfg c;
-      c.block = block;
-      c.grid = dg::num_sms() * std::max(1, occ / div);
-      v.push_back(c);
-    }
+  const int occ = dg::ddm_max_blocks_per_sm(256);
+  for (int per_sm : {occ, 6, 5, 4, 3, 2}) {
+    if (per_sm > occ || per_sm < 1) continue;
+    if (!v.empty() && per_sm == occ) continue;
+    dg::LaunchCfg c;
+    c.block = 256;
+    c.grid = dg::num_sms() * per_sm;
+    v.push_back(c);
   }
   return v;
 }
@@ -290,11 +323,13 @@ std::vector<dg::LaunchCfg> lca_candidates(int N) {
   const int only = forced_tpt();
   for (int tpt : {1, 2, 4}) {
     if (!dg::lca_tpt_supported(N, tpt) || (only && tpt != only)) continue;
-    for (int block : {256, 128}) {
+    const int occ = std::max(1, dg::lca_max_blocks_per_sm(N, tpt, 256));
+    for (int div : {1, 2, 4}) {
+      if (div > 1 && occ / div < 1) continue;
       dg::LaunchCfg c;
-      c.block = block;
+      c.block = 256;
       c.tpt = tpt;
-      c.grid = dg::num_sms() * std::max(1, dg::lca_max_blocks_per_sm(N, tpt, block));
+      c.grid = dg::num_sms() * std::max(1, occ / div);
       v.push_back(c);
     }
   }
@@ -353,6 +388,22 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
       return DG_OK;
     };
     if (mode == DG_MODE_PLAIN) return go(dg::LaunchCfg{});
+    if (lpt_enabled(d->n_trials)) {
+      if ((st = scratch_perm(m->ctx, sc, (size_t)d->n_trials, s)) != DG_OK) return st;
+      dg::SchedParams sp{};
+      sp.kind = 0;
+      sp.a = p.A;
+      sp.b = p.z;
+      sp.n = p.n;
+      sp.dt = m->dt;
+      sp.sigma2 = m->sigma * m->sigma;
+      sp.max_steps = m->max_steps;
+      sp.hist = sc->hist();
+      sp.cursor = sc->bucket_cursor();
+      sp.perm = sc->perm;
+      DG_CUDA(dg::launch_sched(sp, s));
+      p.perm = sc->perm;
+    }
     return run_tuned(m->ctx, "ddm/" + bucket, ddm_candidates(), s, go);
   }
   if (m->kind == K_LCA) {
@@ -381,6 +432,23 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
       return DG_OK;
     };
     if (mode == DG_MODE_PLAIN) return go(dg::LaunchCfg{});
+    if (lpt_enabled(d->n_trials) && !m->two_sided) {
+      if ((st = scratch_perm(m->ctx, sc, (size_t)d->n_trials, s)) != DG_OK) return st;
+      dg::SchedParams sp{};
+      sp.kind = 1;
+      sp.a = p.I;
+      sp.N = m->N;
+      sp.n = p.n;
+      sp.dt = m->dt;
+      sp.leak = m->leak;
+      sp.threshold = m->threshold;
+      sp.max_steps = m->max_steps;
+      sp.hist = sc->hist();
+      sp.cursor = sc->bucket_cursor();
+      sp.perm = sc->perm;
+      DG_CUDA(dg::launch_sched(sp, s));
+      p.perm = sc->perm;
+    }
     auto cands = lca_candidates(m->N);
     if (cands.empty()) return fail(DG_E_UNSUPPORTED, "dg_run: no LCA layout for N=%d", m->N);
     return run_tuned(m->ctx,
@@ -1027,6 +1095,7 @@ dg_status dg_destroy(dg_ctx* ctx) {
   for (auto& kv : ctx->scratch) {
     cudaFree(kv.second.base);
     if (kv.second.means) cudaFree(kv.second.means);
+    if (kv.second.perm) cudaFree(kv.second.perm);
   }
   delete ctx;
   return DG_OK;
@@ -1072,6 +1141,7 @@ dg_status dg_compose(dg_ctx* ctx, const dg_mechanism* mechs, int32_t n_mech,
     if (!(g.dt > 0.0) || !(g.noise >= 0.0))
       return fail(DG_E_ARG, "dg_compose: integrator needs dt > 0 and noise >= 0");
     m->dt = (float)g.dt;
+    m->sigma = (float)g.noise;
     m->diffusion = (float)(g.noise * std::sqrt(g.dt));
     m->max_steps = stop->max_steps;
     if (g.kind == DG_DDM) {

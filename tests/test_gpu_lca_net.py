@@ -52,6 +52,18 @@ def test_lca_parity(ctx, orc, threads, monkeypatch, N, tpt):
         assert np.all(x >= 0)
 
 
+def test_lca_batched_equals_plain_bitwise(ctx):
+    """The batched form hands trials out longest-expected-first and splits a
+    trial over several lanes; neither changes any result bit."""
+    from paper_2110_15425_gb300 import workloads as W
+    for N in (4, 8, 16):
+        w = W.lca(n_trials=30000, N=N)
+        a = _lca(ctx, w["I"], w["seed"], 0)
+        b = _lca(ctx, w["I"], w["seed"], 1)
+        for u, v in zip(a, b):
+            assert np.array_equal(u, v), N
+
+
 def test_lca_ddm_mapping(ctx, orc, threads):
     """Sec. 4.4: LCA(N=1, leak 0, no competition, unit noise, two-sided, no
     rectification) decides like the DDM on the same draws."""
