@@ -214,6 +214,14 @@ dg_status dg_grid_search(dg_model* model, const dg_grid_desc* desc, dg_grid_resu
 dg_status dg_argmax_f64(dg_ctx* ctx, const double* values, int64_t n, dg_grid_result* result,
                         void* stream);
 
+/* Device-side status of the work enqueued on `stream` through this context:
+   waits for the stream, then reports and clears the status word that kernels
+   set when one of their bounded waits (the tensor-core kernel's mbarrier
+   waits, about one second each) gives up instead of hanging. Returns DG_OK, or
+   DG_E_TIMEOUT when a wait expired (the affected trials' outputs are not
+   written), or DG_E_CUDA. */
+dg_status dg_stream_status(dg_ctx* ctx, void* stream);
+
 /* Allocation-free dg_grid_search. The paper has no counterpart: this entry
    point exists for callers that may not allocate device memory themselves or
    let a library do it behind their back - code that runs while someone else's

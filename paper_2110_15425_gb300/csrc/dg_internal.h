@@ -95,10 +95,10 @@ cudaError_t launch_net(const NetParams& p, int mode, const LaunchCfg& cfg, cudaS
 
 // --------------------------------------------------- wide network (tensor cores) ---
 struct WideParams {
-  const float* w_stim;           // [H][S] FP32
-  const float* w_task;           // [H][T] FP32
-  const uint16_t* w_resp_bf16;   // [R][H] bfloat16 bits (K-major rows for the MMA B operand)
-  const float* w_resp_f32;       // [R][H] FP32 copy of the same bf16 values (plain kernel)
+  const float* w_in;             // [H][S + T] FP32: stimulus and task weights side by side
+  const uint16_t* w_resp_bf16;   // shared-memory image of the MMA B operand: [16][2H]
+                                 // bfloat16 (W | W) in the K-major canonical layout
+  const float* w_resp_f32;       // [16][H] FP32 copy of the same bf16 values (plain kernel)
   const float* cond;             // [n_cond][S + T] one-hot rows
   int n_cond, cond_block;
   int S, T, H, R;
@@ -114,6 +114,8 @@ struct WideParams {
   int* status;                   // device status word (bounded mbarrier waits)
 };
 cudaError_t launch_wide(const WideParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
+size_t wide_smem_bytes(int H, int nin, bool tc);
+void wide_b_image(const uint16_t* w_bf16, int H, uint16_t* img);
 
 // ------------------------------------------------------- predator-prey grid ---
 struct TopTwo {                  // running argmax with lowest-index ties

@@ -1,14 +1,538 @@
-// Wide multitask network (stimulus + task one-hot -> hidden -> response).
+// Wide multitask network (the PyTorch network of the Multitasking model,
+// Sec. 5): stimulus and task inputs (clamped) -> hidden (H logistic units,
+// H = 64..256) -> response (16 logistic units), every unit time-averaging,
+//   s <- (1 - rate) s + rate net + noise eps,  y = 1 / (1 + exp(-gain (s + bias))),
+// synchronous update (Sec. 3.3), stop when the largest response exceeds the
+// second largest by more than the threshold, or at max_steps.
+// Noise of unit u (hidden 0..H-1, then response H..H+15) at step j is normal
+// (j-1)(H+16) + u of the trial's stream.
+//
+// A CTA holds 128 trials (one M = 128 MMA tile) with four threads per trial:
+// thread (row r, quarter q) keeps the integrator state of hidden units
+// [q H/4, (q+1) H/4) of trial r in registers. The hidden net input is constant
+// per trial (inputs are clamped); it is computed once per trial and kept in
+// tensor memory (TMEM lane r). Per step:
+//   1. every thread integrates its hidden units (reading y(t-1) first) and
+//      writes y(t-1) into a shared-memory A tile as a bfloat16 hi + lo pair
+//      (y = hi + lo to about 2^-17), K-major canonical layout;
+//   2. one thread issues tcgen05.mma (kind::f16, M128 N16, K16 at a time) over
+//      K = 2H: D[r][n] = sum_h (hi + lo)[r][h] W[n][h], accumulated in FP32 in
+//      TMEM; the BF16 response weights (B operand) were staged into shared
+//      memory once per CTA by a bulk (TMA) copy;
+//   3. the quarter-0 threads read their row of D back (tcgen05.ld), integrate
+//      the 16 response units and apply the stop rule; finished trials are
+//      replaced from the global trial cursor.
+// Every wait on an mbarrier is bounded by a clock limit; on expiry the kernel
+// records the failure in a status word and leaves.
+//
+// TC = false is the CUDA-core comparison form: the same CTA layout, with the
+// response net input summed from per-quarter partial dot products in shared
+// memory instead of the tensor-core GEMM.
+#include <cuda_bf16.h>
+
 #include "dg_device.cuh"
 #include "dg_internal.h"
 
 namespace dg {
 
+namespace {
+
+constexpr int kRows = 128;        // trials per CTA
+constexpr int kThreads = 512;     // four threads per trial
+constexpr int kR = 16;            // response units
+constexpr long long kWaitCycles = 2000000000ll;  // about one second
+
+// ---------------------------------------------------------------- PTX ---
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of the barrier, giving up after about a second.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// 1-D bulk copy global -> shared (TMA engine), completion counted on `bar`.
+// Both addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+// 32 lanes x 16 consecutive 32-bit columns, one lane per thread of the warp.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of 8
+// rows x 16 bytes stored contiguously (128 bytes); `lbo` = byte distance
+// between core matrices adjacent along K, `sbo` = between 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of this architecture
+  return d;                // base offset 0, no swizzle
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N and M encoded as N/8 and M/16.
+__host__ __device__ constexpr uint32_t mma_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// ------------------------------------------------------------- layout ---
+
+// Byte offset of the 8-element K run starting at kk (multiple of 8) in row
+// `row` of a K-major canonical tile with `kdim` columns.
+__host__ __device__ __forceinline__ uint32_t kmajor_off(int row, int kk, int kdim) {
+  return (uint32_t)(((row >> 3) * (kdim >> 3) + (kk >> 3)) * 128 + (row & 7) * 16);
+}
+
+template <int H, bool TC>
+struct Lay {
+  static constexpr int HQ = H / 4;      // hidden units per thread
+  static constexpr int K2 = 2 * H;      // hi and lo halves along K
+  static constexpr int U = H + kR;      // noisy units
+  // TC: B tile (BF16 [16][K2]) + A tile (BF16 [128][K2]); plain: FP32 W [16][H] +
+  // partial sums [4][16][128] + hidden net [H][128]
+  static constexpr uint32_t B_OFF = 0;
+  static constexpr uint32_t B_BYTES = TC ? kR * K2 * 2 : kR * H * 4;
+  static constexpr uint32_t A_OFF = (B_BYTES + 1023) / 1024 * 1024;
+  static constexpr uint32_t A_BYTES = TC ? kRows * K2 * 2 : (4 * kR * kRows + H * kRows) * 4;
+  static constexpr uint32_t WIN_OFF = A_OFF + A_BYTES;
+};
+
+struct WideShared {
+  uint64_t bar_load;
+  uint64_t bar_mma;
+  uint32_t tmem_base;
+  int fail;
+  long long slot[kRows];
+};
+
+__device__ __forceinline__ uint32_t bf16_bits(float f) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f));
+}
+
+// y = hi + lo with hi = bf16(y), lo = bf16(y - hi); packs two values per word.
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+  const __nv_bfloat16 la = __float2bfloat16_rn(a - __bfloat162float(ha));
+  const __nv_bfloat16 lb = __float2bfloat16_rn(b - __bfloat162float(hb));
+  hi = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+  lo = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
+}
+
+template <int H, bool TC>
+__global__ void __launch_bounds__(kThreads, 1) wide_kernel(WideParams p) {
+  using L = Lay<H, TC>;
+  constexpr int HQ = L::HQ, NCH = HQ / 16;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ WideShared sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q = warp >> 2;                   // quarter of the hidden units
+  const int r = ((warp & 3) << 5) | lane;    // trial row = TMEM lane
+  const int nin = p.S + p.T;
+  float* w_in = reinterpret_cast<float*>(smem + L::WIN_OFF);   // [H][nin]
+
+  // ---- set-up: TMEM, barriers, weights staged by bulk copies
+  if (TC && warp == 0) {
+    tmem_alloc(&sh.tmem_base, 512);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&sh.bar_load, 1);
+    mbar_init(&sh.bar_mma, 1);
+    fence_mbar_init();
+    sh.fail = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid == 0) {
+    const uint32_t wb = L::B_BYTES, ib = (uint32_t)(H * nin * 4);
+    mbar_expect_tx(&sh.bar_load, wb + ib);
+    bulk_g2s(smem + L::B_OFF, TC ? (const void*)p.w_resp_bf16 : (const void*)p.w_resp_f32, wb,
+             &sh.bar_load);
+    bulk_g2s(w_in, p.w_in, ib, &sh.bar_load);
+  }
+  if (!mbar_wait(&sh.bar_load, 0)) {
+    atomicExch(p.status, 1);
+    sh.fail = 1;
+  }
+  const uint32_t tmem = TC ? sh.tmem_base : 0u;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;   // this warp's TMEM lanes
+  const uint32_t tmem_d = tmem + 256u;                            // accumulator columns
+
+  // ---- first trials
+  if (q == 0) {
+    const long long f = fetch_trial(p.cursor, true);
+    sh.slot[r] = (f >= 0 && f < p.n) ? f : -1;
+  }
+  __syncthreads();
+
+  float s[HQ];
+  float sr[kR];
+  long long t = -1;
+  int k = 0;
+  uint32_t phase = 0;
+  const float keep = 1.0f - p.rate;
+  float* net_sm = reinterpret_cast<float*>(smem + L::A_OFF) + 4 * kR * kRows;  // plain: [H][128]
+  float* part = reinterpret_cast<float*>(smem + L::A_OFF);                      // plain: [4][16][128]
+
+  while (true) {
+    // ---- (re)start trials whose slot changed
+    const long long ns = sh.slot[r];
+    const bool fresh = ns != t;
+    t = ns;
+    if (fresh) {
+      k = 0;
+#pragma unroll
+      for (int i = 0; i < HQ; ++i) s[i] = 0.f;
+#pragma unroll
+      for (int i = 0; i < kR; ++i) sr[i] = 0.f;
+    }
+    const bool active = t >= 0;
+    if (__any_sync(kFull, fresh)) {
+      // hidden net input of the new trial, once: net_h = sum_q W_in[h][q] c[q]
+      const float* cin = p.cond;
+      if (active) {
+        const long long g = (long long)p.trial0 + t;
+        cin = p.cond + (size_t)((g / p.cond_block) % p.n_cond) * nin;
+      }
+#pragma unroll 1
+      for (int c = 0; c < NCH; ++c) {
+        float nv[16];
+        if (TC) tmem_ld16(tmem + lane_base + (uint32_t)(q * HQ + 16 * c), nv);
+        if (fresh && active) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float* w = w_in + (size_t)(q * HQ + 16 * c + i) * nin;
+            float acc = 0.f;
+            for (int j = 0; j < nin; ++j) acc = fmaf(w[j], __ldg(cin + j), acc);
+            nv[i] = acc;
+          }
+        }
+        if (TC) {
+          tmem_st16(tmem + lane_base + (uint32_t)(q * HQ + 16 * c), nv);
+        } else if (fresh && active) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) net_sm[(q * HQ + 16 * c + i) * kRows + r] = nv[i];
+        }
+      }
+    }
+    if (!__syncthreads_or(active ? 1 : 0) || sh.fail) break;
+
+    // ---- 1. hidden units: read y(t-1), integrate, publish y(t-1)
+    const uint32_t tg = p.trial0 + (uint32_t)(active ? t : 0);
+    const uint32_t blk0 = (uint32_t)k * (uint32_t)(L::U / 4) + (uint32_t)(q * (HQ / 4));
+    float acc[kR];
+#pragma unroll
+    for (int n = 0; n < kR; ++n) acc[n] = 0.f;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      float nv[16];
+      if (TC) {
+        tmem_ld16(tmem + lane_base + (uint32_t)(q * HQ + 16 * c), nv);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) nv[i] = net_sm[(q * HQ + 16 * c + i) * kRows + r];
+      }
+      float e[16];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float4 z = normals4(noise_block(p.k0, p.k1, tg, 0u, blk0 + (uint32_t)(4 * c + b)));
+        e[4 * b] = z.x;
+        e[4 * b + 1] = z.y;
+        e[4 * b + 2] = z.z;
+        e[4 * b + 3] = z.w;
+      }
+      float y[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        float& sv = s[16 * c + i];
+        y[i] = logistic(p.gain_h, p.bias_h, sv);
+        sv = fmaf(keep, sv, fmaf(p.rate, nv[i], p.noise * e[i]));
+      }
+      if (TC) {
+        unsigned char* A = smem + L::A_OFF;
+        const int kk = q * HQ + 16 * c;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          uint4 hi, lo;
+          split2(y[8 * half + 0], y[8 * half + 1], hi.x, lo.x);
+          split2(y[8 * half + 2], y[8 * half + 3], hi.y, lo.y);
+          split2(y[8 * half + 4], y[8 * half + 5], hi.z, lo.z);
+          split2(y[8 * half + 6], y[8 * half + 7], hi.w, lo.w);
+          *reinterpret_cast<uint4*>(A + kmajor_off(r, kk + 8 * half, L::K2)) = hi;
+          *reinterpret_cast<uint4*>(A + kmajor_off(r, H + kk + 8 * half, L::K2)) = lo;
+        }
+      } else {
+        const float* W = reinterpret_cast<const float*>(smem + L::B_OFF);   // [16][H]
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int h = q * HQ + 16 * c + i;
+#pragma unroll
+          for (int n = 0; n < kR; ++n) acc[n] = fmaf(W[n * H + h], y[i], acc[n]);
+        }
+      }
+    }
+    if (TC) {
+      fence_proxy_async();
+      tc_fence_before();
+    } else {
+#pragma unroll
+      for (int n = 0; n < kR; ++n) part[(q * kR + n) * kRows + r] = acc[n];
+    }
+    __syncthreads();
+
+    // ---- 2. response net input D = y(t-1) W^T on the tensor cores
+    if (TC && tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(smem + L::A_OFF), b0 = smem_u32(smem + L::B_OFF);
+      const uint32_t sbo = (uint32_t)(L::K2 / 8) * 128u;
+      constexpr uint32_t idesc = mma_idesc(kRows, kR);
+#pragma unroll 1
+      for (int kc = 0; kc < L::K2 / 16; ++kc) {
+        const uint32_t off = (uint32_t)kc * 256u;   // two core matrices along K
+        mma_bf16(tmem_d, smem_desc(a0 + off, 128u, sbo), smem_desc(b0 + off, 128u, sbo), idesc,
+                 kc > 0 ? 1u : 0u);
+      }
+      mma_commit(&sh.bar_mma);
+    }
+
+    // ---- 3. response units and the stop rule (quarter 0)
+    bool finished = false;
+    if (q == 0) {
+      float net[kR];
+      if (TC) {
+        if (!mbar_wait(&sh.bar_mma, phase)) {
+          atomicExch(p.status, 1);
+          sh.fail = 1;
+        }
+        tc_fence_after();
+        tmem_ld16(tmem_d + lane_base, net);
+      } else {
+#pragma unroll
+        for (int n = 0; n < kR; ++n)
+          net[n] = ((part[(0 * kR + n) * kRows + r] + part[(1 * kR + n) * kRows + r]) +
+                    part[(2 * kR + n) * kRows + r]) + part[(3 * kR + n) * kRows + r];
+      }
+      if (active) {
+        const uint32_t rb = (uint32_t)k * (uint32_t)(L::U / 4) + (uint32_t)(H / 4);
+        float yr[kR];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const float4 z = normals4(noise_block(p.k0, p.k1, tg, 0u, rb + (uint32_t)b));
+          const float e4[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int n = 4 * b + j;
+            sr[n] = fmaf(keep, sr[n], fmaf(p.rate, net[n], p.noise * e4[j]));
+            yr[n] = logistic(p.gain_r, p.bias_r, sr[n]);
+          }
+        }
+        int best = 0;
+        float v1 = yr[0];
+#pragma unroll
+        for (int n = 1; n < kR; ++n)
+          if (yr[n] > v1) {
+            v1 = yr[n];
+            best = n;
+          }
+        float v2 = -INFINITY;
+#pragma unroll
+        for (int n = 0; n < kR; ++n)
+          if (n != best) v2 = fmaxf(v2, yr[n]);
+        const bool hit = v1 - v2 > p.stop_threshold;
+        if (hit || k + 1 >= p.max_steps) {
+          p.choice[t] = hit ? (int8_t)best : (int8_t)-1;
+          p.step[t] = hit ? k + 1 : p.max_steps;
+          if (p.yout)
+#pragma unroll
+            for (int n = 0; n < kR; ++n) p.yout[(size_t)t * kR + n] = yr[n];
+          finished = true;
+        }
+      }
+      if (TC) tc_fence_before();
+    }
+    phase ^= 1u;
+    __syncthreads();
+
+    // ---- refill finished rows from the trial cursor
+    if (q == 0) {
+      const long long f = fetch_trial(p.cursor, finished);
+      if (finished) sh.slot[r] = (f >= 0 && f < p.n) ? f : -1;
+    }
+    ++k;
+    __syncthreads();
+  }
+
+  // ---- tear-down
+  __syncthreads();
+  if (TC) {
+    if (sh.fail) {
+      // give an MMA that may still be in flight a bounded time to finish
+      if (tid == 0) mbar_wait(&sh.bar_mma, phase ^ 1u);
+      __syncthreads();
+    }
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+  }
+}
+
+template <int H, bool TC>
+cudaError_t launch_h(const WideParams& p, cudaStream_t s) {
+  using L = Lay<H, TC>;
+  size_t smem = L::WIN_OFF + (size_t)H * (p.S + p.T) * 4;
+  // more than half of an SM's shared memory, so that two CTAs never share an
+  // SM (each takes all 512 TMEM columns)
+  if (smem < 120 * 1024) smem = 120 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(wide_kernel<H, TC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  long long grid = (p.n + kRows - 1) / kRows;
+  const long long cap = (long long)num_sms();  // one CTA per SM (all of its TMEM)
+  if (grid > cap) grid = cap;
+  wide_kernel<H, TC><<<(unsigned)grid, kThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t wide_smem_bytes(int H, int nin, bool tc) {
+  const size_t b = tc ? (size_t)kR * 2 * H * 2 : (size_t)kR * H * 4;
+  const size_t a_off = (b + 1023) / 1024 * 1024;
+  const size_t a = tc ? (size_t)kRows * 2 * H * 2 : (size_t)(4 * kR * kRows + H * kRows) * 4;
+  return a_off + a + (size_t)H * nin * 4;
+}
+
+void wide_b_image(const uint16_t* w_bf16, int H, uint16_t* img) {
+  // B operand image: row n of K2 = 2H elements is [W[n][0..H) | W[n][0..H)],
+  // in the K-major canonical layout of the tensor-core tile
+  const int K2 = 2 * H;
+  for (int n = 0; n < kR; ++n)
+    for (int kk = 0; kk < K2; kk += 8) {
+      const uint32_t off = kmajor_off(n, kk, K2) / 2;
+      for (int j = 0; j < 8; ++j) img[off + j] = w_bf16[(size_t)n * H + ((kk + j) % H)];
+    }
+}
+
 cudaError_t launch_wide(const WideParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s) {
-  (void)p;
-  (void)mode;
   (void)cfg;
-  (void)s;
+  if (p.n <= 0) return cudaSuccess;
+  const bool tc = mode == 0;
+  switch (p.H) {
+    case 64: return tc ? launch_h<64, true>(p, s) : launch_h<64, false>(p, s);
+    case 128: return tc ? launch_h<128, true>(p, s) : launch_h<128, false>(p, s);
+    case 192: return tc ? launch_h<192, true>(p, s) : launch_h<192, false>(p, s);
+    case 256: return tc ? launch_h<256, true>(p, s) : launch_h<256, false>(p, s);
+  }
   return cudaErrorNotSupported;
 }
 

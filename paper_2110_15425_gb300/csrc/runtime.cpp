@@ -111,8 +111,7 @@ struct dg_model {
   // wide network
   int S = 0, T = 0, H = 0, R = 0;
   float bias_h = 0, bias_r = 0, gain_h = 1, gain_r = 1, rate = 0, noise = 0, stop_thr = 0;
-  float* d_w_stim = nullptr;
-  float* d_w_task = nullptr;
+  float* d_w_hid = nullptr;  // wide: [H][S + T]
   uint16_t* d_w_resp_bf16 = nullptr;
   float* d_w_resp_f32 = nullptr;
   // predator-prey
@@ -480,8 +479,7 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
   }
   if (m->kind == K_WIDE) {
     dg::WideParams p{};
-    p.w_stim = m->d_w_stim;
-    p.w_task = m->d_w_task;
+    p.w_in = m->d_w_hid;
     p.w_resp_bf16 = m->d_w_resp_bf16;
     p.w_resp_f32 = m->d_w_resp_f32;
     p.cond = d->cond_inputs;
@@ -508,7 +506,7 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
     p.yout = fs;
     p.cursor = sc->cursor();
     p.status = sc->status();
-    if (mode == DG_MODE_BATCHED) DG_CUDA(cudaMemsetAsync(sc->cursor(), 0, 8, s));
+    DG_CUDA(cudaMemsetAsync(sc->cursor(), 0, 8, s));
     cudaError_t e = dg::launch_wide(p, mode, dg::LaunchCfg{}, s);
     if (e == cudaErrorNotSupported)
       return fail(DG_E_UNSUPPORTED, "wide network kernel not available in this build");
@@ -943,8 +941,9 @@ dg_status compose_transfer(dg_model* m, const dg_mechanism* mechs, int n_mech,
       if (projs[p].sender == hid && projs[p].receiver == resp) pr = &projs[p];
     }
     const int H = hid >= 0 ? mechs[hid].size : 0;
+    const int nin = (in0 >= 0 ? mechs[in0].size : 0) + (in1 >= 0 ? mechs[in1].size : 0);
     if (ps && pt && pr && pr->dtype == DG_BF16 && H >= 64 && H <= 256 && H % 64 == 0 &&
-        mechs[resp].size == 16) {
+        mechs[resp].size == 16 && dg::wide_smem_bytes(H, nin, true) <= 227 * 1024) {
       m->kind = K_WIDE;
       m->S = mechs[in0].size;
       m->T = mechs[in1].size;
@@ -954,19 +953,26 @@ dg_status compose_transfer(dg_model* m, const dg_mechanism* mechs, int n_mech,
       m->gain_h = (float)mechs[hid].gain;
       m->bias_r = (float)mechs[resp].bias;
       m->gain_r = (float)mechs[resp].gain;
-      std::vector<float> ws(ps->weights, ps->weights + (size_t)H * m->S);
-      std::vector<float> wt(pt->weights, pt->weights + (size_t)H * m->T);
+      // hidden weights: row h = [stimulus weights | task weights]
+      const int S = m->S, T = m->T;
+      std::vector<float> win((size_t)H * (S + T));
+      for (int h = 0; h < H; ++h) {
+        for (int j = 0; j < S; ++j) win[(size_t)h * (S + T) + j] = ps->weights[(size_t)h * S + j];
+        for (int j = 0; j < T; ++j) win[(size_t)h * (S + T) + S + j] = pt->weights[(size_t)h * T + j];
+      }
       std::vector<uint16_t> wr(16 * (size_t)H);
       std::vector<float> wrf(16 * (size_t)H);
       for (size_t i = 0; i < wr.size(); ++i) {
         wr[i] = to_bf16(pr->weights[i]);
         wrf[i] = from_bf16(wr[i]);
       }
+      std::vector<uint16_t> img(16 * 2 * (size_t)H);
+      dg::wide_b_image(wr.data(), H, img.data());
       dg_status st;
-      if ((st = upload(&m->d_w_stim, ws)) != DG_OK) return st;
-      if ((st = upload(&m->d_w_task, wt)) != DG_OK) return st;
-      if ((st = upload(&m->d_w_resp_bf16, wr)) != DG_OK) return st;
+      if ((st = upload(&m->d_w_hid, win)) != DG_OK) return st;
+      if ((st = upload(&m->d_w_resp_bf16, img)) != DG_OK) return st;
       if ((st = upload(&m->d_w_resp_f32, wrf)) != DG_OK) return st;
+      m->n_inputs = S + T;
       return DG_OK;
     }
   }
@@ -1208,8 +1214,7 @@ dg_status dg_model_free(dg_model* m) {
   if (!m) return fail(DG_E_ARG, "dg_model_free: null model");
   cudaFree(m->d_layout);
   cudaFree(m->d_w_in);
-  cudaFree(m->d_w_stim);
-  cudaFree(m->d_w_task);
+  cudaFree(m->d_w_hid);
   cudaFree(m->d_w_resp_bf16);
   cudaFree(m->d_w_resp_f32);
   delete m;
@@ -1249,6 +1254,26 @@ dg_status dg_argmax_f64(dg_ctx* ctx, const double* values, int64_t n, dg_grid_re
   DG_CUDA(cudaMemsetAsync(sc->ticket(), 0, 4, s));
   DG_CUDA(dg::launch_argmax(values, n, sc->partials(), sc->ticket(), result, s));
   return DG_OK;
+}
+
+dg_status dg_stream_status(dg_ctx* ctx, void* stream) {
+  if (!ctx) return fail(DG_E_ARG, "dg_stream_status: null ctx");
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_CUDA(cudaSetDevice(ctx->device));
+  DG_CUDA(cudaStreamSynchronize(s));
+  Scratch* sc = nullptr;
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->scratch.find(s);
+    if (it == ctx->scratch.end()) return DG_OK;  // nothing ran on this stream
+    sc = &it->second;
+  }
+  int word = 0;
+  DG_CUDA(cudaMemcpy(&word, sc->status(), sizeof word, cudaMemcpyDeviceToHost));
+  if (word == 0) return DG_OK;
+  DG_CUDA(cudaMemset(sc->status(), 0, sizeof word));
+  return fail(DG_E_TIMEOUT, "a device-side wait gave up (status %d); affected outputs unwritten",
+              word);
 }
 
 dg_status dg_philox_words(uint64_t seed, uint32_t trial, uint32_t cand, uint32_t purpose,
