@@ -697,7 +697,10 @@ def served_mix(B, W, torch, ctx, step, n_jobs=48, seed=7):
         r = B.dg_wait(ctx, t, 600000)
         lat.append(r.t_done - r.t_submit)
         # keep[-1] is the job's host step array
-        total_steps += job.grid.n_levels[0] ** 3 * 64 if k == "grid" else int(keep[-1].sum())
+        js = job.grid.n_levels[0] ** 3 * 64 if k == "grid" else int(keep[-1].sum())
+        if os.environ.get("DG_BENCH_DEBUG"):
+            print("served job", k, n, js, r.status, file=sys.stderr)
+        total_steps += js
     wall = time.perf_counter() - t_start
     lat.sort()
     return {"jobs": n_jobs, "arrival_rate_per_s": rate, "wall_s": wall,
