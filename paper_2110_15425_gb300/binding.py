@@ -353,6 +353,8 @@ def run_desc(n_trials, seed, trial_params=None, cond_inputs=None, n_cond=0, cond
     d.seed = seed
     d.trial_params = None if trial_params is None else trial_params.data_ptr()
     d.cond_inputs = None if cond_inputs is None else cond_inputs.data_ptr()
+    # the struct holds raw addresses: keep the tensors alive as long as it lives
+    d._keep = (trial_params, cond_inputs)
     d.n_cond = n_cond
     d.cond_block = cond_block
     d.mode = mode
@@ -361,6 +363,7 @@ def run_desc(n_trials, seed, trial_params=None, cond_inputs=None, n_cond=0, cond
 
 def grid_desc(levels, positions, seed, mode=DG_MODE_BATCHED, cand_begin=0, cand_count=0):
     d = dg_grid_desc()
+    d._keep = (tuple(levels), positions)
     d.cand_begin = cand_begin
     d.cand_count = cand_count
     for i in range(3):

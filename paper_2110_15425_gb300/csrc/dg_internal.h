@@ -160,6 +160,7 @@ struct SchedParams {
   unsigned int* hist;            // [kSchedBuckets] scratch
   unsigned int* cursor;          // [kSchedBuckets] scratch
   unsigned int* perm;            // [n] output
+  unsigned short* bucket;        // [n] scratch: each trial's bucket
 };
 cudaError_t launch_sched(const SchedParams& s, cudaStream_t st);
 

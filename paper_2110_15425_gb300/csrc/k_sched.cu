@@ -15,6 +15,8 @@
 //        -ln(1 - k thr / I_max) / (k dt); never (max_steps) when I_max <= k thr.
 // Keys fall into kBuckets buckets; a three-kernel counting sort (histogram,
 // scan, scatter) writes the permutation. Order inside a bucket is arbitrary.
+// Each trial's bucket is computed once (by the histogram kernel) and stored,
+// so the scatter places exactly the trials the histogram counted.
 #include "dg_device.cuh"
 #include "dg_internal.h"
 
@@ -68,7 +70,11 @@ __global__ void __launch_bounds__(kSortBlock) sched_hist(SchedParams s) {
 #pragma unroll
   for (int j = 0; j < kPerThread; ++j) {
     const long long t = base + (long long)j * kSortBlock + threadIdx.x;
-    if (t < s.n) atomicAdd(&h[key_bucket(s, t)], 1u);
+    if (t < s.n) {
+      const int b = key_bucket(s, t);
+      s.bucket[t] = (unsigned short)b;
+      atomicAdd(&h[b], 1u);
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kSchedBuckets; i += blockDim.x)
@@ -103,7 +109,7 @@ __global__ void __launch_bounds__(kSortBlock) sched_scatter(SchedParams s) {
     const long long t = base + (long long)j * kSortBlock + threadIdx.x;
     bk[j] = -1;
     if (t < s.n) {
-      bk[j] = key_bucket(s, t);
+      bk[j] = s.bucket[t];
       rank[j] = atomicAdd(&h[bk[j]], 1u);
     }
   }
@@ -114,7 +120,10 @@ __global__ void __launch_bounds__(kSortBlock) sched_scatter(SchedParams s) {
 #pragma unroll
   for (int j = 0; j < kPerThread; ++j) {
     const long long t = base + (long long)j * kSortBlock + threadIdx.x;
-    if (bk[j] >= 0) s.perm[start[bk[j]] + rank[j]] = (unsigned int)t;
+    if (bk[j] >= 0) {
+      const unsigned int pos = start[bk[j]] + rank[j];
+      if (pos < (unsigned long long)s.n) s.perm[pos] = (unsigned int)t;
+    }
   }
 }
 

@@ -134,7 +134,9 @@ dg_status get_scratch(dg_ctx* ctx, cudaStream_t s, Scratch** out) {
                   "first use of a stream must not be inside stream capture (scratch allocation)");
     Scratch sc;
     DG_CUDA(cudaMalloc(&sc.base, kScratchBytes));
-    DG_CUDA(cudaMemset(sc.base, 0, kScratchBytes));
+    // zeroed on the stream itself: a plain cudaMemset runs on the legacy
+    // stream, which does not order against non-blocking streams
+    DG_CUDA(cudaMemsetAsync(sc.base, 0, kScratchBytes, s));
     it = ctx->scratch.emplace(s, sc).first;
   }
   *out = &it->second;
@@ -168,7 +170,8 @@ dg_status scratch_perm(dg_ctx* ctx, Scratch* sc, size_t n, cudaStream_t s) {
   DG_CUDA(cudaStreamSynchronize(s));
   if (sc->perm) cudaFree(sc->perm);
   sc->perm = nullptr;
-  DG_CUDA(cudaMalloc(&sc->perm, n * sizeof(unsigned int)));
+  // permutation (4 B per trial) followed by each trial's bucket (2 B per trial)
+  DG_CUDA(cudaMalloc(&sc->perm, n * (sizeof(unsigned int) + sizeof(unsigned short))));
   sc->perm_cap = n;
   return DG_OK;
 }
@@ -400,6 +403,7 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
       sp.hist = sc->hist();
       sp.cursor = sc->bucket_cursor();
       sp.perm = sc->perm;
+      sp.bucket = reinterpret_cast<unsigned short*>(sc->perm + sc->perm_cap);
       DG_CUDA(dg::launch_sched(sp, s));
       p.perm = sc->perm;
     }
@@ -445,6 +449,7 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
       sp.hist = sc->hist();
       sp.cursor = sc->bucket_cursor();
       sp.perm = sc->perm;
+      sp.bucket = reinterpret_cast<unsigned short*>(sc->perm + sc->perm_cap);
       DG_CUDA(dg::launch_sched(sp, s));
       p.perm = sc->perm;
     }
@@ -1206,6 +1211,9 @@ dg_status dg_compose(dg_ctx* ctx, const dg_mechanism* mechs, int32_t n_mech,
     dg_model_free(m.release());
     return st;
   }
+  // the weight copies (from pageable memory) must have landed before any
+  // stream, blocking or not, launches on this model
+  DG_CUDA(cudaDeviceSynchronize());
   *out = m.release();
   return DG_OK;
 }
@@ -1269,9 +1277,11 @@ dg_status dg_stream_status(dg_ctx* ctx, void* stream) {
     sc = &it->second;
   }
   int word = 0;
-  DG_CUDA(cudaMemcpy(&word, sc->status(), sizeof word, cudaMemcpyDeviceToHost));
+  DG_CUDA(cudaMemcpyAsync(&word, sc->status(), sizeof word, cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaStreamSynchronize(s));
   if (word == 0) return DG_OK;
-  DG_CUDA(cudaMemset(sc->status(), 0, sizeof word));
+  DG_CUDA(cudaMemsetAsync(sc->status(), 0, sizeof word, s));
+  DG_CUDA(cudaStreamSynchronize(s));
   return fail(DG_E_TIMEOUT, "a device-side wait gave up (status %d); affected outputs unwritten",
               word);
 }

@@ -248,3 +248,109 @@ def test_wait_timeout_status(ctx):
     assert e.value.status == B.DG_E_TIMEOUT
     B.dg_wait(ctx, t, 120000)
     B.dg_model_free(model)
+
+
+def test_trial_order_is_a_permutation_for_many_inputs(ctx):
+    """The longest-expected-first order must hand out every trial exactly
+    once for any inputs: batched (ordered) and plain (unordered) runs agree bit
+    for bit on many input sets and sizes, including keys on bucket edges."""
+    import torch
+    from paper_2110_15425_gb300 import binding as B
+    from paper_2110_15425_gb300 import workloads as W
+    ml = B.compose_lca(ctx, 8)
+    md = B.compose_ddm(ctx)
+    for i, n in enumerate([4096, 4097, 42018, 45761, 70001]):
+        l = W.lca(n_trials=n, N=8, input_seed=1000 + i)
+        d = W.ddm(n_trials=n, param_seed=2000 + i)
+        for model, params in ((ml, dev(l["I"])), (md, dev(np.concatenate([d["A"], d["z"]])))):
+            outs = []
+            for mode in (0, 1):
+                ch = torch.full((n,), 99, dtype=torch.int8, device="cuda")
+                st = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+                B.dg_run(model, B.run_desc(n, 5 + i, trial_params=params, mode=mode), ch, st)
+                outs.append((host(ch), host(st)))
+            assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+            assert outs[0][1].min() >= 1
+    B.dg_model_free(ml)
+    B.dg_model_free(md)
+
+
+def test_served_mix_of_every_kind_equals_direct_runs(ctx):
+    """Jobs of every model kind submitted together (overlapping on the
+    device) return exactly what a direct dg_run / dg_grid_search returns."""
+    import torch
+    from paper_2110_15425_gb300 import binding as B
+    from paper_2110_15425_gb300 import workloads as W
+    s = W.stroop_small(weight_seed=4)
+    wd = W.stroop_wide(n_trials=3000, max_steps=150)
+    models = dict(
+        ddm=B.compose_ddm(ctx), lca=B.compose_lca(ctx, 8), pp=B.compose_predator_prey(ctx),
+        stroop=B.compose_network(ctx, s["layers"], s["projections"], rate=s["rate"],
+                                 noise_sd=s["noise_sd"], stop_layer=5, stop_threshold=0.7,
+                                 max_steps=500),
+        wide=B.compose_network(ctx, wd["layers"], wd["projections"], rate=wd["rate"],
+                               noise_sd=wd["noise_sd"], stop_layer=3, stop_threshold=0.7,
+                               max_steps=150, bf16_edges=(2,)))
+    specs = []
+    for i, n in enumerate([20000, 45761, 3000, 60000, 8000, 1500]):
+        specs.append(("ddm", n, W.ddm(n_trials=n, param_seed=40 + i)))
+        specs.append(("lca", n, W.lca(n_trials=n, N=8, input_seed=60 + i)))
+    specs.append(("stroop", 4000, s))
+    specs.append(("wide", 3000, wd))
+    jobs = []
+    for k, n, w in specs:
+        j = B.dg_job()
+        j.model = models[k].value
+        if k == "ddm":
+            h = np.ascontiguousarray(np.concatenate([w["A"], w["z"]]))
+            j.run.trial_params = h.ctypes.data
+        elif k == "lca":
+            h = np.ascontiguousarray(w["I"])
+            j.run.trial_params = h.ctypes.data
+        else:
+            h = np.ascontiguousarray(w["cond_inputs"])
+            j.run.cond_inputs = h.ctypes.data
+            j.run.n_cond = h.shape[0]
+            j.run.cond_block = w["cond_block"]
+        j.run.n_trials = n
+        j.run.seed = 3
+        ch = np.zeros(n, np.int8)
+        st = np.full(n, -7, np.int32)
+        j.choice = ch.ctypes.data
+        j.step = st.ctypes.data
+        jobs.append((k, n, w, j, h, ch, st))
+    g = W.predator_prey(levels=12)
+    gj = B.dg_job()
+    gj.model = models["pp"].value
+    gj.is_grid = 1
+    pos = np.ascontiguousarray(g["pos"])
+    lvs = [np.ascontiguousarray(x) for x in g["levels"]]
+    gj.grid.positions = pos.ctypes.data
+    gj.grid.n_trials = 64
+    gj.grid.seed = g["seed"]
+    for i in range(3):
+        gj.grid.levels[i] = lvs[i].ctypes.data
+        gj.grid.n_levels[i] = 12
+    gres = np.zeros(3, np.float64)
+    gmeans = np.zeros(12 ** 3, np.float64)
+    gj.grid_result = gres.ctypes.data
+    gj.cand_means = gmeans.ctypes.data
+    tickets = [B.dg_submit(ctx, j[3]) for j in jobs] + [B.dg_submit(ctx, gj)]
+    for t in tickets:
+        B.dg_wait(ctx, t, 120000)
+    for k, n, w, j, h, ch, st in jobs:
+        d = B.run_desc(n, 3, trial_params=dev(h) if k in ("ddm", "lca") else None,
+                       cond_inputs=dev(h) if k in ("stroop", "wide") else None,
+                       n_cond=h.shape[0] if k in ("stroop", "wide") else 0,
+                       cond_block=w.get("cond_block", 1) if k in ("stroop", "wide") else 1)
+        c2 = torch.zeros(n, dtype=torch.int8, device="cuda")
+        s2 = torch.zeros(n, dtype=torch.int32, device="cuda")
+        B.dg_run(models[k], d, c2, s2)
+        assert np.array_equal(ch, host(c2)), (k, n)
+        assert np.array_equal(st, host(s2)), (k, n)
+    m2 = torch.zeros(12 ** 3, dtype=torch.float64, device="cuda")
+    r2 = torch.zeros(3, dtype=torch.float64, device="cuda")
+    B.dg_grid_search(models["pp"], B.grid_desc([dev(x) for x in lvs], dev(pos), g["seed"]), r2, m2)
+    assert np.array_equal(gmeans, host(m2)) and np.array_equal(gres, host(r2))
+    for m in models.values():
+        B.dg_model_free(m)
