@@ -52,10 +52,10 @@ __device__ __forceinline__ float u01(uint32_t w) {
 // v < 2^-6 five terms leave a relative truncation error below 2e-10.
 __device__ __forceinline__ float neg_log_u01(float u) {
   const float v = 1.0f - u;
-  const float series =
-      v * fmaf(v, fmaf(v, fmaf(v, fmaf(v, 0.2f, 0.25f), 1.0f / 3.0f), 0.5f), 1.0f);
-  const float hw = -0.69314718055994531f * __log2f(u);
-  return v < 0x1p-6f ? series : hw;
+  float r = -0.69314718055994531f * __log2f(u);
+  if (v < 0x1p-6f)  // taken for 1 draw in 64
+    r = v * fmaf(v, fmaf(v, fmaf(v, fmaf(v, 0.2f, 0.25f), 1.0f / 3.0f), 0.5f), 1.0f);
+  return r;
 }
 
 // Box-Muller (1958): radius sqrt(-2 ln u_a) from the first word, angle

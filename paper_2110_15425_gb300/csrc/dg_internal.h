@@ -57,24 +57,24 @@ int lca_max_blocks_per_sm(int N, int tpt, int block);
 // ---------------------------------------------------- small logistic network ---
 constexpr int kNetMaxUnits = 32;     // logistic units
 constexpr int kNetMaxInputs = 64;    // input units
-constexpr int kNetMaxEdges = 512;    // weighted edges between logistic units
+constexpr int kNetMaxInDegree = 32;  // incoming edges from logistic units, per unit
 
-// Static layout of a small network (Sec. 3.3): units numbered in mechanism
-// order; edges from logistic units listed as (dst, src, w); the input part of
-// each unit's net input is a dense [U][n_in] matrix applied once per trial.
+// Static layout of a small network (Sec. 3.3): logistic units numbered in
+// mechanism order; unit u's incoming edges from logistic units are the dense
+// row src[u][0..D), w[u][0..D) (in projection order, padded with weight 0);
+// the input part of each net input is a [U][n_in] matrix applied once per trial.
 struct NetLayout {
   int U;                         // logistic units
   int n_in;                      // input units
-  int n_edges;
+  int D;                         // incoming-edge row length
   int stop_off, stop_size;       // stop layer among logistic units
   float rate, noise;
   float stop_threshold;
   int max_steps;
   float gain[kNetMaxUnits];
   float bias[kNetMaxUnits];
-  int16_t edge_dst[kNetMaxEdges];
-  int16_t edge_src[kNetMaxEdges];
-  float edge_w[kNetMaxEdges];
+  float w[kNetMaxUnits][kNetMaxInDegree];
+  int8_t src[kNetMaxUnits][kNetMaxInDegree];
 };
 
 struct NetParams {

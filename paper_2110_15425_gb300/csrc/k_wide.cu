@@ -136,6 +136,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
@@ -213,19 +223,21 @@ struct WideShared {
   uint32_t tmem_base;
   int fail;
   long long slot[kRows];
+  float yr[kR][kRows];   // response outputs of the step, [unit][trial row]
 };
 
 __device__ __forceinline__ uint32_t bf16_bits(float f) {
   return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f));
 }
 
-// y = hi + lo with hi = bf16(y), lo = bf16(y - hi); packs two values per word.
+// y = hi + lo with hi = bf16(y), lo = bf16(y - hi); two values per word, one
+// paired conversion for each half.
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
-  const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-  const __nv_bfloat16 la = __float2bfloat16_rn(a - __bfloat162float(ha));
-  const __nv_bfloat16 lb = __float2bfloat16_rn(b - __bfloat162float(hb));
-  hi = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
-  lo = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 template <int H, bool TC>
@@ -277,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1) wide_kernel(WideParams p) {
   __syncthreads();
 
   float s[HQ];
-  float sr[kR];
+  float sr[4];        // response units 4q .. 4q+3 of this thread's trial
   long long t = -1;
   int k = 0;
   uint32_t phase = 0;
@@ -295,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, 1) wide_kernel(WideParams p) {
 #pragma unroll
       for (int i = 0; i < HQ; ++i) s[i] = 0.f;
 #pragma unroll
-      for (int i = 0; i < kR; ++i) sr[i] = 0.f;
+      for (int i = 0; i < 4; ++i) sr[i] = 0.f;
     }
     const bool active = t >= 0;
     if (__any_sync(kFull, fresh)) {
@@ -406,66 +418,65 @@ __global__ void __launch_bounds__(kThreads, 1) wide_kernel(WideParams p) {
       mma_commit(&sh.bar_mma);
     }
 
-    // ---- 3. response units and the stop rule (quarter 0)
-    bool finished = false;
-    if (q == 0) {
-      float net[kR];
+    // ---- 3. response units 4q .. 4q+3 of every trial (all quarters)
+    {
+      float net[4];
       if (TC) {
         if (!mbar_wait(&sh.bar_mma, phase)) {
           atomicExch(p.status, 1);
           sh.fail = 1;
         }
         tc_fence_after();
-        tmem_ld16(tmem_d + lane_base, net);
+        tmem_ld4(tmem_d + lane_base + (uint32_t)(4 * q), net);
+        tc_fence_before();
       } else {
 #pragma unroll
-        for (int n = 0; n < kR; ++n)
-          net[n] = ((part[(0 * kR + n) * kRows + r] + part[(1 * kR + n) * kRows + r]) +
+        for (int j = 0; j < 4; ++j) {
+          const int n = 4 * q + j;
+          net[j] = ((part[(0 * kR + n) * kRows + r] + part[(1 * kR + n) * kRows + r]) +
                     part[(2 * kR + n) * kRows + r]) + part[(3 * kR + n) * kRows + r];
-      }
-      if (active) {
-        const uint32_t rb = (uint32_t)k * (uint32_t)(L::U / 4) + (uint32_t)(H / 4);
-        float yr[kR];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const float4 z = normals4(noise_block(p.k0, p.k1, tg, 0u, rb + (uint32_t)b));
-          const float e4[4] = {z.x, z.y, z.z, z.w};
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int n = 4 * b + j;
-            sr[n] = fmaf(keep, sr[n], fmaf(p.rate, net[n], p.noise * e4[j]));
-            yr[n] = logistic(p.gain_r, p.bias_r, sr[n]);
-          }
         }
-        int best = 0;
-        float v1 = yr[0];
+      }
+      const float4 z = normals4(noise_block(
+          p.k0, p.k1, tg, 0u, (uint32_t)k * (uint32_t)(L::U / 4) + (uint32_t)(H / 4 + q)));
+      const float e4[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
-        for (int n = 1; n < kR; ++n)
-          if (yr[n] > v1) {
-            v1 = yr[n];
+      for (int j = 0; j < 4; ++j) {
+        sr[j] = fmaf(keep, sr[j], fmaf(p.rate, net[j], p.noise * e4[j]));
+        sh.yr[4 * q + j][r] = logistic(p.gain_r, p.bias_r, sr[j]);
+      }
+    }
+    phase ^= 1u;
+    __syncthreads();
+
+    // ---- stop rule on the 16 responses; refill finished rows (quarter 0)
+    if (q == 0) {
+      bool finished = false;
+      if (active) {
+        int best = 0;
+        float v1 = sh.yr[0][r];
+#pragma unroll
+        for (int n = 1; n < kR; ++n) {
+          const float v = sh.yr[n][r];
+          if (v > v1) {
+            v1 = v;
             best = n;
           }
+        }
         float v2 = -INFINITY;
 #pragma unroll
         for (int n = 0; n < kR; ++n)
-          if (n != best) v2 = fmaxf(v2, yr[n]);
+          if (n != best) v2 = fmaxf(v2, sh.yr[n][r]);
         const bool hit = v1 - v2 > p.stop_threshold;
         if (hit || k + 1 >= p.max_steps) {
           p.choice[t] = hit ? (int8_t)best : (int8_t)-1;
           p.step[t] = hit ? k + 1 : p.max_steps;
           if (p.yout)
 #pragma unroll
-            for (int n = 0; n < kR; ++n) p.yout[(size_t)t * kR + n] = yr[n];
+            for (int n = 0; n < kR; ++n) p.yout[(size_t)t * kR + n] = sh.yr[n][r];
           finished = true;
         }
       }
-      if (TC) tc_fence_before();
-    }
-    phase ^= 1u;
-    __syncthreads();
-
-    // ---- refill finished rows from the trial cursor
-    if (q == 0) {
       const long long f = fetch_trial(p.cursor, finished);
       if (finished) sh.slot[r] = (f >= 0 && f < p.n) ? f : -1;
     }

@@ -1006,7 +1006,7 @@ dg_status compose_transfer(dg_model* m, const dg_mechanism* mechs, int n_mech,
         L.bias[noff[i] + u] = (float)mechs[i].bias;
       }
   std::vector<float> w_in((size_t)U * std::max(1, n_in), 0.f);
-  int ne = 0;
+  std::vector<int> deg(U, 0);
   for (int p = 0; p < n_proj; ++p) {
     const auto& e = projs[p];
     const int rs = mechs[e.receiver].size, ss = mechs[e.sender].size;
@@ -1017,17 +1017,18 @@ dg_status compose_transfer(dg_model* m, const dg_mechanism* mechs, int n_mech,
         if (mechs[e.sender].kind == DG_INPUT) {
           w_in[(size_t)dst * n_in + ioff[e.sender] + j] += w;
         } else {
-          if (ne >= dg::kNetMaxEdges)
-            return fail(DG_E_UNSUPPORTED, "compose: more than %d edges between logistic units",
-                        dg::kNetMaxEdges);
-          L.edge_dst[ne] = (int16_t)dst;
-          L.edge_src[ne] = (int16_t)(noff[e.sender] + j);
-          L.edge_w[ne] = w;
-          ++ne;
+          if (deg[dst] >= dg::kNetMaxInDegree)
+            return fail(DG_E_UNSUPPORTED,
+                        "compose: a unit receives more than %d edges from logistic units",
+                        dg::kNetMaxInDegree);
+          L.src[dst][deg[dst]] = (int8_t)(noff[e.sender] + j);
+          L.w[dst][deg[dst]] = w;
+          ++deg[dst];
         }
       }
   }
-  L.n_edges = ne;
+  L.D = 0;
+  for (int u = 0; u < U; ++u) L.D = std::max(L.D, deg[u]);
   dg_status st;
   if ((st = upload(&m->d_w_in, w_in)) != DG_OK) return st;
   DG_CUDA(cudaMalloc(&m->d_layout, sizeof(dg::NetLayout)));
