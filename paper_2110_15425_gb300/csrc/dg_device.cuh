@@ -45,16 +45,20 @@ __device__ __forceinline__ float u01(uint32_t w) {
   return fmaf(__uint2float_rn(w >> 9), 0x1p-23f, 0x1p-24f);
 }
 
-// -ln(u) for u in (0, 1). The hardware log2 approximation has a small
+// The 23 payload bits of w as the binary32 value 1 + (w >> 9) 2^-23 in [1, 2);
+// u = that - (1 - 2^-24) equals ((w >> 9) + 1/2) 2^-23 exactly.
+__device__ __forceinline__ float one_plus(uint32_t w) { return __uint_as_float((w >> 9) | 0x3F800000u); }
+
+// -2 ln(u) for u in (0, 1). The hardware log2 approximation has a small
 // absolute error, which is a large relative error when u is close to 1 and
-// ln(u) is tiny; there the Taylor series of -ln(1 - v) = v + v^2/2 + v^3/3 +
-// ... in v = 1 - u (exact in binary32 for u >= 1/2) is used instead: for
+// ln(u) is tiny; there the Taylor series -2 ln(1 - v) = 2 (v + v^2/2 + v^3/3
+// + ...) in v = 1 - u (exact in binary32 for u >= 1/2) is used instead: for
 // v < 2^-6 five terms leave a relative truncation error below 2e-10.
-__device__ __forceinline__ float neg_log_u01(float u) {
+__device__ __forceinline__ float neg2_log_u01(float u) {
   const float v = 1.0f - u;
-  float r = -0.69314718055994531f * __log2f(u);
+  float r = -1.38629436111989062f * __log2f(u);   // -2 ln 2
   if (v < 0x1p-6f)  // taken for 1 draw in 64
-    r = v * fmaf(v, fmaf(v, fmaf(v, fmaf(v, 0.2f, 0.25f), 1.0f / 3.0f), 0.5f), 1.0f);
+    r = v * fmaf(v, fmaf(v, fmaf(v, fmaf(v, 0.4f, 0.5f), 2.0f / 3.0f), 1.0f), 2.0f);
   return r;
 }
 
@@ -63,10 +67,14 @@ __device__ __forceinline__ float neg_log_u01(float u) {
 // (-pi, pi) (u_b - 1/2 is exact), which flips the sign of both sine and
 // cosine, so the hardware sine/cosine see a reduced argument.
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& z0, float& z1) {
-  const float y = 2.0f * neg_log_u01(u01(wa));
+  const float y = neg2_log_u01(one_plus(wa) - 0.99999994039535522f);   // 1 - 2^-24
   const float r = y * rsqrtf(y);
   float s, c;
-  __sincosf(6.28318530717958648f * (u01(wb) - 0.5f), &s, &c);
+  // u_b - 1/2 = (one_plus(w_b) - 3/2) + 2^-24, both steps exact; the fma
+  // rounds 2 pi (u_b - 1/2) once, as a plain product of the exact difference
+  // would (2 pi 2^-24 is exact)
+  __sincosf(fmaf(6.28318530717958648f, one_plus(wb) - 1.5f, 6.28318530717958648f * 0x1p-24f), &s,
+            &c);
   z0 = -r * c;
   z1 = -r * s;
 }
