@@ -118,8 +118,20 @@ __device__ __forceinline__ long long fetch_trial(unsigned long long* cursor, boo
   return (long long)(base + (unsigned long long)__popc(mask & ((1u << lane) - 1u)));
 }
 
-__device__ __forceinline__ float logistic(float gain, float bias, float s) {
-  return __fdividef(1.0f, 1.0f + __expf(-gain * (s + bias)));
-}
+// y = 1 / (1 + exp(-gain (s + bias))) = 1 / (1 + 2^(c1 s + c0)) with
+// c1 = -gain log2(e), c0 = -gain bias log2(e): one fma, the hardware 2^x and
+// reciprocal approximations.
+struct Logistic {
+  float c1, c0;
+  __device__ __forceinline__ static Logistic of(float gain, float bias) {
+    const float l2e = 1.44269504088896341f;
+    return Logistic{-gain * l2e, -(gain * bias) * l2e};
+  }
+  __device__ __forceinline__ float operator()(float s) const {
+    float e;
+    asm("ex2.approx.f32 %0, %1;" : "=f"(e) : "f"(fmaf(s, c1, c0)));
+    return __fdividef(1.0f, 1.0f + e);
+  }
+};
 
 }  // namespace dg

@@ -88,12 +88,11 @@ struct Lca {
     }
   }
 
-  // One step of one trial. Returns true when the trial has ended at this step.
-  static __device__ __forceinline__ bool step(const LcaParams& p, uint32_t trial, int k, int g,
+  // One step of one trial with its normals e. Returns true when the trial has
+  // ended at this step.
+  static __device__ __forceinline__ bool step(const LcaParams& p, const float (&e)[NU], int g,
                                               unsigned gmask, float (&x)[NU], const float (&I)[NU],
                                               int8_t& choice) {
-    float e[NU];
-    noise(p, trial, k, g, e);
     const float S = group_sum(chunk_sum(x), gmask);
 #pragma unroll
     for (int i = 0; i < NU; ++i) {
@@ -156,23 +155,32 @@ __global__ void __launch_bounds__(256) lca_batched(LcaParams p) {
   const int g = lane % TPT;
   const int root = lane - g;
   const unsigned gmask = (TPT == 32 ? kFull : ((1u << TPT) - 1u)) << root;
-  float x[L::NU], I[L::NU];
+  float x[L::NU], I[L::NU], e[L::NU];
   long long f = fetch_trial(p.cursor, g == 0);
   f = __shfl_sync(kFull, f, root);
   bool active = f >= 0 && f < p.n;
   long long t = active ? (p.perm ? (long long)__ldg(p.perm + f) : f) : 0;
   int k = 0;
-  if (active) L::load(p, t, g, x, I);
+  if (active) {
+    L::load(p, t, g, x, I);
+    L::noise(p, p.trial0 + (uint32_t)t, 0, g, e);
+  }
   while (__any_sync(kFull, active)) {
     bool finished = false;
     if (active) {
+      // the next step's normals do not depend on the state: drawn alongside
+      // this step's update, they take the noise off the step's critical path
+      float en[L::NU];
+      L::noise(p, p.trial0 + (uint32_t)t, k + 1, g, en);
       int8_t c = -1;
-      const bool hit = L::step(p, p.trial0 + (uint32_t)t, k, g, gmask, x, I, c);
+      const bool hit = L::step(p, e, g, gmask, x, I, c);
       ++k;
       if (hit || k >= p.max_steps) {
         L::store(p, t, g, hit ? c : (int8_t)-1, hit ? k : p.max_steps, x);
         finished = true;
       }
+#pragma unroll
+      for (int i = 0; i < L::NU; ++i) e[i] = en[i];
     }
     f = fetch_trial(p.cursor, finished && g == 0);
     f = __shfl_sync(kFull, f, root);
@@ -182,6 +190,7 @@ __global__ void __launch_bounds__(256) lca_batched(LcaParams p) {
       if (active) {
         t = p.perm ? (long long)__ldg(p.perm + f) : f;
         L::load(p, t, g, x, I);
+        L::noise(p, p.trial0 + (uint32_t)t, 0, g, e);
       }
     }
   }
@@ -198,7 +207,9 @@ __global__ void __launch_bounds__(256) lca_plain(LcaParams p) {
   L::load(p, t, 0, x, I);
   for (int k = 0; k < p.max_steps; ++k) {
     int8_t c = -1;
-    if (L::step(p, p.trial0 + (uint32_t)t, k, 0, gmask, x, I, c)) {
+    float e[L::NU];
+    L::noise(p, p.trial0 + (uint32_t)t, k, 0, e);
+    if (L::step(p, e, 0, gmask, x, I, c)) {
       L::store(p, t, 0, c, k + 1, x);
       return;
     }

@@ -65,14 +65,14 @@ __global__ void __launch_bounds__(256) net_group(NetParams p) {
   const unsigned gmask = (G == 32 ? kFull : ((1u << G) - 1u)) << root;
   const bool real = u < L.U;
   const bool in_stop = u >= L.stop_off && u < L.stop_off + L.stop_size;
-  const float gain = real ? L.gain[u] : 1.f, bias = real ? L.bias[u] : 0.f;
+  const Logistic lg = Logistic::of(real ? L.gain[u] : 1.f, real ? L.bias[u] : 0.f);
 
   long long f = fetch_trial(p.cursor, u == 0);
   f = __shfl_sync(kFull, f, root);
   bool active = f >= 0 && f < p.n;
   long long t = f;
   int k = 0;
-  float s = 0.f, y = logistic(gain, bias, 0.f), netc = 0.f;
+  float s = 0.f, y = lg(0.f), netc = 0.f;
   if (active && real) netc = const_net(p, L, t, u);
   while (__any_sync(kFull, active)) {
     bool finished = false;
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) net_group(NetParams p) {
       if (real) {
         const float e = unit_noise(p, p.trial0 + (uint32_t)t, k, L.U, u);
         s = fmaf(1.0f - L.rate, s, fmaf(L.rate, net, L.noise * e));
-        y = logistic(gain, bias, s);
+        y = lg(s);
       }
       // top-1 (lowest index on ties) and top-2 of the stop layer
       float v1 = in_stop ? y : -FLT_MAX, v2 = -FLT_MAX;
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(256) net_group(NetParams p) {
       t = f;
       k = 0;
       s = 0.f;
-      y = logistic(gain, bias, 0.f);
+      y = lg(0.f);
       netc = (active && real) ? const_net(p, L, t, u) : 0.f;
     }
   }
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(128) net_plain(NetParams p) {
   for (int u = 0; u < U; ++u) {
     netc[u * B + tid] = const_net(p, L, t, u);
     s[u * B + tid] = 0.f;
-    y[u * B + tid] = logistic(L.gain[u], L.bias[u], 0.f);
+    y[u * B + tid] = Logistic::of(L.gain[u], L.bias[u])(0.f);
   }
   const uint32_t trial = p.trial0 + (uint32_t)t;
   for (int k = 0; k < L.max_steps; ++k) {
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(128) net_plain(NetParams p) {
       const float e = pick4(z, dn & 3u);
       const float sv = fmaf(1.0f - L.rate, s[u * B + tid], fmaf(L.rate, net, L.noise * e));
       s[u * B + tid] = sv;
-      yn[u * B + tid] = logistic(L.gain[u], L.bias[u], sv);
+      yn[u * B + tid] = Logistic::of(L.gain[u], L.bias[u])(sv);
     }
     float* tmp = y;
     y = yn;

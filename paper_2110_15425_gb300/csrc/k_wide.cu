@@ -136,6 +136,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
   uint32_t r[4];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
@@ -294,6 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1) wide_kernel(WideParams p) {
   int k = 0;
   uint32_t phase = 0;
   const float keep = 1.0f - p.rate;
+  const Logistic lg_h = Logistic::of(p.gain_h, p.bias_h), lg_r = Logistic::of(p.gain_r, p.bias_r);
   float* net_sm = reinterpret_cast<float*>(smem + L::A_OFF) + 4 * kR * kRows;  // plain: [H][128]
   float* part = reinterpret_cast<float*>(smem + L::A_OFF);                      // plain: [4][16][128]
 
@@ -346,49 +358,47 @@ __global__ void __launch_bounds__(kThreads, 1) wide_kernel(WideParams p) {
     float acc[kR];
 #pragma unroll
     for (int n = 0; n < kR; ++n) acc[n] = 0.f;
+    // eight hidden units (two Philox blocks) at a time
 #pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-      float nv[16];
+    for (int c = 0; c < HQ / 8; ++c) {
+      float nv[8];
       if (TC) {
-        tmem_ld16(tmem + lane_base + (uint32_t)(q * HQ + 16 * c), nv);
+        tmem_ld8(tmem + lane_base + (uint32_t)(q * HQ + 8 * c), nv);
       } else {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) nv[i] = net_sm[(q * HQ + 16 * c + i) * kRows + r];
+        for (int i = 0; i < 8; ++i) nv[i] = net_sm[(q * HQ + 8 * c + i) * kRows + r];
       }
-      float e[16];
+      float e[8];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const float4 z = normals4(noise_block(p.k0, p.k1, tg, 0u, blk0 + (uint32_t)(4 * c + b)));
+      for (int b = 0; b < 2; ++b) {
+        const float4 z = normals4(noise_block(p.k0, p.k1, tg, 0u, blk0 + (uint32_t)(2 * c + b)));
         e[4 * b] = z.x;
         e[4 * b + 1] = z.y;
         e[4 * b + 2] = z.z;
         e[4 * b + 3] = z.w;
       }
-      float y[16];
+      float y[8];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        float& sv = s[16 * c + i];
-        y[i] = logistic(p.gain_h, p.bias_h, sv);
+      for (int i = 0; i < 8; ++i) {
+        float& sv = s[8 * c + i];
+        y[i] = lg_h(sv);
         sv = fmaf(keep, sv, fmaf(p.rate, nv[i], p.noise * e[i]));
       }
       if (TC) {
         unsigned char* A = smem + L::A_OFF;
-        const int kk = q * HQ + 16 * c;
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          uint4 hi, lo;
-          split2(y[8 * half + 0], y[8 * half + 1], hi.x, lo.x);
-          split2(y[8 * half + 2], y[8 * half + 3], hi.y, lo.y);
-          split2(y[8 * half + 4], y[8 * half + 5], hi.z, lo.z);
-          split2(y[8 * half + 6], y[8 * half + 7], hi.w, lo.w);
-          *reinterpret_cast<uint4*>(A + kmajor_off(r, kk + 8 * half, L::K2)) = hi;
-          *reinterpret_cast<uint4*>(A + kmajor_off(r, H + kk + 8 * half, L::K2)) = lo;
-        }
+        const int kk = q * HQ + 8 * c;
+        uint4 hi, lo;
+        split2(y[0], y[1], hi.x, lo.x);
+        split2(y[2], y[3], hi.y, lo.y);
+        split2(y[4], y[5], hi.z, lo.z);
+        split2(y[6], y[7], hi.w, lo.w);
+        *reinterpret_cast<uint4*>(A + kmajor_off(r, kk, L::K2)) = hi;
+        *reinterpret_cast<uint4*>(A + kmajor_off(r, H + kk, L::K2)) = lo;
       } else {
         const float* W = reinterpret_cast<const float*>(smem + L::B_OFF);   // [16][H]
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int h = q * HQ + 16 * c + i;
+        for (int i = 0; i < 8; ++i) {
+          const int h = q * HQ + 8 * c + i;
 #pragma unroll
           for (int n = 0; n < kR; ++n) acc[n] = fmaf(W[n * H + h], y[i], acc[n]);
         }
@@ -443,7 +453,7 @@ __global__ void __launch_bounds__(kThreads, 1) wide_kernel(WideParams p) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         sr[j] = fmaf(keep, sr[j], fmaf(p.rate, net[j], p.noise * e4[j]));
-        sh.yr[4 * q + j][r] = logistic(p.gain_r, p.bias_r, sr[j]);
+        sh.yr[4 * q + j][r] = lg_r(sr[j]);
       }
     }
     phase ^= 1u;
