@@ -222,6 +222,14 @@ dg_status dg_argmax_f64(dg_ctx* ctx, const double* values, int64_t n, dg_grid_re
    written), or DG_E_CUDA. */
 dg_status dg_stream_status(dg_ctx* ctx, void* stream);
 
+/* Exercise the device-side failure path on `stream`: a kernel waits on a
+   barrier that nothing ever completes, gives up after about wait_us
+   microseconds (1 .. 2,000,000) and records it in the stream's status word, as
+   the tensor-core kernel does when one of its waits expires. A following
+   dg_stream_status returns DG_E_TIMEOUT; the context stays usable. Test aid;
+   the paper has no counterpart. */
+dg_status dg_selftest_wait_timeout(dg_ctx* ctx, int32_t wait_us, void* stream);
+
 /* Allocation-free dg_grid_search. The paper has no counterpart: this entry
    point exists for callers that may not allocate device memory themselves or
    let a library do it behind their back - code that runs while someone else's

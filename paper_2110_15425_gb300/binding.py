@@ -86,7 +86,7 @@ EXPORTS = [
     "dg_model_info", "dg_run", "dg_grid_search", "dg_argmax_f64", "dg_philox_words",
     "dg_normals", "dg_batch_create", "dg_batch_add_run", "dg_batch_add_grid",
     "dg_batch_launch", "dg_batch_free", "dg_submit", "dg_wait", "dg_serve_stats",
-    "dg_grid_search_noalloc", "dg_stream_status",
+    "dg_grid_search_noalloc", "dg_stream_status", "dg_selftest_wait_timeout",
 ]
 
 _lib = None
@@ -120,6 +120,7 @@ def _declare(L):
         "dg_grid_search": [P, C.POINTER(dg_grid_desc), P, P, P],
         "dg_grid_search_noalloc": [P, C.POINTER(dg_grid_desc), P, P, P],
         "dg_stream_status": [P, P],
+        "dg_selftest_wait_timeout": [P, i32, P],
         "dg_argmax_f64": [P, P, i64, P, P],
         "dg_philox_words": [u64, u32, u32, u32, u32, i64, P, P],
         "dg_normals": [u64, u32, u32, u64, i64, P, P],
@@ -214,6 +215,10 @@ def dg_grid_search(model, desc, result, cand_means=None, stream=None):
 def dg_grid_search_noalloc(model, desc, result, cand_means=None, stream=None):
     check(lib().dg_grid_search_noalloc(model, C.byref(desc), ptr(result), ptr(cand_means),
                                        stream_handle(stream)))
+
+
+def dg_selftest_wait_timeout(ctx, wait_us, stream=None):
+    check(lib().dg_selftest_wait_timeout(ctx, wait_us, stream_handle(stream)))
 
 
 def dg_stream_status(ctx, stream=None):

@@ -170,6 +170,8 @@ cudaError_t launch_philox_words(uint64_t seed, uint32_t trial, uint32_t cand, ui
 cudaError_t launch_normals(uint64_t seed, uint32_t trial, uint32_t cand, uint64_t d0, int64_t n,
                            float* out, cudaStream_t s);
 
+cudaError_t launch_wait_timeout(long long limit_cycles, int* status, cudaStream_t s);
+
 int num_sms();
 
 }  // namespace dg

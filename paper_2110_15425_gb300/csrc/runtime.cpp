@@ -1287,6 +1287,21 @@ dg_status dg_stream_status(dg_ctx* ctx, void* stream) {
               word);
 }
 
+dg_status dg_selftest_wait_timeout(dg_ctx* ctx, int32_t wait_us, void* stream) {
+  if (!ctx || wait_us < 1 || wait_us > 2000000)
+    return fail(DG_E_ARG, "dg_selftest_wait_timeout: wait_us must be in [1, 2e6]");
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_CUDA(cudaSetDevice(ctx->device));
+  Scratch* sc = nullptr;
+  dg_status st = get_scratch(ctx, s, &sc);
+  if (st != DG_OK) return st;
+  int khz = 0;
+  DG_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device));
+  if (khz <= 0) khz = 2000000;
+  DG_CUDA(dg::launch_wait_timeout((long long)wait_us * khz / 1000, sc->status(), s));
+  return DG_OK;
+}
+
 dg_status dg_philox_words(uint64_t seed, uint32_t trial, uint32_t cand, uint32_t purpose,
                           uint32_t block0, int64_t nblocks, uint32_t* out, void* stream) {
   if (nblocks < 0 || (nblocks > 0 && !out)) return fail(DG_E_ARG, "dg_philox_words: bad arguments");
