@@ -98,6 +98,7 @@ def _bind(L):
     L.or_pp_means.argtypes = [P, C.c_int32, P, C.c_int32, P, C.c_int32, P, C.c_int32, P,
                               C.c_int64, C.c_uint64, C.c_double, C.c_double, P]
     L.or_argmax.argtypes = [P, C.c_int64, P, P, P]
+    L.or_argmax_reservoir.argtypes = [P, C.c_int64, C.c_uint64, P, P, P, P]
     return L
 
 
@@ -307,3 +308,16 @@ def argmax(v):
     g = C.c_double()
     lib().or_argmax(_p(v), v.shape[0], C.byref(b), C.byref(bv), C.byref(g))
     return int(b.value), float(bv.value), float(g.value)
+
+
+def argmax_reservoir(v, seed):
+    """(best index, best value, gap, number of ties): random choice among exact
+    ties by reservoir sampling (Sec. 3.3)."""
+    v = _c(v, np.float64)
+    b = C.c_int64()
+    bv = C.c_double()
+    g = C.c_double()
+    k = C.c_int64()
+    lib().or_argmax_reservoir(_p(v), v.shape[0], seed, C.byref(b), C.byref(bv), C.byref(g),
+                              C.byref(k))
+    return int(b.value), float(bv.value), float(g.value), int(k.value)

@@ -340,3 +340,31 @@ void or_argmax(const double* v, int64_t n, int64_t* best, double* best_value, do
   *best_value = v[b];
   *gap = (n > 1) ? v[b] - second : 0.0;
 }
+
+void or_argmax_reservoir(const double* v, int64_t n, uint64_t seed, int64_t* best,
+                         double* best_value, double* gap, int64_t* n_ties) {
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  int64_t choice = 0; /* the reservoir's one element */
+  int64_t k = 1;      /* values equal to the running maximum seen so far */
+  double top = v[0];
+  for (int64_t i = 1; i < n; ++i) {
+    if (v[i] > top) {
+      top = v[i];
+      choice = i;
+      k = 1;
+    } else if (v[i] == top) {
+      k += 1;
+      const uint32_t ctr[4] = {(uint32_t)i, (uint32_t)((uint64_t)i >> 32), 0u, 4u};
+      uint32_t w[4];
+      or_philox4x32_10(ctr, key, w);
+      if ((uint64_t)w[0] * (uint64_t)k < ((uint64_t)1 << 32)) choice = i;
+    }
+  }
+  double second = -INFINITY;
+  for (int64_t i = 0; i < n; ++i)
+    if (i != choice && v[i] > second) second = v[i];
+  *best = choice;
+  *best_value = top;
+  *gap = (n > 1) ? top - second : 0.0;
+  *n_ties = k;
+}

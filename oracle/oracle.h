@@ -23,6 +23,8 @@
  *     logistic range, stop-rule closed form.
  *   - Grid search: noise-free geometric limits, perception variance,
  *     candidate index layout, lowest-index argmax.
+ *   - Reservoir tie-break: a rank-based restatement (the last tied index whose
+ *     draw accepts its rank), uniformity over the tie set, the no-tie case.
  */
 #ifndef DISTILL_ORACLE_H
 #define DISTILL_ORACLE_H
@@ -154,6 +156,18 @@ void or_pp_means(const float* pos, int32_t n_trials, const float* lv0, int32_t L
 /* argmax with lowest index on exact ties; gap = best - second best (0 on a tie;
    0 when n == 1). */
 void or_argmax(const double* v, int64_t n, int64_t* best, double* best_value, double* gap);
+
+/* argmax with a uniformly random choice among exact ties (the reservoir
+   sampling of Sec. 3.3; Vitter, ACM TOMS 1985, Algorithm R with a reservoir of
+   one). One pass over v in index order: a value above the running maximum
+   empties the reservoir and becomes its element (k = 1); the k-th value equal
+   to the running maximum, at index i, replaces the element with probability
+   1/k, decided by word 0 w of Philox4x32-10(key = (seed lo, seed hi),
+   counter = (i lo, i hi, 0, 4)): replace iff w k < 2^32. Purpose 4 keeps these
+   draws apart from every noise stream (purpose 0). n_ties = number of values
+   equal to the maximum; gap as or_argmax (0 on a tie). */
+void or_argmax_reservoir(const double* v, int64_t n, uint64_t seed, int64_t* best,
+                         double* best_value, double* gap, int64_t* n_ties);
 
 #ifdef __cplusplus
 }
