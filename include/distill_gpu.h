@@ -73,6 +73,11 @@ typedef enum {
 #define DG_MODE_BATCHED 0 /* persistent kernel, trials refilled as others finish, autotuned */
 #define DG_MODE_PLAIN 1   /* one thread per trial, one launch, no refill (comparison form) */
 
+/* dg_grid_desc.tie_break: which of several exactly equal best means is chosen */
+#define DG_TIE_LOWEST 0    /* the lowest candidate index */
+#define DG_TIE_RESERVOIR 1 /* uniformly at random by reservoir sampling (Sec. 3.3), see
+                              dg_argmax_f64_reservoir */
+
 typedef struct {
   int32_t kind;       /* dg_mech_kind */
   int32_t size;       /* number of units */
@@ -134,14 +139,14 @@ typedef struct {
   const float* positions;     /* device, [n_trials][6]: player xy, predator xy, prey xy */
   uint64_t seed;
   int32_t mode;               /* DG_MODE_* */
-  int32_t reserved;
+  int32_t tie_break;          /* DG_TIE_*; the reservoir draws use `seed` */
   int64_t cand_begin;         /* evaluate candidates cand_begin .. cand_begin + cand_count - 1 */
   int64_t cand_count;         /* (0 = all); cand_means[i] is candidate cand_begin + i, and
                                  best_index is a global candidate index */
 } dg_grid_desc;
 
 typedef struct {
-  int64_t best_index;         /* c = (l0 * L1 + l1) * L2 + l2; lowest index on exact ties */
+  int64_t best_index;         /* c = (l0 * L1 + l1) * L2 + l2; on exact ties as tie_break says */
   double best_value;          /* FP64 mean outcome of the best candidate */
   double runner_up_gap;       /* best_value - second best value (0 on a tie) */
 } dg_grid_result;
@@ -202,7 +207,10 @@ dg_status dg_run(dg_model* model, const dg_run_desc* desc, int8_t* choice, int32
 
 /* Predator-prey grid search (Sec. 2.1, 3.6): simulate every candidate
    allocation over desc->n_trials noisy trials, average the outcomes in FP64,
-   and take the argmax (lowest index on exact ties).
+   and take the argmax. Exact ties of the best mean go to the lowest index, or
+   with desc->tie_break = DG_TIE_RESERVOIR to a random one of them, drawn as
+   dg_argmax_f64_reservoir does over the evaluated candidates (indices
+   cand_begin ..) in order.
    result: device pointer to one dg_grid_result.
    cand_means (may be NULL): device, FP64 [L0 L1 L2] mean outcome per candidate.
    Errors: DG_E_ARG, DG_E_UNSUPPORTED (not a PREDATOR_PREY model), DG_E_CUDA. */
@@ -213,6 +221,17 @@ dg_status dg_grid_search(dg_model* model, const dg_grid_desc* desc, dg_grid_resu
    device dg_grid_result. n >= 1. */
 dg_status dg_argmax_f64(dg_ctx* ctx, const double* values, int64_t n, dg_grid_result* result,
                         void* stream);
+
+/* Argmax over n FP64 values (device) with a uniformly random choice among the
+   values equal to the maximum - the reservoir sampling of Sec. 3.3 (Vitter's
+   Algorithm R, reservoir of one, values visited in index order): the k-th
+   value equal to the running maximum, at index i, replaces the reservoir's
+   element when w k < 2^32, w = word 0 of Philox4x32-10(key = (seed lo, seed
+   hi), counter = (i lo, i hi, 0, 4)); a larger value restarts the count at 1.
+   The choice is deterministic for a seed. result->runner_up_gap is 0 on a tie.
+   Errors: DG_E_ARG (null pointers, n < 1), DG_E_CUDA. */
+dg_status dg_argmax_f64_reservoir(dg_ctx* ctx, const double* values, int64_t n, uint64_t seed,
+                                  dg_grid_result* result, void* stream);
 
 /* Device-side status of the work enqueued on `stream` through this context:
    waits for the stream, then reports and clears the status word that kernels
@@ -242,8 +261,8 @@ dg_status dg_selftest_wait_timeout(dg_ctx* ctx, int32_t wait_us, void* stream);
    device memory instead (280 KiB, present on every GPU that loads the library
    until the process exits) and calls no allocator.
    Same arguments, outputs and results as dg_grid_search, with these limits:
-     - DG_MODE_PLAIN without cand_means evaluates at most 32768 candidates
-       per call (DG_E_ARG beyond that);
+     - DG_MODE_PLAIN, or DG_TIE_RESERVOIR, without cand_means evaluates at
+       most 32768 candidates per call (DG_E_ARG beyond that);
      - the first call on a device looks up the array's device address; make
        that first call before any stream capture on that device;
      - every call shares the one array and it keeps the last call's contents

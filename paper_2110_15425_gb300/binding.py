@@ -24,6 +24,7 @@ DG_INPUT, DG_TRANSFER_LOGISTIC, DG_DDM, DG_LCA, DG_PP_OBSERVE, DG_PP_ACTION, DG_
 DG_LCA_NO_RECTIFY, DG_LCA_TWO_SIDED = 1, 2
 DG_F32, DG_BF16 = 0, 1
 DG_MODE_BATCHED, DG_MODE_PLAIN = 0, 1
+DG_TIE_LOWEST, DG_TIE_RESERVOIR = 0, 1
 MODEL_KINDS = {0: "ddm", 1: "lca", 2: "transfer", 3: "transfer_wide", 4: "predator_prey"}
 
 
@@ -60,7 +61,7 @@ class dg_run_desc(C.Structure):
 class dg_grid_desc(C.Structure):
     _fields_ = [("n_levels", C.c_int32 * 3), ("n_trials", C.c_int32),
                 ("levels", C.c_void_p * 3), ("positions", C.c_void_p), ("seed", C.c_uint64),
-                ("mode", C.c_int32), ("reserved", C.c_int32), ("cand_begin", C.c_int64),
+                ("mode", C.c_int32), ("tie_break", C.c_int32), ("cand_begin", C.c_int64),
                 ("cand_count", C.c_int64)]
 
 
@@ -87,6 +88,7 @@ EXPORTS = [
     "dg_normals", "dg_batch_create", "dg_batch_add_run", "dg_batch_add_grid",
     "dg_batch_launch", "dg_batch_free", "dg_submit", "dg_wait", "dg_serve_stats",
     "dg_grid_search_noalloc", "dg_stream_status", "dg_selftest_wait_timeout",
+    "dg_argmax_f64_reservoir",
 ]
 
 _lib = None
@@ -122,6 +124,7 @@ def _declare(L):
         "dg_stream_status": [P, P],
         "dg_selftest_wait_timeout": [P, i32, P],
         "dg_argmax_f64": [P, P, i64, P, P],
+        "dg_argmax_f64_reservoir": [P, P, i64, u64, P, P],
         "dg_philox_words": [u64, u32, u32, u32, u32, i64, P, P],
         "dg_normals": [u64, u32, u32, u64, i64, P, P],
         "dg_batch_create": [P, C.POINTER(P)],
@@ -228,6 +231,11 @@ def dg_stream_status(ctx, stream=None):
 def dg_argmax_f64(ctx, values, result, stream=None):
     check(lib().dg_argmax_f64(ctx, ptr(values), values.numel(), ptr(result),
                               stream_handle(stream)))
+
+
+def dg_argmax_f64_reservoir(ctx, values, seed, result, stream=None):
+    check(lib().dg_argmax_f64_reservoir(ctx, ptr(values), values.numel(), seed, ptr(result),
+                                        stream_handle(stream)))
 
 
 def dg_philox_words(seed, trial, cand, purpose, block0, nblocks, out, stream=None):
@@ -366,8 +374,10 @@ def run_desc(n_trials, seed, trial_params=None, cond_inputs=None, n_cond=0, cond
     return d
 
 
-def grid_desc(levels, positions, seed, mode=DG_MODE_BATCHED, cand_begin=0, cand_count=0):
+def grid_desc(levels, positions, seed, mode=DG_MODE_BATCHED, cand_begin=0, cand_count=0,
+              tie_break=DG_TIE_LOWEST):
     d = dg_grid_desc()
+    d.tie_break = tie_break
     d._keep = (tuple(levels), positions)
     d.cand_begin = cand_begin
     d.cand_count = cand_count

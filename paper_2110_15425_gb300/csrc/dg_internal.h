@@ -145,6 +145,10 @@ int grid_blocks(int mode, long long n_cand, int n_trials);
 
 cudaError_t launch_argmax(const double* v, long long n, TopTwo* partials, unsigned int* ticket,
                           void* result, cudaStream_t s);
+// After an argmax into `result` over v[0..n) (global indices base..): replace
+// the lowest tied index by the reservoir-sampled one when the maximum is tied.
+cudaError_t launch_tie_reservoir(const double* v, long long n, long long base, uint64_t seed,
+                                 void* result, cudaStream_t s);
 
 // ------------------------------------------- longest-expected-first order ---
 constexpr int kSchedBuckets = 1024;

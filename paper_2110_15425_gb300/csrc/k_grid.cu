@@ -13,6 +13,15 @@
 // to finish merges the per-block partials (no second launch, no atomics on
 // the values). Plain form (the paper's mapping): one thread per candidate
 // with a sequential FP64 sum, then a separate argmax launch.
+//
+// Random tie-break (Sec. 3.3: one of several equally good choices is picked at
+// random by reservoir sampling). A one-element reservoir filled in candidate
+// order (Vitter's Algorithm R) ends holding the last tie t_k, among the ties
+// t_1 < t_2 < ... at the maximum, whose draw accepted its rank k (t_1 always
+// does; t_k for k >= 2 when w k < 2^32, w = word 0 of Philox(seed, counter
+// (t_k lo, t_k hi, 0, 4))). tie_reservoir computes exactly that after the
+// argmax: one block scans the stored means in index order, ranks the ties by
+// a block prefix count, and keeps the largest accepted index.
 #include <cfloat>
 #include <climits>
 
@@ -219,6 +228,54 @@ __global__ void __launch_bounds__(256) argmax_kernel(const double* v, long long 
   finish_argmax(best, partials, ticket, result);
 }
 
+__device__ __forceinline__ bool reservoir_accepts(uint32_t k0, uint32_t k1, long long i,
+                                                  long long k) {
+  if (k == 1) return true;
+  const unsigned long long u = (unsigned long long)i;
+  const uint4 w = philox(make_uint4((uint32_t)u, (uint32_t)(u >> 32), 0u, 4u), k0, k1);
+  return (unsigned long long)w.x * (unsigned long long)k < (1ull << 32);
+}
+
+__global__ void __launch_bounds__(1024) tie_reservoir(const double* v, long long n,
+                                                      long long base, uint32_t k0,
+                                                      uint32_t k1, void* result) {
+  __shared__ int cnt[32];
+  __shared__ long long pick[32];
+  GridResultDev* out = reinterpret_cast<GridResultDev*>(result);
+  const double top = out->best_value;
+  // gap != 0: the maximum is unique and the argmax already holds it
+  if (n < 2 || out->gap != 0.0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  long long rank0 = 0, chosen = -1;
+  for (long long start = 0; start < n; start += blockDim.x) {
+    const long long i = start + threadIdx.x;
+    const bool tie = i < n && v[i] == top;
+    const unsigned b = __ballot_sync(kFull, tie);
+    if (lane == 0) cnt[warp] = __popc(b);
+    __syncthreads();
+    int before = __popc(b & ((1u << lane) - 1u)), total = 0;
+    for (int w = 0; w < nw; ++w) {
+      total += cnt[w];
+      if (w < warp) before += cnt[w];
+    }
+    if (tie && reservoir_accepts(k0, k1, base + i, rank0 + before + 1)) chosen = base + i;
+    rank0 += total;
+    __syncthreads();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long other = __shfl_xor_sync(kFull, chosen, o);
+    chosen = other > chosen ? other : chosen;
+  }
+  if (lane == 0) pick[warp] = chosen;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long c = pick[0];
+    for (int w = 1; w < nw; ++w) c = pick[w] > c ? pick[w] : c;
+    if (c >= 0) out->best_index = c;
+  }
+}
+
 size_t grid_smem(const GridParams& p) {
   return sizeof(float) * (6 * (size_t)p.n_trials + p.L[0] + p.L[1] + p.L[2]);
 }
@@ -263,6 +320,12 @@ cudaError_t launch_grid(const GridParams& p, int mode, const LaunchCfg& cfg, cud
   const long long need = (p.n_cand + block / 32 - 1) / (block / 32);
   if (grid > need) grid = (int)need;
   grid_batched<<<grid, block, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tie_reservoir(const double* v, long long n, long long base, uint64_t seed,
+                                 void* result, cudaStream_t s) {
+  tie_reservoir<<<1, 1024, 0, s>>>(v, n, base, (uint32_t)seed, (uint32_t)(seed >> 32), result);
   return cudaGetLastError();
 }
 

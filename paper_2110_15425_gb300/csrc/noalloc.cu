@@ -61,11 +61,13 @@ extern "C" dg_status dg_grid_search_noalloc(dg_model* model, const dg_grid_desc*
   dg_status st = dg::grid_params_noalloc(model, desc, result, cand_means, &p);
   if (st != DG_OK) return st;
   const bool plain = desc->mode == DG_MODE_PLAIN;
-  if (plain && !cand_means && p.n_cand > kMaxCandidates)
+  const bool reservoir = desc->tie_break == DG_TIE_RESERVOIR;
+  const bool need_means = (plain || reservoir) && !cand_means;
+  if (need_means && p.n_cand > kMaxCandidates)
     return dg::set_error(DG_E_ARG,
-                         "dg_grid_search_noalloc: the plain form without cand_means holds at most "
-                         "32768 candidate means in its fixed scratch; pass cand_means or evaluate "
-                         "fewer candidates per call");
+                         "dg_grid_search_noalloc: the plain form or the reservoir tie-break "
+                         "without cand_means holds at most 32768 candidate means in its fixed "
+                         "scratch; pass cand_means or evaluate fewer candidates per call");
   const int dev = dg::model_device(model);
   if (cudaSetDevice(dev) != cudaSuccess)
     return dg::set_error(DG_E_CUDA, "dg_grid_search_noalloc: cudaSetDevice failed");
@@ -75,7 +77,7 @@ extern "C" dg_status dg_grid_search_noalloc(dg_model* model, const dg_grid_desc*
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   p.ticket = reinterpret_cast<unsigned int*>(base);
   p.partials = reinterpret_cast<dg::TopTwo*>(base + kHeader);
-  if (plain && !cand_means) p.means = reinterpret_cast<double*>(base + kHeader + kPartialsBytes);
+  if (need_means) p.means = reinterpret_cast<double*>(base + kHeader + kPartialsBytes);
   // the array keeps the previous call's contents: the ticket must start at 0
   if (cudaMemsetAsync(p.ticket, 0, sizeof(unsigned int), s) != cudaSuccess)
     return dg::set_error(DG_E_CUDA, "dg_grid_search_noalloc: ticket reset failed");
@@ -84,7 +86,9 @@ extern "C" dg_status dg_grid_search_noalloc(dg_model* model, const dg_grid_desc*
   const int want = dg::grid_blocks(0, p.n_cand, p.n_trials);
   cfg.grid = want < kBlocks ? want : kBlocks;
   if (cfg.grid < 1) cfg.grid = 1;
-  const cudaError_t e = dg::launch_grid(p, plain ? 1 : 0, cfg, s);
+  cudaError_t e = dg::launch_grid(p, plain ? 1 : 0, cfg, s);
+  if (e == cudaSuccess && reservoir)
+    e = dg::launch_tie_reservoir(p.means, p.n_cand, p.cand0, desc->seed, result, s);
   if (e != cudaSuccess) return dg::set_error(DG_E_CUDA, cudaGetErrorString(e));
   return DG_OK;
 }

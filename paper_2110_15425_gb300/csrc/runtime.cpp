@@ -570,6 +570,8 @@ dg_status check_grid_args(dg_model* m, const dg_grid_desc* d, dg_grid_result* re
     return fail(DG_E_ARG, "dg_grid_search: null positions or levels");
   if (d->mode != DG_MODE_BATCHED && d->mode != DG_MODE_PLAIN)
     return fail(DG_E_ARG, "dg_grid_search: unknown mode %d", d->mode);
+  if (d->tie_break != DG_TIE_LOWEST && d->tie_break != DG_TIE_RESERVOIR)
+    return fail(DG_E_ARG, "dg_grid_search: unknown tie_break %d", d->tie_break);
   const long long n = (long long)d->n_levels[0] * d->n_levels[1] * d->n_levels[2];
   if (n > 0xFFFFFFFFll) return fail(DG_E_ARG, "dg_grid_search: more than 2^32 candidates");
   if (d->cand_begin < 0 || d->cand_count < 0 || d->cand_begin + d->cand_count > n ||
@@ -602,7 +604,8 @@ dg_status grid_device(dg_model* m, const dg_grid_desc* d, dg_grid_result* result
   p.partials = sc->partials();
   p.ticket = sc->ticket();
   p.result = result;
-  if (d->mode == DG_MODE_PLAIN && !means) {
+  const bool reservoir = d->tie_break == DG_TIE_RESERVOIR;
+  if ((d->mode == DG_MODE_PLAIN || reservoir) && !means) {
     st = scratch_means(m->ctx, sc, (size_t)p.n_cand, s);
     if (st != DG_OK) return st;
     p.means = sc->means;
@@ -610,6 +613,8 @@ dg_status grid_device(dg_model* m, const dg_grid_desc* d, dg_grid_result* result
   auto go = [&](const dg::LaunchCfg& c) -> dg_status {
     DG_CUDA(cudaMemsetAsync(sc->ticket(), 0, 4, s));
     DG_CUDA(dg::launch_grid(p, d->mode, c, s));
+    if (reservoir)
+      DG_CUDA(dg::launch_tie_reservoir(p.means, p.n_cand, p.cand0, d->seed, result, s));
     return DG_OK;
   };
   if (d->mode == DG_MODE_PLAIN) return go(dg::LaunchCfg{});
@@ -1262,6 +1267,20 @@ dg_status dg_argmax_f64(dg_ctx* ctx, const double* values, int64_t n, dg_grid_re
   if (st != DG_OK) return st;
   DG_CUDA(cudaMemsetAsync(sc->ticket(), 0, 4, s));
   DG_CUDA(dg::launch_argmax(values, n, sc->partials(), sc->ticket(), result, s));
+  return DG_OK;
+}
+
+dg_status dg_argmax_f64_reservoir(dg_ctx* ctx, const double* values, int64_t n, uint64_t seed,
+                                  dg_grid_result* result, void* stream) {
+  if (!ctx || !values || !result || n < 1)
+    return fail(DG_E_ARG, "dg_argmax_f64_reservoir: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch* sc = nullptr;
+  dg_status st = get_scratch(ctx, s, &sc);
+  if (st != DG_OK) return st;
+  DG_CUDA(cudaMemsetAsync(sc->ticket(), 0, 4, s));
+  DG_CUDA(dg::launch_argmax(values, n, sc->partials(), sc->ticket(), result, s));
+  DG_CUDA(dg::launch_tie_reservoir(values, n, 0, seed, result, s));
   return DG_OK;
 }
 
