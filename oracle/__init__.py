@@ -99,6 +99,8 @@ def _bind(L):
                               C.c_int64, C.c_uint64, C.c_double, C.c_double, P]
     L.or_argmax.argtypes = [P, C.c_int64, P, P, P]
     L.or_argmax_reservoir.argtypes = [P, C.c_int64, C.c_uint64, P, P, P, P]
+    L.or_pp_refine.argtypes = [P, C.c_int32, P, P, C.c_int32, C.c_int32, C.c_uint64, C.c_double,
+                               C.c_double, P, P, P, P, P]
     return L
 
 
@@ -321,3 +323,20 @@ def argmax_reservoir(v, seed):
     lib().or_argmax_reservoir(_p(v), v.shape[0], seed, C.byref(b), C.byref(bv), C.byref(g),
                               C.byref(k))
     return int(b.value), float(bv.value), float(g.value), int(k.value)
+
+
+def pp_refine(pos, lo, hi, points, rounds, seed, obs_offset=0.1, pred_weight=0.5):
+    """Coarse-to-fine grid search (Sec. 4.3 by simulation): per round the best
+    index, its mean, the runner-up gap, the round's box (lo[3], hi[3]) and the
+    best allocation."""
+    pos = _c(pos, np.float32)
+    lo = _c(lo, np.float32)
+    hi = _c(hi, np.float32)
+    best = np.zeros(rounds, np.int64)
+    value = np.zeros(rounds, np.float64)
+    gap = np.zeros(rounds, np.float64)
+    box = np.zeros((rounds, 6), np.float32)
+    alloc = np.zeros((rounds, 3), np.float32)
+    lib().or_pp_refine(_p(pos), pos.shape[0], _p(lo), _p(hi), points, rounds, seed, obs_offset,
+                       pred_weight, _p(best), _p(value), _p(gap), _p(box), _p(alloc))
+    return dict(best=best, value=value, gap=gap, box=box, alloc=alloc)

@@ -368,3 +368,55 @@ void or_argmax_reservoir(const double* v, int64_t n, uint64_t seed, int64_t* bes
   *gap = (n > 1) ? top - second : 0.0;
   *n_ties = k;
 }
+
+/* Level l of G on [lo, hi]: lo + (hi - lo) l / (G - 1) in FP64, rounded to FP32. */
+static float refine_level(float lo, float hi, int l, int G) {
+  double w = (double)hi - (double)lo;
+  double t = (w * (double)l) / (double)(G - 1);
+  return (float)((double)lo + t);
+}
+
+void or_pp_refine(const float* pos, int32_t n_trials, const float lo0[3], const float hi0[3],
+                  int32_t G, int32_t R, uint64_t seed, double obs_offset, double pred_weight,
+                  int64_t* best, double* value, double* gap, float* box, float* alloc) {
+  float lo[3] = {lo0[0], lo0[1], lo0[2]};
+  float hi[3] = {hi0[0], hi0[1], hi0[2]};
+  const int64_t n_cand = (int64_t)G * G * G;
+  double* means = (double*)malloc(sizeof(double) * (size_t)n_cand);
+  float lv[3][64];
+  for (int32_t r = 0; r < R; ++r) {
+    /* the grid of this round */
+    for (int e = 0; e < 3; ++e) {
+      box[6 * r + e] = lo[e];
+      box[6 * r + 3 + e] = hi[e];
+      for (int l = 0; l < G; ++l) lv[e][l] = refine_level(lo[e], hi[e], l, G);
+    }
+    /* simulate every candidate; its noise stream is candidate r G^3 + c */
+    for (int64_t c = 0; c < n_cand; ++c) {
+      const int l2 = (int)(c % G), l1 = (int)((c / G) % G), l0 = (int)(c / ((int64_t)G * G));
+      const double a[3] = {(double)lv[0][l0], (double)lv[1][l1], (double)lv[2][l2]};
+      const uint32_t stream = (uint32_t)((int64_t)r * n_cand + c);
+      double sum = 0.0;
+      for (int32_t j = 0; j < n_trials; ++j)
+        sum += or_pp_outcome(pos + 6 * (size_t)j, a, seed, (uint32_t)j, stream, obs_offset,
+                             pred_weight, NULL);
+      means[c] = sum / (double)n_trials;
+    }
+    int64_t b;
+    or_argmax(means, n_cand, &b, &value[r], &gap[r]);
+    best[r] = b;
+    const int lb[3] = {(int)(b / ((int64_t)G * G)), (int)((b / G) % G), (int)(b % G)};
+    /* next box: the best point +- one grid spacing, inside the domain */
+    for (int e = 0; e < 3; ++e) {
+      const float center = lv[e][lb[e]];
+      alloc[3 * r + e] = center;
+      const double s = ((double)hi[e] - (double)lo[e]) / (double)(G - 1);
+      double nlo = (double)center - s, nhi = (double)center + s;
+      if (nlo < (double)lo0[e]) nlo = (double)lo0[e];
+      if (nhi > (double)hi0[e]) nhi = (double)hi0[e];
+      lo[e] = (float)nlo;
+      hi[e] = (float)nhi;
+    }
+  }
+  free(means);
+}

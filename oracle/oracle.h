@@ -23,6 +23,8 @@
  *     logistic range, stop-rule closed form.
  *   - Grid search: noise-free geometric limits, perception variance,
  *     candidate index layout, lowest-index argmax.
+ *   - Coarse-to-fine grid: round 0 equals the full grid search; noise-free
+ *     closed forms of the shrinking box; convergence to the known optimum.
  *   - Reservoir tie-break: a rank-based restatement (the last tied index whose
  *     draw accepts its rank), uniformity over the tie set, the no-tie case.
  */
@@ -168,6 +170,21 @@ void or_argmax(const double* v, int64_t n, int64_t* best, double* best_value, do
    equal to the maximum; gap as or_argmax (0 on a tie). */
 void or_argmax_reservoir(const double* v, int64_t n, uint64_t seed, int64_t* best,
                          double* best_value, double* gap, int64_t* n_ties);
+
+/* Coarse-to-fine grid search (the refinement of the prey-attention search of
+   Sec. 4.3, done by simulation instead of value-range analysis). Round r =
+   0..R-1 lays G points on each signal's interval [lo_e, hi_e]:
+   level l = lo + (hi - lo) l / (G - 1) (FP64, rounded to FP32); candidate
+   c = (l0 G + l1) G + l2 is simulated over n_trials trials exactly as in
+   or_pp_means but with noise stream (seed, trial, r G^3 + c); best = argmax
+   (lowest index on ties). The next interval of each signal is the best level
+   +- one grid spacing (hi - lo)/(G - 1), clipped to the domain [lo0, hi0]
+   (FP64, rounded to FP32), so it shrinks by 2/(G - 1) per round (G >= 4).
+   Outputs per round: best[r], value[r], gap[r], box[r][6] = (lo[3], hi[3])
+   of the round, alloc[r][3] = allocation of the best candidate. G <= 64. */
+void or_pp_refine(const float* pos, int32_t n_trials, const float lo0[3], const float hi0[3],
+                  int32_t G, int32_t R, uint64_t seed, double obs_offset, double pred_weight,
+                  int64_t* best, double* value, double* gap, float* box, float* alloc);
 
 #ifdef __cplusplus
 }
