@@ -40,6 +40,13 @@ WORKLOAD = ("hot-path pass: Stroop 4x1000 (weights seed 0) + DDM 2^20 + LCA 2621
 # algorithmic lane-operations per DDM trial-step (Philox4x32-10 quarter block,
 # one uniform and half a Box-Muller pair, the compensated update and the test)
 DDM_OPS_PER_TRIAL_STEP = 32
+# DRAM bytes (read + write) of one ddm_batched launch over the 2^20-trial job,
+# from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
+# -k regex:ddm_batched -s 1 -c 1 python bench.py --only ddm` on the current
+# kernel (profiles/ddm_batched_2p20_trials.md): 12,593,408 read + 0 written
+# (the 5 MB of outputs stay in L2 within the launch). Algorithmic: 8 B of
+# parameters in and 5 B out per trial = 13.6 MB.
+DDM_TRAFFIC_BYTES = 12_593_408
 LANES_PER_SM = 128
 WIDE_TRIALS = 16384
 
@@ -264,11 +271,12 @@ def cpu_baseline(seconds_hint=True):
     import oracle
     from paper_2110_15425_gb300 import workloads as W
     threads = os.cpu_count() or 1
-    frac = 4
+    frac = 1
+    wide_every = 2
     t0 = time.perf_counter()
     steps = 0
     s = W.stroop_small()
-    ids = np.arange(0, s["n_trials"], 8, dtype=np.uint32)
+    ids = np.arange(0, s["n_trials"], 1, dtype=np.uint32)
     o = oracle.transfer_run(s["layers"], s["projections"], s["cond_inputs"], s["cond_block"],
                             s["seed"], trial_ids=ids, threads=threads)
     steps += int(o["step"].sum())
@@ -282,7 +290,7 @@ def cpu_baseline(seconds_hint=True):
         o = oracle.lca_run(l["I"], l["seed"], trial_ids=ids, threads=threads)
         steps += int(o["step"].sum())
     wd = W.stroop_wide(n_trials=WIDE_TRIALS)
-    ids = np.arange(0, WIDE_TRIALS, frac * 4, dtype=np.uint32)
+    ids = np.arange(0, WIDE_TRIALS, wide_every, dtype=np.uint32)
     o = oracle.transfer_run(wd["layers"], wd["projections"], wd["cond_inputs"], 1, wd["seed"],
                             trial_ids=ids, threads=threads)
     steps += int(o["step"].sum())
@@ -291,8 +299,8 @@ def cpu_baseline(seconds_hint=True):
     oracle.pp_means(g["pos"], g["levels"], g["seed"], cand_ids=ids, threads=threads)
     steps += ids.shape[0] * g["pos"].shape[0]
     dt = time.perf_counter() - t0
-    sample = (f"every 8th Stroop trial, every {frac}th DDM/LCA trial and grid candidate, every "
-              f"{frac * 4}th wide trial: {steps} trial-steps in {dt:.1f} s")
+    sample = (f"the whole Stroop, DDM, LCA and grid jobs, every {wide_every}nd trial of the wide "
+              f"job: {steps} trial-steps in {dt:.1f} s")
     return steps / dt, threads, sample
 
 
@@ -493,7 +501,7 @@ def main():
     achieved = ddm_ops / (ddm_ms / 1000.0)
     roofline = {"bound": "alu", "kernel": "ddm_batched", "achieved": achieved / 1e12,
                 "peak": peak_ops / 1e12, "unit": "Tlane-op/s", "frac": achieved / peak_ops,
-                "traffic": None,
+                "traffic": DDM_TRAFFIC_BYTES, "traffic_unit": "bytes per launch",
                 "peak_source": f"{sms} SMs x {LANES_PER_SM} FP32/INT32 lanes x {sm_max:.0f} MHz "
                                f"({pk_kind} max SM clock)",
                 "ops_per_trial_step": DDM_OPS_PER_TRIAL_STEP, "dominant_in_pass": dominant}
