@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--profile-once", action="store_true",
                     help="run warmup + 1 step only (for ncu launch lists)")
     ap.add_argument("--only", default=None,
-                    choices=["ddm", "lca4", "lca8", "lca16", "grid", "stroop", "wide"],
+                    choices=["ddm", "lca4", "lca8", "lca16", "grid", "stroop", "wide", "refine"],
                     help="one job of this kind, default launch shape, 1 warm + 1 timed launch "
                          "(the small case for per-kernel ncu captures)")
     ap.add_argument("--n", type=int, default=0, help="trials (or candidates) for --only")
@@ -351,6 +351,14 @@ def run_only(args):
         pos = cuda(g["pos"])
         res = torch.zeros(3, dtype=torch.float64, device="cuda")
         go = lambda: B.dg_grid_search(m, B.grid_desc(lv, pos, g["seed"]), res)  # noqa: E731
+    elif k == "refine":
+        G, R = (args.n or 5), 7
+        g = W.predator_prey()
+        m = B.compose_predator_prey(ctx)
+        pos = cuda(g["pos"])
+        out = torch.zeros(64 * R, dtype=torch.uint8, device="cuda")
+        d = B.refine_desc(pos, [0, 0, 0], [1, 1, 1], G, R, g["seed"])
+        go = lambda: B.dg_grid_refine(m, d, out)  # noqa: E731
     else:
         if k == "ddm":
             w = W.ddm(n_trials=args.n or (1 << 20))

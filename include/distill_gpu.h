@@ -217,6 +217,44 @@ dg_status dg_run(dg_model* model, const dg_run_desc* desc, int8_t* choice, int32
 dg_status dg_grid_search(dg_model* model, const dg_grid_desc* desc, dg_grid_result* result,
                          double* cand_means, void* stream);
 
+/* Coarse-to-fine grid search: the refinement of the attention search in
+   Sec. 4.3 ("adaptive mesh refinement"), done by simulating the model instead
+   of by value-range analysis. Round r = 0 .. rounds-1 lays `points` (G) levels
+   on each signal's interval [lo_e, hi_e]: level l = lo + (hi - lo) l / (G - 1),
+   computed in FP64 and rounded to FP32. Its G^3 candidates c = (l0 G + l1) G + l2
+   are simulated and averaged exactly as dg_grid_search does, with the noise
+   stream of candidate r G^3 + c, and the best one (lowest index on exact ties)
+   is taken. The next interval of each signal is the best level +- one grid
+   spacing (hi - lo)/(G - 1), clipped to the domain (FP64, rounded to FP32): it
+   shrinks by 2/(G - 1) per round. R rounds simulate R G^3 candidates instead
+   of the (G-fold finer) full grid. */
+typedef struct {
+  int32_t points;             /* G: levels per signal in every round, 4 .. 64 */
+  int32_t rounds;             /* R >= 1, with R G^3 <= 2^32 */
+  int32_t n_trials;           /* noisy trials per candidate, 1 .. 1024 */
+  int32_t reserved;           /* 0 */
+  float lo[3], hi[3];         /* domain of each signal (player, predator, prey); lo <= hi */
+  const float* positions;     /* device, [n_trials][6] as in dg_grid_desc */
+  uint64_t seed;
+} dg_refine_desc;
+
+typedef struct {
+  float alloc[3];             /* allocation of the round's best candidate */
+  float lo[3], hi[3];         /* the round's interval of each signal */
+  int32_t round;              /* r */
+  int64_t best_index;         /* (l0 G + l1) G + l2 within the round */
+  double best_value;          /* FP64 mean outcome of the best candidate */
+  double runner_up_gap;       /* best - second best of the round (0 on a tie) */
+} dg_refine_round;
+
+/* Run a coarse-to-fine search on a PREDATOR_PREY model. rounds: device,
+   dg_refine_round[desc->rounds], written in order (entry rounds-1 holds the
+   answer). 1 + 2 R kernel launches, no host synchronisation (capturable).
+   Errors: DG_E_ARG (bad sizes, domain or pointers), DG_E_UNSUPPORTED (not a
+   PREDATOR_PREY model), DG_E_CUDA. */
+dg_status dg_grid_refine(dg_model* model, const dg_refine_desc* desc, dg_refine_round* rounds,
+                         void* stream);
+
 /* Argmax over n FP64 values (device), lowest index on exact ties, into a
    device dg_grid_result. n >= 1. */
 dg_status dg_argmax_f64(dg_ctx* ctx, const double* values, int64_t n, dg_grid_result* result,

@@ -65,6 +65,18 @@ class dg_grid_desc(C.Structure):
                 ("cand_count", C.c_int64)]
 
 
+class dg_refine_desc(C.Structure):
+    _fields_ = [("points", C.c_int32), ("rounds", C.c_int32), ("n_trials", C.c_int32),
+                ("reserved", C.c_int32), ("lo", C.c_float * 3), ("hi", C.c_float * 3),
+                ("positions", C.c_void_p), ("seed", C.c_uint64)]
+
+
+class dg_refine_round(C.Structure):
+    _fields_ = [("alloc", C.c_float * 3), ("lo", C.c_float * 3), ("hi", C.c_float * 3),
+                ("round", C.c_int32), ("best_index", C.c_int64), ("best_value", C.c_double),
+                ("runner_up_gap", C.c_double)]
+
+
 class dg_grid_result(C.Structure):
     _fields_ = [("best_index", C.c_int64), ("best_value", C.c_double),
                 ("runner_up_gap", C.c_double)]
@@ -88,7 +100,7 @@ EXPORTS = [
     "dg_normals", "dg_batch_create", "dg_batch_add_run", "dg_batch_add_grid",
     "dg_batch_launch", "dg_batch_free", "dg_submit", "dg_wait", "dg_serve_stats",
     "dg_grid_search_noalloc", "dg_stream_status", "dg_selftest_wait_timeout",
-    "dg_argmax_f64_reservoir",
+    "dg_argmax_f64_reservoir", "dg_grid_refine",
 ]
 
 _lib = None
@@ -125,6 +137,7 @@ def _declare(L):
         "dg_selftest_wait_timeout": [P, i32, P],
         "dg_argmax_f64": [P, P, i64, P, P],
         "dg_argmax_f64_reservoir": [P, P, i64, u64, P, P],
+        "dg_grid_refine": [P, C.POINTER(dg_refine_desc), P, P],
         "dg_philox_words": [u64, u32, u32, u32, u32, i64, P, P],
         "dg_normals": [u64, u32, u32, u64, i64, P, P],
         "dg_batch_create": [P, C.POINTER(P)],
@@ -231,6 +244,34 @@ def dg_stream_status(ctx, stream=None):
 def dg_argmax_f64(ctx, values, result, stream=None):
     check(lib().dg_argmax_f64(ctx, ptr(values), values.numel(), ptr(result),
                               stream_handle(stream)))
+
+
+def dg_grid_refine(model, desc, rounds, stream=None):
+    """rounds: device uint8 tensor of desc.rounds * 64 bytes (dg_refine_round[])."""
+    check(lib().dg_grid_refine(model, C.byref(desc), ptr(rounds), stream_handle(stream)))
+
+
+def refine_desc(positions, lo, hi, points, rounds, seed):
+    d = dg_refine_desc()
+    d._keep = positions
+    d.points = points
+    d.rounds = rounds
+    d.n_trials = positions.shape[0]
+    for i in range(3):
+        d.lo[i] = float(lo[i])
+        d.hi[i] = float(hi[i])
+    d.positions = positions.data_ptr()
+    d.seed = seed
+    return d
+
+
+def refine_rounds(raw):
+    """Decode dg_refine_round[] from host bytes into numpy arrays."""
+    import numpy as np
+    rec = np.dtype([("alloc", "<f4", 3), ("lo", "<f4", 3), ("hi", "<f4", 3), ("round", "<i4"),
+                    ("best_index", "<i8"), ("best_value", "<f8"), ("runner_up_gap", "<f8")])
+    assert rec.itemsize == C.sizeof(dg_refine_round) == 64
+    return np.frombuffer(np.ascontiguousarray(raw).tobytes(), dtype=rec)
 
 
 def dg_argmax_f64_reservoir(ctx, values, seed, result, stream=None):

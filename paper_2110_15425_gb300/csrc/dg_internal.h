@@ -135,6 +135,7 @@ struct GridParams {
   float offset, weight;
   long long cand0;               // global index of local candidate 0
   long long n_cand;              // candidates evaluated by this launch
+  uint32_t stream0;              // noise stream of candidate c is stream0 + c
   double* means;                 // [n_cand] local, may be null
   TopTwo* partials;              // scratch, one per block
   unsigned int* ticket;          // scratch, zeroed per launch
@@ -145,6 +146,21 @@ int grid_blocks(int mode, long long n_cand, int n_trials);
 
 cudaError_t launch_argmax(const double* v, long long n, TopTwo* partials, unsigned int* ticket,
                           void* result, cudaStream_t s);
+// ------------------------------------------------- coarse-to-fine grid ---
+constexpr int kRefineMaxPoints = 64;
+struct RefineParams {
+  float lo0[3], hi0[3];          // domain of each signal
+  int G;                         // points per signal per round
+  int R;                         // rounds
+  float* lv;                     // scratch [2][3][kRefineMaxPoints]: levels, double-buffered
+  void* rounds;                  // dg_refine_round[R]
+  unsigned int* ticket;          // the grid launch's argmax ticket, reset for the next round
+};
+// Levels and box of round 0.
+cudaError_t launch_refine_init(const RefineParams& p, cudaStream_t s);
+// After round r's grid launch: record the best allocation and lay out round r + 1.
+cudaError_t launch_refine_step(const RefineParams& p, int r, cudaStream_t s);
+
 // After an argmax into `result` over v[0..n) (global indices base..): replace
 // the lowest tied index by the reservoir-sampled one when the maximum is tied.
 cudaError_t launch_tie_reservoir(const double* v, long long n, long long base, uint64_t seed,

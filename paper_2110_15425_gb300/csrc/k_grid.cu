@@ -83,6 +83,7 @@ __device__ __forceinline__ void unit2(float vx, float vy, float& ox, float& oy) 
   }
 }
 
+// c: the candidate's noise stream
 __device__ __forceinline__ float pp_outcome(const GridParams& p, const float* pos, int j,
                                             uint32_t c, float sd0, float sd1, float sd2,
                                             float cost) {
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(256) grid_batched(GridParams p) {
     const float cost = a0 * a0 + a1 * a1 + a2 * a2;
     double acc = 0.0;
     for (int j = lane; j < p.n_trials; j += 32)
-      acc += (double)pp_outcome(p, pos, j, (uint32_t)cg, sd0, sd1, sd2, cost);
+      acc += (double)pp_outcome(p, pos, j, p.stream0 + (uint32_t)cg, sd0, sd1, sd2, cost);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
     const double mean = __shfl_sync(kFull, acc, 0) * inv;
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(256) grid_plain(GridParams p) {
   const float cost = a0 * a0 + a1 * a1 + a2 * a2;
   double acc = 0.0;
   for (int j = 0; j < p.n_trials; ++j)
-    acc += (double)pp_outcome(p, pos, j, (uint32_t)cg, sd0, sd1, sd2, cost);
+    acc += (double)pp_outcome(p, pos, j, p.stream0 + (uint32_t)cg, sd0, sd1, sd2, cost);
   p.means[c] = acc / (double)p.n_trials;
 }
 
@@ -276,6 +277,86 @@ __global__ void __launch_bounds__(1024) tie_reservoir(const double* v, long long
   }
 }
 
+// ------------------------------------------------- coarse-to-fine grid ---
+// The search-space refinement of Sec. 4.3, by simulation: round r lays G
+// points on each signal's interval, level l = lo + (hi - lo) l / (G - 1)
+// (FP64, rounded to FP32), simulates the G^3 candidates with noise streams
+// r G^3 + c (grid_batched with stream0 = r G^3), and centres the next
+// interval on the best level with half-width one grid spacing, clipped to the
+// domain. The explicit _rn intrinsics keep the FP64 steps unfused, as the
+// definition states them.
+
+struct RefineRoundDev {          // dg_refine_round
+  float alloc[3];
+  float lo[3];
+  float hi[3];
+  int round;
+  long long best_index;          // this and the next two: a dg_grid_result
+  double value;
+  double gap;
+};
+static_assert(sizeof(RefineRoundDev) == 64, "dg_refine_round layout");
+
+__device__ __forceinline__ float refine_level(float lo, float hi, int l, int G) {
+  const double w = __dsub_rn((double)hi, (double)lo);
+  const double t = __ddiv_rn(__dmul_rn(w, (double)l), (double)(G - 1));
+  return __double2float_rn(__dadd_rn((double)lo, t));
+}
+
+__device__ __forceinline__ void refine_layout(const RefineParams& p, const float* lo,
+                                              const float* hi, float* lv) {
+  const int l = threadIdx.x;
+  if (l < p.G)
+    for (int e = 0; e < 3; ++e) lv[e * kRefineMaxPoints + l] = refine_level(lo[e], hi[e], l, p.G);
+}
+
+__global__ void refine_init(RefineParams p) {
+  RefineRoundDev* rounds = reinterpret_cast<RefineRoundDev*>(p.rounds);
+  refine_layout(p, p.lo0, p.hi0, p.lv);
+  if (threadIdx.x == 0) {
+    for (int e = 0; e < 3; ++e) {
+      rounds[0].lo[e] = p.lo0[e];
+      rounds[0].hi[e] = p.hi0[e];
+    }
+    rounds[0].round = 0;
+    *p.ticket = 0u;
+  }
+}
+
+__global__ void refine_step(RefineParams p, int r) {
+  RefineRoundDev* rounds = reinterpret_cast<RefineRoundDev*>(p.rounds);
+  const float* cur = p.lv + (r & 1) * 3 * kRefineMaxPoints;
+  const int G = p.G;
+  long long b = rounds[r].best_index;
+  if (b < 0 || b >= (long long)G * G * G) b = 0;  // only after a failed round
+  const int lb[3] = {(int)(b / ((long long)G * G)), (int)((b / G) % G), (int)(b % G)};
+  float nlo[3], nhi[3];
+  for (int e = 0; e < 3; ++e) {
+    const float center = cur[e * kRefineMaxPoints + lb[e]];
+    const double lo = rounds[r].lo[e], hi = rounds[r].hi[e];
+    const double sp = __ddiv_rn(__dsub_rn(hi, lo), (double)(G - 1));
+    double a = __dsub_rn((double)center, sp), z = __dadd_rn((double)center, sp);
+    if (a < (double)p.lo0[e]) a = (double)p.lo0[e];
+    if (z > (double)p.hi0[e]) z = (double)p.hi0[e];
+    nlo[e] = __double2float_rn(a);
+    nhi[e] = __double2float_rn(z);
+  }
+  __syncthreads();  // every thread has read round r before round r + 1 is written
+  if (threadIdx.x == 0) {
+    for (int e = 0; e < 3; ++e) rounds[r].alloc[e] = cur[e * kRefineMaxPoints + lb[e]];
+    *p.ticket = 0u;
+  }
+  if (r + 1 >= p.R) return;
+  refine_layout(p, nlo, nhi, p.lv + ((r + 1) & 1) * 3 * kRefineMaxPoints);
+  if (threadIdx.x == 0) {
+    for (int e = 0; e < 3; ++e) {
+      rounds[r + 1].lo[e] = nlo[e];
+      rounds[r + 1].hi[e] = nhi[e];
+    }
+    rounds[r + 1].round = r + 1;
+  }
+}
+
 size_t grid_smem(const GridParams& p) {
   return sizeof(float) * (6 * (size_t)p.n_trials + p.L[0] + p.L[1] + p.L[2]);
 }
@@ -320,6 +401,16 @@ cudaError_t launch_grid(const GridParams& p, int mode, const LaunchCfg& cfg, cud
   const long long need = (p.n_cand + block / 32 - 1) / (block / 32);
   if (grid > need) grid = (int)need;
   grid_batched<<<grid, block, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_init(const RefineParams& p, cudaStream_t s) {
+  refine_init<<<1, kRefineMaxPoints, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_step(const RefineParams& p, int r, cudaStream_t s) {
+  refine_step<<<1, kRefineMaxPoints, 0, s>>>(p, r);
   return cudaGetLastError();
 }
 

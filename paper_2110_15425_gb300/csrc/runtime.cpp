@@ -62,7 +62,8 @@ enum ModelKind { K_DDM = 0, K_LCA = 1, K_NET = 2, K_WIDE = 3, K_PP = 4 };
 constexpr size_t kMaxPartials = dg::kMaxGridBlocks;
 constexpr size_t kSortOff = 256;
 constexpr size_t kScratchHead = kSortOff + 2 * dg::kSchedBuckets * sizeof(unsigned int) + 256;
-constexpr size_t kScratchBytes = kScratchHead + kMaxPartials * sizeof(dg::TopTwo);
+constexpr size_t kRefineOff = kScratchHead + kMaxPartials * sizeof(dg::TopTwo);
+constexpr size_t kScratchBytes = kRefineOff + 2 * 3 * dg::kRefineMaxPoints * sizeof(float);
 
 struct Scratch {
   unsigned char* base = nullptr;
@@ -76,6 +77,7 @@ struct Scratch {
   unsigned int* hist() { return reinterpret_cast<unsigned int*>(base + kSortOff); }
   unsigned int* bucket_cursor() { return hist() + dg::kSchedBuckets; }
   dg::TopTwo* partials() { return reinterpret_cast<dg::TopTwo*>(base + kScratchHead); }
+  float* refine_levels() { return reinterpret_cast<float*>(base + kRefineOff); }
 };
 
 struct Server;
@@ -1267,6 +1269,62 @@ dg_status dg_argmax_f64(dg_ctx* ctx, const double* values, int64_t n, dg_grid_re
   if (st != DG_OK) return st;
   DG_CUDA(cudaMemsetAsync(sc->ticket(), 0, 4, s));
   DG_CUDA(dg::launch_argmax(values, n, sc->partials(), sc->ticket(), result, s));
+  return DG_OK;
+}
+
+dg_status dg_grid_refine(dg_model* m, const dg_refine_desc* d, dg_refine_round* rounds,
+                         void* stream) {
+  if (!m || !d || !rounds) return fail(DG_E_ARG, "dg_grid_refine: null model, desc or rounds");
+  if (m->kind != K_PP)
+    return fail(DG_E_UNSUPPORTED, "dg_grid_refine: model is not a predator-prey model");
+  const int G = d->points, R = d->rounds;
+  if (G < 4 || G > dg::kRefineMaxPoints)
+    return fail(DG_E_ARG, "dg_grid_refine: points %d out of [4, %d]", G, dg::kRefineMaxPoints);
+  const long long n_cand = (long long)G * G * G;
+  if (R < 1 || (long long)R * n_cand > (1ll << 32))
+    return fail(DG_E_ARG, "dg_grid_refine: rounds %d out of [1, 2^32 / points^3]", R);
+  if (d->n_trials < 1 || d->n_trials > 1024)
+    return fail(DG_E_ARG, "dg_grid_refine: n_trials %d out of [1, 1024]", d->n_trials);
+  if (!d->positions) return fail(DG_E_ARG, "dg_grid_refine: null positions");
+  for (int e = 0; e < 3; ++e)
+    if (!std::isfinite(d->lo[e]) || !std::isfinite(d->hi[e]) || !(d->lo[e] <= d->hi[e]))
+      return fail(DG_E_ARG, "dg_grid_refine: domain of signal %d is not a finite lo <= hi", e);
+  DG_CUDA(cudaSetDevice(m->ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch* sc = nullptr;
+  dg_status st = get_scratch(m->ctx, s, &sc);
+  if (st != DG_OK) return st;
+  dg::RefineParams rp{};
+  for (int e = 0; e < 3; ++e) {
+    rp.lo0[e] = d->lo[e];
+    rp.hi0[e] = d->hi[e];
+  }
+  rp.G = G;
+  rp.R = R;
+  rp.lv = sc->refine_levels();
+  rp.rounds = rounds;
+  rp.ticket = sc->ticket();
+  dg::GridParams p{};
+  p.pos = d->positions;
+  p.n_trials = d->n_trials;
+  p.k0 = (uint32_t)d->seed;
+  p.k1 = (uint32_t)(d->seed >> 32);
+  p.offset = m->offset;
+  p.weight = m->weight;
+  p.cand0 = 0;
+  p.n_cand = n_cand;
+  p.partials = sc->partials();
+  p.ticket = sc->ticket();
+  for (int e = 0; e < 3; ++e) p.L[e] = G;
+  DG_CUDA(dg::launch_refine_init(rp, s));
+  for (int r = 0; r < R; ++r) {
+    for (int e = 0; e < 3; ++e) p.lv[e] = rp.lv + ((r & 1) * 3 + e) * dg::kRefineMaxPoints;
+    p.stream0 = (uint32_t)((long long)r * n_cand);
+    // the round's dg_grid_result fields (best_index, value, gap) sit at byte 40
+    p.result = reinterpret_cast<unsigned char*>(rounds + r) + offsetof(dg_refine_round, best_index);
+    DG_CUDA(dg::launch_grid(p, DG_MODE_BATCHED, dg::LaunchCfg{}, s));
+    DG_CUDA(dg::launch_refine_step(rp, r, s));
+  }
   return DG_OK;
 }
 
