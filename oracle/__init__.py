@@ -99,6 +99,9 @@ def _bind(L):
                               C.c_int64, C.c_uint64, C.c_double, C.c_double, P]
     L.or_argmax.argtypes = [P, C.c_int64, P, P, P]
     L.or_argmax_reservoir.argtypes = [P, C.c_int64, C.c_uint64, P, P, P, P]
+    L.or_pp_episode.argtypes = [P, C.c_uint32, P, C.c_int32, P, C.c_int32, P, C.c_int32,
+                                C.c_int32, C.c_int32, C.c_uint64, C.c_double, C.c_double, P,
+                                C.c_double, P, P, P, P, P, P, P, P]
     L.or_pp_refine.argtypes = [P, C.c_int32, P, P, C.c_int32, C.c_int32, C.c_uint64, C.c_double,
                                C.c_double, P, P, P, P, P]
     return L
@@ -340,3 +343,40 @@ def pp_refine(pos, lo, hi, points, rounds, seed, obs_offset=0.1, pred_weight=0.5
     lib().or_pp_refine(_p(pos), pos.shape[0], _p(lo), _p(hi), points, rounds, seed, obs_offset,
                        pred_weight, _p(best), _p(value), _p(gap), _p(box), _p(alloc))
     return dict(best=best, value=value, gap=gap, box=box, alloc=alloc)
+
+
+def pp_episodes(start, levels, n_trials, max_steps, seed, episode_ids=None, obs_offset=0.1,
+                pred_weight=0.5, speed=(1.0, 0.6, 0.5), radius=1.0, threads=1):
+    """Time-stepped predator-prey episodes (Sec. 2.1), one per row of start
+    [E][6] (episode id = row, or episode_ids). Returns outcome, steps, final
+    positions and per-step trajectories (best index, its mean, gap, positions,
+    capture margin; -1 / nan after the end)."""
+    start = _c(start, np.float32)
+    lv = [_c(l, np.float32) for l in levels]
+    E = start.shape[0]
+    ids = np.arange(E, dtype=np.uint32) if episode_ids is None else _c(episode_ids, np.uint32)
+    sp = _c(speed, np.float64)
+    outc = np.zeros(E, np.int8)
+    steps = np.zeros(E, np.int32)
+    fin = np.zeros((E, 6), np.float32)
+    best = np.full((E, max_steps), -1, np.int64)
+    gap = np.full((E, max_steps), np.nan)
+    val = np.full((E, max_steps), np.nan)
+    pos = np.full((E, max_steps, 6), np.nan, np.float32)
+    marg = np.full((E, max_steps), np.nan)
+    L = lib()
+
+    def run(lo, hi):
+        for k in range(lo, hi):
+            o = C.c_int8()
+            s = C.c_int32()
+            L.or_pp_episode(_p(start[k]), int(ids[k]), _p(lv[0]), lv[0].shape[0], _p(lv[1]),
+                            lv[1].shape[0], _p(lv[2]), lv[2].shape[0], n_trials, max_steps, seed,
+                            obs_offset, pred_weight, _p(sp), radius, C.byref(o), C.byref(s),
+                            _p(fin[k]), _p(best[k]), _p(val[k]), _p(gap[k]), _p(pos[k]),
+                            _p(marg[k]))
+            outc[k] = o.value
+            steps[k] = s.value
+    _threaded(run, E, threads)
+    return dict(outcome=outc, steps=steps, final=fin, best=best, value=val, gap=gap, pos=pos,
+                margin=marg)

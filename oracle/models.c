@@ -14,6 +14,7 @@
 typedef struct {
   uint64_t seed;
   uint32_t trial, cand;
+  uint32_t block0; /* block of normal 0 (episodes give each episode its own blocks) */
   int64_t block;
   double z[4];
 } noise_stream;
@@ -22,6 +23,7 @@ static void noise_open(noise_stream* s, uint64_t seed, uint32_t trial, uint32_t 
   s->seed = seed;
   s->trial = trial;
   s->cand = cand;
+  s->block0 = 0u;
   s->block = -1;
 }
 
@@ -29,7 +31,7 @@ static double noise_at(noise_stream* s, uint64_t d) {
   int64_t block = (int64_t)(d >> 2);
   if (block != s->block) {
     uint32_t w[4];
-    or_philox_words(s->seed, s->trial, s->cand, 0u, (uint32_t)block, 1, w);
+    or_philox_words(s->seed, s->trial, s->cand, 0u, s->block0 + (uint32_t)block, 1, w);
     or_box_muller(w, s->z);
     s->block = block;
   }
@@ -285,11 +287,15 @@ static void unit2(double vx, double vy, double* ox, double* oy) {
   }
 }
 
-double or_pp_outcome(const float pos[6], const double a[3], uint64_t seed, uint32_t trial,
-                     uint32_t cand, double obs_offset, double pred_weight, double* perceived) {
+/* Perceived positions X^_e = X_e + eps_{2e+c} / (obs_offset + a_e) with the
+   normals of stream (seed, trial, cand) starting at block block0, and the
+   Action node's unit step act = unit(unit(Y^ - P^) - w unit(D^ - P^)). */
+static void pp_perceive_act(const float pos[6], const double a[3], uint64_t seed,
+                            uint32_t trial, uint32_t cand, uint32_t block0, double obs_offset,
+                            double pred_weight, double ph[6], double* ax, double* ay) {
   noise_stream ns;
   noise_open(&ns, seed, trial, cand);
-  double ph[6];
+  ns.block0 = block0;
   for (int e = 0; e < 3; ++e) {
     double sd = 1.0 / (obs_offset + a[e]);
     for (int c = 0; c < 2; ++c) {
@@ -297,17 +303,31 @@ double or_pp_outcome(const float pos[6], const double a[3], uint64_t seed, uint3
       ph[d] = (double)pos[d] + sd * noise_at(&ns, (uint64_t)d);
     }
   }
-  if (perceived)
-    for (int d = 0; d < 6; ++d) perceived[d] = ph[d];
-  /* entity order: player (0,1), predator (2,3), prey (4,5) */
-  double uyx, uyy, udx, udy, ax, ay;
+  double uyx, uyy, udx, udy;
   unit2(ph[4] - ph[0], ph[5] - ph[1], &uyx, &uyy);
   unit2(ph[2] - ph[0], ph[3] - ph[1], &udx, &udy);
-  unit2(uyx - pred_weight * udx, uyy - pred_weight * udy, &ax, &ay);
+  unit2(uyx - pred_weight * udx, uyy - pred_weight * udy, ax, ay);
+}
+
+/* Objective node: -|P + act - Y| - sum_e a_e^2 with true P, Y. */
+static double pp_outcome_b(const float pos[6], const double a[3], uint64_t seed,
+                           uint32_t trial, uint32_t cand, uint32_t block0, double obs_offset,
+                           double pred_weight) {
+  double ph[6], ax, ay;
+  pp_perceive_act(pos, a, seed, trial, cand, block0, obs_offset, pred_weight, ph, &ax, &ay);
   double nx = (double)pos[0] + ax - (double)pos[4];
   double ny = (double)pos[1] + ay - (double)pos[5];
   double cost = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
   return -sqrt(nx * nx + ny * ny) - cost;
+}
+
+double or_pp_outcome(const float pos[6], const double a[3], uint64_t seed, uint32_t trial,
+                     uint32_t cand, double obs_offset, double pred_weight, double* perceived) {
+  if (perceived) {
+    double ax, ay;
+    pp_perceive_act(pos, a, seed, trial, cand, 0u, obs_offset, pred_weight, perceived, &ax, &ay);
+  }
+  return pp_outcome_b(pos, a, seed, trial, cand, 0u, obs_offset, pred_weight);
 }
 
 void or_pp_means(const float* pos, int32_t n_trials, const float* lv0, int32_t L0,
@@ -418,5 +438,75 @@ void or_pp_refine(const float* pos, int32_t n_trials, const float lo0[3], const 
       hi[e] = (float)nhi;
     }
   }
+  free(means);
+}
+
+void or_pp_episode(const float start[6], uint32_t episode, const float* lv0, int32_t L0,
+                   const float* lv1, int32_t L1, const float* lv2, int32_t L2, int32_t n_trials,
+                   int32_t max_steps, uint64_t seed, double obs_offset, double pred_weight,
+                   const double speed[3], double radius, int8_t* outcome, int32_t* steps,
+                   float final_pos[6], int64_t* traj_best, double* traj_value,
+                   double* traj_gap, float* traj_pos, double* traj_margin) {
+  const int64_t n_cand = (int64_t)L0 * L1 * L2;
+  double* means = (double*)malloc(sizeof(double) * (size_t)n_cand);
+  float S[6];
+  for (int d = 0; d < 6; ++d) S[d] = start[d];
+  const uint32_t block0 = 2u * episode;
+  int8_t out = 0;
+  int32_t t = 0;
+  for (t = 0; t < max_steps; ++t) {
+    /* Control: simulate every allocation on n_trials perceptions of the
+       current positions (Sec. 2.1) and keep the best */
+    for (int64_t c = 0; c < n_cand; ++c) {
+      const int l2 = (int)(c % L2), l1 = (int)((c / L2) % L1), l0 = (int)(c / ((int64_t)L2 * L1));
+      const double a[3] = {(double)lv0[l0], (double)lv1[l1], (double)lv2[l2]};
+      double sum = 0.0;
+      for (int32_t j = 0; j < n_trials; ++j)
+        sum += pp_outcome_b(S, a, seed, (uint32_t)t * (uint32_t)n_trials + (uint32_t)j,
+                            (uint32_t)c, block0, obs_offset, pred_weight);
+      means[c] = sum / (double)n_trials;
+    }
+    int64_t b;
+    double bv, gap;
+    or_argmax(means, n_cand, &b, &bv, &gap);
+    const int l2 = (int)(b % L2), l1 = (int)((b / L2) % L1), l0 = (int)(b / ((int64_t)L2 * L1));
+    const double a[3] = {(double)lv0[l0], (double)lv1[l1], (double)lv2[l2]};
+    /* Act: one more perception with the chosen allocation moves the player;
+       the predator steps toward the player, the prey away from it */
+    double ph[6], ax, ay, ux, uy, vx, vy;
+    pp_perceive_act(S, a, seed, (uint32_t)t, 0xFFFFFFFFu, block0, obs_offset, pred_weight, ph,
+                    &ax, &ay);
+    unit2((double)S[0] - (double)S[2], (double)S[1] - (double)S[3], &ux, &uy);
+    unit2((double)S[4] - (double)S[0], (double)S[5] - (double)S[1], &vx, &vy);
+    float N[6];
+    N[0] = (float)((double)S[0] + speed[0] * ax);
+    N[1] = (float)((double)S[1] + speed[0] * ay);
+    N[2] = (float)((double)S[2] + speed[1] * ux);
+    N[3] = (float)((double)S[3] + speed[1] * uy);
+    N[4] = (float)((double)S[4] + speed[2] * vx);
+    N[5] = (float)((double)S[5] + speed[2] * vy);
+    for (int d = 0; d < 6; ++d) S[d] = N[d];
+    const double py = sqrt(((double)S[0] - S[4]) * ((double)S[0] - S[4]) +
+                           ((double)S[1] - S[5]) * ((double)S[1] - S[5]));
+    const double pd = sqrt(((double)S[0] - S[2]) * ((double)S[0] - S[2]) +
+                           ((double)S[1] - S[3]) * ((double)S[1] - S[3]));
+    if (traj_best) traj_best[t] = b;
+    if (traj_value) traj_value[t] = bv;
+    if (traj_gap) traj_gap[t] = gap;
+    if (traj_pos)
+      for (int d = 0; d < 6; ++d) traj_pos[6 * (size_t)t + d] = S[d];
+    if (traj_margin) traj_margin[t] = fmin(fabs(py - radius), fabs(pd - radius));
+    if (py <= radius) {
+      out = 1;
+      break;
+    }
+    if (pd <= radius) {
+      out = -1;
+      break;
+    }
+  }
+  *outcome = out;
+  *steps = (t < max_steps) ? t + 1 : max_steps;
+  for (int d = 0; d < 6; ++d) final_pos[d] = S[d];
   free(means);
 }

@@ -25,6 +25,8 @@
  *     candidate index layout, lowest-index argmax.
  *   - Coarse-to-fine grid: round 0 equals the full grid search; noise-free
  *     closed forms of the shrinking box; convergence to the known optimum.
+ *   - Episodes: one step equals the grid search on the start positions; the
+ *     moves' geometry (pursuit, evasion, unit steps); capture rules.
  *   - Reservoir tie-break: a rank-based restatement (the last tied index whose
  *     draw accepts its rank), uniformity over the tie set, the no-tie case.
  */
@@ -185,6 +187,32 @@ void or_argmax_reservoir(const double* v, int64_t n, uint64_t seed, int64_t* bes
 void or_pp_refine(const float* pos, int32_t n_trials, const float lo0[3], const float hi0[3],
                   int32_t G, int32_t R, uint64_t seed, double obs_offset, double pred_weight,
                   int64_t* best, double* value, double* gap, float* box, float* alloc);
+
+/* One time-stepped predator-prey episode (Sec. 2.1: the search over
+   allocations is repeated at every time step until the prey or the player is
+   caught). State S = (P, D, Y) in FP32. At step t = 0, 1, ...:
+     - every candidate allocation c (layout as or_pp_means) is simulated on
+       n_trials perceptions of the current S, perception noise from stream
+       (seed, trial t n_trials + j, cand c) at Philox blocks 2 episode + {0, 1};
+       FP64 mean; best = argmax (lowest index on ties);
+     - the player perceives S once more with the best allocation (stream
+       (seed, t, 0xFFFFFFFF), same blocks) and moves by speed[0] act; the
+       predator moves speed[1] unit(P - D) toward the player and the prey
+       speed[2] unit(Y - P) away from it, all from the positions at the start
+       of the step (FP64, rounded to FP32);
+     - with the new positions, |P - Y| <= radius ends the episode with
+       outcome +1 (prey caught), else |P - D| <= radius with -1 (player
+       caught); after max_steps steps without either, outcome 0.
+   steps = steps taken. Per step t (may be NULL): traj_best[t], its mean
+   traj_value[t], the runner-up gap traj_gap[t], positions after the step
+   traj_pos[t][6], and
+   traj_margin[t] = min(| |P-Y| - radius |, | |P-D| - radius |). */
+void or_pp_episode(const float start[6], uint32_t episode, const float* lv0, int32_t L0,
+                   const float* lv1, int32_t L1, const float* lv2, int32_t L2, int32_t n_trials,
+                   int32_t max_steps, uint64_t seed, double obs_offset, double pred_weight,
+                   const double speed[3], double radius, int8_t* outcome, int32_t* steps,
+                   float final_pos[6], int64_t* traj_best, double* traj_value,
+                   double* traj_gap, float* traj_pos, double* traj_margin);
 
 #ifdef __cplusplus
 }

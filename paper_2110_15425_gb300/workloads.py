@@ -140,3 +140,16 @@ def predator_prey(n_trials: int = 64, levels: int = 30, pos_seed: int = 3, noise
     lv = (np.arange(levels, dtype=np.float64) / (levels - 1)).astype(F32)
     return dict(pos=pos, levels=[lv.copy(), lv.copy(), lv.copy()], obs_offset=0.1,
                 pred_weight=0.5, seed=noise_seed)
+
+
+def predator_prey_episodes(n_episodes: int = 64, levels: int = 30, n_trials: int = 64,
+                           max_steps: int = 100, pos_seed: int = 21, noise_seed: int = 23):
+    """Start positions of time-stepped episodes: player, predator and prey
+    uniform on [-10, 10]^2; the same allocation levels as the grid search.
+    Player steps 1.0, predator 0.6, prey 0.5 per time step; capture radius 1."""
+    rng = _rng(pos_seed)
+    start = _u(rng, -10.0, 10.0, (n_episodes, 6))
+    lv = (np.arange(levels, dtype=np.float64) / (levels - 1)).astype(F32)
+    return dict(start=start, levels=[lv.copy(), lv.copy(), lv.copy()], n_trials=n_trials,
+                max_steps=max_steps, obs_offset=0.1, pred_weight=0.5, speed=(1.0, 0.6, 0.5),
+                radius=1.0, seed=noise_seed)
