@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--profile-once", action="store_true",
                     help="run warmup + 1 step only (for ncu launch lists)")
     ap.add_argument("--only", default=None,
-                    choices=["ddm", "lca4", "lca8", "lca16", "grid", "stroop", "wide", "refine"],
+                    choices=["ddm", "lca4", "lca8", "lca16", "grid", "stroop", "wide", "refine",
+                             "episodes"],
                     help="one job of this kind, default launch shape, 1 warm + 1 timed launch "
                          "(the small case for per-kernel ncu captures)")
     ap.add_argument("--n", type=int, default=0, help="trials (or candidates) for --only")
@@ -351,6 +352,16 @@ def run_only(args):
         pos = cuda(g["pos"])
         res = torch.zeros(3, dtype=torch.float64, device="cuda")
         go = lambda: B.dg_grid_search(m, B.grid_desc(lv, pos, g["seed"]), res)  # noqa: E731
+    elif k == "episodes":
+        w = W.predator_prey_episodes(n_episodes=args.n or 64)
+        m = B.compose_predator_prey(ctx)
+        E, T = w["start"].shape[0], w["max_steps"]
+        d = B.episode_desc([cuda(x) for x in w["levels"]], cuda(w["start"]), w["n_trials"], T,
+                           w["seed"], speed=w["speed"], radius=w["radius"])
+        oc = torch.zeros(E, dtype=torch.int8, device="cuda")
+        st = torch.zeros(E, dtype=torch.int32, device="cuda")
+        o = B.episode_out(oc, st)
+        go = lambda: B.dg_run_episodes(m, d, o)  # noqa: E731
     elif k == "refine":
         G, R = (args.n or 5), 7
         g = W.predator_prey()

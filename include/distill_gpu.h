@@ -217,6 +217,54 @@ dg_status dg_run(dg_model* model, const dg_run_desc* desc, int8_t* choice, int32
 dg_status dg_grid_search(dg_model* model, const dg_grid_desc* desc, dg_grid_result* result,
                          double* cand_means, void* stream);
 
+/* Time-stepped predator-prey episodes (Sec. 2.1: the whole search over
+   allocations is repeated at every time step until the prey or the player is
+   caught; the positions carried between steps are the sequential state of
+   Sec. 2.1 that caps the parallelism of such models). Episode e starts from
+   start[e] = (player xy, predator xy, prey xy). At step t = 0, 1, ...:
+     - every allocation c (layout as dg_grid_search) is simulated on n_trials
+       perceptions of the current positions, noise stream (trial t n_trials + j,
+       cand c) at Philox blocks 2e and 2e + 1; FP64 mean; best = argmax
+       (lowest index on exact ties);
+     - the player perceives once more with the best allocation (stream
+       (trial t, cand 0xFFFFFFFF), same blocks) and moves speed[0] times the
+       Action node's unit step; the predator moves speed[1] unit(P - D) toward
+       the player and the prey speed[2] unit(Y - P) away from it, all from the
+       positions at the start of the step (FP32);
+     - then |P - Y| <= radius ends the episode with +1 (prey caught), else
+       |P - D| <= radius with -1 (player caught); after max_steps steps, 0. */
+typedef struct {
+  int32_t n_episodes;         /* E >= 1 */
+  int32_t max_steps;          /* T >= 1, with T n_trials <= 2^32 */
+  int32_t n_levels[3];        /* levels per signal, 1 .. 4096 */
+  int32_t n_trials;           /* perceptions per candidate and step, 1 .. 1024 */
+  const float* levels[3];     /* device, allocation values of each signal */
+  const float* start;         /* device, [E][6] start positions */
+  uint64_t seed;
+  float speed[3];             /* step lengths of player, predator, prey (>= 0) */
+  float capture_radius;       /* >= 0 */
+} dg_episode_desc;
+
+/* Outputs of dg_run_episodes (device pointers, caller-owned). */
+typedef struct {
+  int8_t* outcome;            /* [E] +1 prey caught, -1 player caught, 0 none by T */
+  int32_t* steps;             /* [E] steps taken (the capture step, or T) */
+  float* final_pos;           /* [E][6] positions at the end, or NULL */
+  int32_t* best;              /* [E][T] best candidate of each step, -1 after the end, or NULL */
+  double* value;              /* [E][T] its FP64 mean outcome (0 after the end), or NULL */
+  float* pos;                 /* [E][T][6] positions after each step (0 after the end), or NULL */
+} dg_episode_out;
+
+/* Run E episodes of a PREDATOR_PREY model side by side: 1 + T kernel launches
+   (one per time step over the episodes still running), no host
+   synchronisation. Episodes are independent: an episode's results depend on
+   its index and start only. The first call on a stream with a given E x
+   candidates size allocates scratch (not inside stream capture).
+   Errors: DG_E_ARG, DG_E_UNSUPPORTED (not a PREDATOR_PREY model), DG_E_STATE
+   (first use inside capture), DG_E_CUDA. */
+dg_status dg_run_episodes(dg_model* model, const dg_episode_desc* desc, const dg_episode_out* out,
+                          void* stream);
+
 /* Coarse-to-fine grid search: the refinement of the attention search in
    Sec. 4.3 ("adaptive mesh refinement"), done by simulating the model instead
    of by value-range analysis. Round r = 0 .. rounds-1 lays `points` (G) levels

@@ -65,6 +65,18 @@ class dg_grid_desc(C.Structure):
                 ("cand_count", C.c_int64)]
 
 
+class dg_episode_desc(C.Structure):
+    _fields_ = [("n_episodes", C.c_int32), ("max_steps", C.c_int32),
+                ("n_levels", C.c_int32 * 3), ("n_trials", C.c_int32),
+                ("levels", C.c_void_p * 3), ("start", C.c_void_p), ("seed", C.c_uint64),
+                ("speed", C.c_float * 3), ("capture_radius", C.c_float)]
+
+
+class dg_episode_out(C.Structure):
+    _fields_ = [("outcome", C.c_void_p), ("steps", C.c_void_p), ("final_pos", C.c_void_p),
+                ("best", C.c_void_p), ("value", C.c_void_p), ("pos", C.c_void_p)]
+
+
 class dg_refine_desc(C.Structure):
     _fields_ = [("points", C.c_int32), ("rounds", C.c_int32), ("n_trials", C.c_int32),
                 ("reserved", C.c_int32), ("lo", C.c_float * 3), ("hi", C.c_float * 3),
@@ -100,7 +112,7 @@ EXPORTS = [
     "dg_normals", "dg_batch_create", "dg_batch_add_run", "dg_batch_add_grid",
     "dg_batch_launch", "dg_batch_free", "dg_submit", "dg_wait", "dg_serve_stats",
     "dg_grid_search_noalloc", "dg_stream_status", "dg_selftest_wait_timeout",
-    "dg_argmax_f64_reservoir", "dg_grid_refine",
+    "dg_argmax_f64_reservoir", "dg_grid_refine", "dg_run_episodes",
 ]
 
 _lib = None
@@ -138,6 +150,7 @@ def _declare(L):
         "dg_argmax_f64": [P, P, i64, P, P],
         "dg_argmax_f64_reservoir": [P, P, i64, u64, P, P],
         "dg_grid_refine": [P, C.POINTER(dg_refine_desc), P, P],
+        "dg_run_episodes": [P, C.POINTER(dg_episode_desc), C.POINTER(dg_episode_out), P],
         "dg_philox_words": [u64, u32, u32, u32, u32, i64, P, P],
         "dg_normals": [u64, u32, u32, u64, i64, P, P],
         "dg_batch_create": [P, C.POINTER(P)],
@@ -244,6 +257,34 @@ def dg_stream_status(ctx, stream=None):
 def dg_argmax_f64(ctx, values, result, stream=None):
     check(lib().dg_argmax_f64(ctx, ptr(values), values.numel(), ptr(result),
                               stream_handle(stream)))
+
+
+def episode_desc(levels, start, n_trials, max_steps, seed, speed=(1.0, 0.6, 0.5), radius=1.0):
+    d = dg_episode_desc()
+    d._keep = (tuple(levels), start)
+    d.n_episodes = start.shape[0]
+    d.max_steps = max_steps
+    d.n_trials = n_trials
+    for i in range(3):
+        d.n_levels[i] = levels[i].numel()
+        d.levels[i] = levels[i].data_ptr()
+        d.speed[i] = float(speed[i])
+    d.start = start.data_ptr()
+    d.seed = seed
+    d.capture_radius = float(radius)
+    return d
+
+
+def episode_out(outcome, steps, final_pos=None, best=None, value=None, pos=None):
+    o = dg_episode_out()
+    o._keep = (outcome, steps, final_pos, best, value, pos)
+    o.outcome, o.steps = ptr(outcome), ptr(steps)
+    o.final_pos, o.best, o.value, o.pos = ptr(final_pos), ptr(best), ptr(value), ptr(pos)
+    return o
+
+
+def dg_run_episodes(model, desc, out, stream=None):
+    check(lib().dg_run_episodes(model, C.byref(desc), C.byref(out), stream_handle(stream)))
 
 
 def dg_grid_refine(model, desc, rounds, stream=None):

@@ -1,0 +1,96 @@
+// Device helpers shared by the predator-prey kernels (grid search, episodes):
+// running top-2 argmax summaries and one evaluation of the model (Sec. 2.1).
+#pragma once
+
+#include <cfloat>
+#include <climits>
+
+#include "dg_device.cuh"
+#include "dg_internal.h"
+
+namespace dg {
+
+struct GridResultDev {           // dg_grid_result
+  long long best_index;
+  double best_value;
+  double gap;
+};
+
+__device__ __forceinline__ TopTwo top_init() { return TopTwo{-DBL_MAX, LLONG_MAX, -DBL_MAX}; }
+
+// Merge two running top-2 summaries: best value with lowest index on ties,
+// and the largest value among the rest.
+__device__ __forceinline__ TopTwo top_merge(TopTwo a, TopTwo b) {
+  const bool b_wins = (b.v1 > a.v1) || (b.v1 == a.v1 && b.i1 < a.i1);
+  TopTwo r;
+  if (b_wins) {
+    r.v1 = b.v1;
+    r.i1 = b.i1;
+    r.v2 = fmax(a.v1, b.v2);
+  } else {
+    r.v1 = a.v1;
+    r.i1 = a.i1;
+    r.v2 = fmax(b.v1, a.v2);
+  }
+  return r;
+}
+
+__device__ __forceinline__ TopTwo top_shfl(TopTwo t, int src, unsigned mask = kFull) {
+  TopTwo r;
+  r.v1 = __shfl_sync(mask, t.v1, src);
+  r.i1 = __shfl_sync(mask, t.i1, src);
+  r.v2 = __shfl_sync(mask, t.v2, src);
+  return r;
+}
+
+__device__ __forceinline__ TopTwo top_warp(TopTwo t) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t = top_merge(t, top_shfl(t, (threadIdx.x & 31) ^ o));
+  return t;
+}
+
+// unit(v), with unit(0) = 0
+__device__ __forceinline__ void unit2(float vx, float vy, float& ox, float& oy) {
+  const float n2 = vx * vx + vy * vy;
+  if (n2 > 0.f) {
+    const float r = rsqrtf(n2);
+    ox = vx * r;
+    oy = vy * r;
+  } else {
+    ox = 0.f;
+    oy = 0.f;
+  }
+}
+
+// Perception and Action nodes: X^_e = X_e + sd_e eps_{2e+c} (normals 0..5 of
+// stream (trial, cand) starting at Philox block block0), then
+// act = unit(unit(Y^ - P^) - weight unit(D^ - P^)).
+__device__ __forceinline__ void pp_act(uint32_t k0, uint32_t k1, uint32_t trial, uint32_t cand,
+                                       uint32_t block0, const float* X, float sd0, float sd1,
+                                       float sd2, float weight, float& ax, float& ay) {
+  const float4 z = normals4(noise_block(k0, k1, trial, cand, block0));
+  const uint4 w1 = noise_block(k0, k1, trial, cand, block0 + 1u);
+  float z4, z5;
+  box_muller(w1.x, w1.y, z4, z5);
+  const float phx = fmaf(sd0, z.x, X[0]), phy = fmaf(sd0, z.y, X[1]);
+  const float dhx = fmaf(sd1, z.z, X[2]), dhy = fmaf(sd1, z.w, X[3]);
+  const float yhx = fmaf(sd2, z4, X[4]), yhy = fmaf(sd2, z5, X[5]);
+  float uyx, uyy, udx, udy;
+  unit2(yhx - phx, yhy - phy, uyx, uyy);
+  unit2(dhx - phx, dhy - phy, udx, udy);
+  unit2(fmaf(-weight, udx, uyx), fmaf(-weight, udy, uyy), ax, ay);
+}
+
+// Objective node: -|P + act - Y| - sum_e a_e^2 (cost given), true P and Y.
+__device__ __forceinline__ float pp_outcome_at(uint32_t k0, uint32_t k1, uint32_t trial,
+                                               uint32_t cand, uint32_t block0, const float* X,
+                                               float sd0, float sd1, float sd2, float weight,
+                                               float cost) {
+  float ax, ay;
+  pp_act(k0, k1, trial, cand, block0, X, sd0, sd1, sd2, weight, ax, ay);
+  const float nx = (X[0] + ax) - X[4];
+  const float ny = (X[1] + ay) - X[5];
+  return -sqrtf(nx * nx + ny * ny) - cost;
+}
+
+}  // namespace dg

@@ -146,6 +146,36 @@ int grid_blocks(int mode, long long n_cand, int n_trials);
 
 cudaError_t launch_argmax(const double* v, long long n, TopTwo* partials, unsigned int* ticket,
                           void* result, cudaStream_t s);
+// --------------------------------------------- predator-prey episodes ---
+constexpr int kEpisodeChunk = 64;   // candidates per work item (8 warps x 8)
+struct EpisodeParams {
+  const float* lv[3];
+  int L[3];
+  long long n_cand;
+  int cpe;                       // work items (candidate chunks) per episode
+  int n_trials;
+  uint32_t k0, k1;
+  float offset, weight;
+  float speed[3];                // player, predator, prey
+  float radius;
+  int E, T;                      // episodes, maximum steps
+  int t;                         // the step a launch performs
+  const float* start;            // [E][6]
+  float* state;                  // [E][6] positions at the start of the step
+  int* active;                   // [3][E] active episode lists, rotating by step
+  int* count;                    // [3] list lengths
+  unsigned int* ticket;          // [E] finished work items of the step
+  TopTwo* partials;              // [E][cpe]
+  int8_t* outcome;               // [E]
+  int32_t* steps;                // [E]
+  float* final_pos;              // [E][6] or null
+  int32_t* traj_best;            // [E][T] or null
+  double* traj_value;            // [E][T] or null
+  float* traj_pos;               // [E][T][6] or null
+};
+cudaError_t launch_episode_init(const EpisodeParams& p, cudaStream_t s);
+cudaError_t launch_episode_step(const EpisodeParams& p, cudaStream_t s);
+
 // ------------------------------------------------- coarse-to-fine grid ---
 constexpr int kRefineMaxPoints = 64;
 struct RefineParams {

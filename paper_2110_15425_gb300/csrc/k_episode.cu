@@ -1,0 +1,197 @@
+// Time-stepped predator-prey episodes (Sec. 2.1: the search over attention
+// allocations is repeated at every time step until the prey or the player is
+// caught; the positions carried from step to step are the sequential outer
+// state that caps the parallelism of such models).
+//
+// Episode e keeps its positions S = (P, D, Y) in device memory. Step t:
+//   - every allocation c is simulated on n_trials perceptions of S (noise
+//     stream (trial t n_trials + j, cand c), Philox blocks 2e and 2e + 1), FP64
+//     mean, best = argmax (lowest index on ties);
+//   - the player perceives S once more with the best allocation (stream
+//     (trial t, cand 0xFFFFFFFF)) and moves speed[0] act; the predator steps
+//     speed[1] unit(P - D) toward it, the prey speed[2] unit(Y - P) away, all
+//     from the positions at the start of the step;
+//   - with the new positions, |P - Y| <= radius ends the episode with +1, else
+//     |P - D| <= radius with -1; after T steps, 0.
+//
+// One launch per step over all episodes still running: the work is the list
+// of (active episode, chunk of 64 candidates) pairs, taken by persistent
+// blocks in order; each chunk's top-2 goes to a per-episode slot, and the
+// block that completes an episode's last chunk merges them, moves the
+// entities and appends the episode to the next step's list if it goes on.
+// Three rotating lists: step t reads list t mod 3, appends to (t + 1) mod 3
+// and clears (t + 2) mod 3, which nothing touches during step t.
+#include "dg_device.cuh"
+#include "dg_grid.cuh"
+#include "dg_internal.h"
+
+namespace dg {
+
+namespace {
+
+__global__ void episode_init(EpisodeParams p) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < p.E) {
+    for (int d = 0; d < 6; ++d) p.state[6 * i + d] = p.start[6 * i + d];
+    p.active[i] = i;
+    p.ticket[i] = 0u;
+    p.outcome[i] = 0;
+    p.steps[i] = p.T;
+    for (int t = 0; t < p.T; ++t) {
+      if (p.traj_best) p.traj_best[(size_t)i * p.T + t] = -1;
+      if (p.traj_value) p.traj_value[(size_t)i * p.T + t] = 0.0;
+      if (p.traj_pos)
+        for (int d = 0; d < 6; ++d) p.traj_pos[((size_t)i * p.T + t) * 6 + d] = 0.f;
+    }
+  }
+  if (i == 0) {
+    p.count[0] = p.E;
+    p.count[1] = 0;
+    p.count[2] = 0;
+  }
+}
+
+// Merge the episode's chunk summaries, move the entities, test for capture.
+__device__ void finish_episode(const EpisodeParams& p, int e) {
+  __shared__ TopTwo warp_best[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  TopTwo t = top_init();
+  for (int b = threadIdx.x; b < p.cpe; b += blockDim.x) {
+    const TopTwo* q = p.partials + (size_t)e * p.cpe + b;
+    TopTwo v;
+    v.v1 = __ldcg(&q->v1);
+    v.i1 = __ldcg(&q->i1);
+    v.v2 = __ldcg(&q->v2);
+    t = top_merge(t, v);
+  }
+  t = top_warp(t);
+  if (lane == 0) warp_best[warp] = t;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  TopTwo r = warp_best[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = top_merge(r, warp_best[w]);
+  const long long b = r.i1;
+  const int l2 = (int)(b % p.L[2]);
+  const int l1 = (int)((b / p.L[2]) % p.L[1]);
+  const int l0 = (int)(b / ((long long)p.L[2] * p.L[1]));
+  const float a0 = p.lv[0][l0], a1 = p.lv[1][l1], a2 = p.lv[2][l2];
+  float S[6];
+  for (int d = 0; d < 6; ++d) S[d] = __ldcg(p.state + 6 * e + d);
+  float ax, ay, ux, uy, vx, vy;
+  pp_act(p.k0, p.k1, (uint32_t)p.t, 0xFFFFFFFFu, 2u * (uint32_t)e, S, 1.0f / (p.offset + a0),
+         1.0f / (p.offset + a1), 1.0f / (p.offset + a2), p.weight, ax, ay);
+  unit2(S[0] - S[2], S[1] - S[3], ux, uy);
+  unit2(S[4] - S[0], S[5] - S[1], vx, vy);
+  float N[6];
+  N[0] = fmaf(p.speed[0], ax, S[0]);
+  N[1] = fmaf(p.speed[0], ay, S[1]);
+  N[2] = fmaf(p.speed[1], ux, S[2]);
+  N[3] = fmaf(p.speed[1], uy, S[3]);
+  N[4] = fmaf(p.speed[2], vx, S[4]);
+  N[5] = fmaf(p.speed[2], vy, S[5]);
+  for (int d = 0; d < 6; ++d) p.state[6 * e + d] = N[d];
+  const size_t k = (size_t)e * p.T + p.t;
+  if (p.traj_best) p.traj_best[k] = (int32_t)b;
+  if (p.traj_value) p.traj_value[k] = r.v1;
+  if (p.traj_pos)
+    for (int d = 0; d < 6; ++d) p.traj_pos[k * 6 + d] = N[d];
+  const float pyx = N[0] - N[4], pyy = N[1] - N[5];
+  const float pdx = N[0] - N[2], pdy = N[1] - N[3];
+  int8_t out = 0;
+  bool done = false;
+  if (sqrtf(pyx * pyx + pyy * pyy) <= p.radius) {
+    out = 1;
+    done = true;
+  } else if (sqrtf(pdx * pdx + pdy * pdy) <= p.radius) {
+    out = -1;
+    done = true;
+  }
+  if (p.t + 1 >= p.T) done = true;
+  if (done) {
+    p.outcome[e] = out;
+    p.steps[e] = p.t + 1;
+    if (p.final_pos)
+      for (int d = 0; d < 6; ++d) p.final_pos[6 * e + d] = N[d];
+  } else {
+    int* next = p.active + (size_t)((p.t + 1) % 3) * p.E;
+    next[atomicAdd(p.count + (p.t + 1) % 3, 1)] = e;
+  }
+  p.ticket[e] = 0u;  // ready for the next step
+}
+
+__global__ void __launch_bounds__(256) episode_step(EpisodeParams p) {
+  __shared__ TopTwo warp_best[8];
+  __shared__ bool last;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cur = p.t % 3;
+  if (blockIdx.x == 0 && threadIdx.x == 0) p.count[(p.t + 2) % 3] = 0;
+  const int na = __ldcg(p.count + cur);
+  const int* act = p.active + (size_t)cur * p.E;
+  const long long items = (long long)na * p.cpe;
+  const double inv = 1.0 / (double)p.n_trials;
+  const uint32_t trial0 = (uint32_t)p.t * (uint32_t)p.n_trials;
+  for (long long w = blockIdx.x; w < items; w += gridDim.x) {
+    const int e = __ldcg(act + w / p.cpe);
+    const int chunk = (int)(w % p.cpe);
+    float S[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) S[d] = __ldcg(p.state + 6 * e + d);
+    TopTwo best = top_init();
+    const long long c_end = min((long long)(chunk + 1) * kEpisodeChunk, p.n_cand);
+    for (long long c = (long long)chunk * kEpisodeChunk + warp; c < c_end; c += 8) {
+      const int l2 = (int)(c % p.L[2]);
+      const int l1 = (int)((c / p.L[2]) % p.L[1]);
+      const int l0 = (int)(c / ((long long)p.L[2] * p.L[1]));
+      const float a0 = __ldg(p.lv[0] + l0), a1 = __ldg(p.lv[1] + l1), a2 = __ldg(p.lv[2] + l2);
+      const float sd0 = 1.0f / (p.offset + a0), sd1 = 1.0f / (p.offset + a1),
+                  sd2 = 1.0f / (p.offset + a2);
+      const float cost = a0 * a0 + a1 * a1 + a2 * a2;
+      double acc = 0.0;
+      for (int j = lane; j < p.n_trials; j += 32)
+        acc += (double)pp_outcome_at(p.k0, p.k1, trial0 + (uint32_t)j, (uint32_t)c,
+                                     2u * (uint32_t)e, S, sd0, sd1, sd2, p.weight, cost);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
+      const double mean = __shfl_sync(kFull, acc, 0) * inv;
+      best = top_merge(best, TopTwo{mean, c, -DBL_MAX});
+    }
+    best = top_warp(best);
+    if (lane == 0) warp_best[warp] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      TopTwo r = warp_best[0];
+      for (int i = 1; i < 8; ++i) r = top_merge(r, warp_best[i]);
+      p.partials[(size_t)e * p.cpe + chunk] = r;
+      __threadfence();
+      last = atomicAdd(p.ticket + e, 1u) == (unsigned)(p.cpe - 1);
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      finish_episode(p, e);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_episode_init(const EpisodeParams& p, cudaStream_t s) {
+  episode_init<<<(p.E + 255) / 256, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_episode_step(const EpisodeParams& p, cudaStream_t s) {
+  static int blocks = 0;
+  if (blocks == 0) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, episode_step, 256, 0);
+    blocks = num_sms() * (nb > 0 ? nb : 1);
+  }
+  long long g = (long long)p.E * p.cpe;
+  if (g > blocks) g = blocks;
+  episode_step<<<(unsigned)g, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace dg

@@ -26,82 +26,19 @@
 #include <climits>
 
 #include "dg_device.cuh"
+#include "dg_grid.cuh"
 #include "dg_internal.h"
 
 namespace dg {
 
 namespace {
 
-struct GridResultDev {
-  long long best_index;
-  double best_value;
-  double gap;
-};
-
-__device__ __forceinline__ TopTwo top_init() { return TopTwo{-DBL_MAX, LLONG_MAX, -DBL_MAX}; }
-
-// Merge two running top-2 summaries: best value with lowest index on ties,
-// and the largest value among the rest.
-__device__ __forceinline__ TopTwo top_merge(TopTwo a, TopTwo b) {
-  const bool b_wins = (b.v1 > a.v1) || (b.v1 == a.v1 && b.i1 < a.i1);
-  TopTwo r;
-  if (b_wins) {
-    r.v1 = b.v1;
-    r.i1 = b.i1;
-    r.v2 = fmax(a.v1, b.v2);
-  } else {
-    r.v1 = a.v1;
-    r.i1 = a.i1;
-    r.v2 = fmax(b.v1, a.v2);
-  }
-  return r;
-}
-
-__device__ __forceinline__ TopTwo top_shfl(TopTwo t, int src, unsigned mask = kFull) {
-  TopTwo r;
-  r.v1 = __shfl_sync(mask, t.v1, src);
-  r.i1 = __shfl_sync(mask, t.i1, src);
-  r.v2 = __shfl_sync(mask, t.v2, src);
-  return r;
-}
-
-__device__ __forceinline__ TopTwo top_warp(TopTwo t) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t = top_merge(t, top_shfl(t, (threadIdx.x & 31) ^ o));
-  return t;
-}
-
-__device__ __forceinline__ void unit2(float vx, float vy, float& ox, float& oy) {
-  const float n2 = vx * vx + vy * vy;
-  if (n2 > 0.f) {
-    const float r = rsqrtf(n2);
-    ox = vx * r;
-    oy = vy * r;
-  } else {
-    ox = 0.f;
-    oy = 0.f;
-  }
-}
-
 // c: the candidate's noise stream
 __device__ __forceinline__ float pp_outcome(const GridParams& p, const float* pos, int j,
                                             uint32_t c, float sd0, float sd1, float sd2,
                                             float cost) {
-  const float4 z = normals4(noise_block(p.k0, p.k1, (uint32_t)j, c, 0u));
-  const uint4 w1 = noise_block(p.k0, p.k1, (uint32_t)j, c, 1u);
-  float z4, z5;
-  box_muller(w1.x, w1.y, z4, z5);
-  const float* X = pos + 6 * j;
-  const float phx = fmaf(sd0, z.x, X[0]), phy = fmaf(sd0, z.y, X[1]);
-  const float dhx = fmaf(sd1, z.z, X[2]), dhy = fmaf(sd1, z.w, X[3]);
-  const float yhx = fmaf(sd2, z4, X[4]), yhy = fmaf(sd2, z5, X[5]);
-  float uyx, uyy, udx, udy, ax, ay;
-  unit2(yhx - phx, yhy - phy, uyx, uyy);
-  unit2(dhx - phx, dhy - phy, udx, udy);
-  unit2(fmaf(-p.weight, udx, uyx), fmaf(-p.weight, udy, uyy), ax, ay);
-  const float nx = (X[0] + ax) - X[4];
-  const float ny = (X[1] + ay) - X[5];
-  return -sqrtf(nx * nx + ny * ny) - cost;
+  return pp_outcome_at(p.k0, p.k1, (uint32_t)j, c, 0u, pos + 6 * j, sd0, sd1, sd2, p.weight,
+                       cost);
 }
 
 // c: global candidate index

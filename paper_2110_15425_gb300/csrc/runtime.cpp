@@ -71,6 +71,8 @@ struct Scratch {
   size_t means_cap = 0;
   unsigned int* perm = nullptr;
   size_t perm_cap = 0;
+  unsigned char* ext = nullptr;  // episodes: state, lists, tickets, partials
+  size_t ext_cap = 0;
   unsigned long long* cursor() { return reinterpret_cast<unsigned long long*>(base); }
   unsigned int* ticket() { return reinterpret_cast<unsigned int*>(base + 8); }
   int* status() { return reinterpret_cast<int*>(base + 16); }
@@ -156,6 +158,20 @@ dg_status scratch_means(dg_ctx* ctx, Scratch* sc, size_t n, cudaStream_t s) {
   sc->means = nullptr;
   DG_CUDA(cudaMalloc(&sc->means, n * sizeof(double)));
   sc->means_cap = n;
+  return DG_OK;
+}
+
+dg_status scratch_ext(dg_ctx* ctx, Scratch* sc, size_t n, cudaStream_t s) {
+  if (sc->ext_cap >= n) return DG_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    return fail(DG_E_STATE, "episodes need scratch of this size; run once before capture");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  DG_CUDA(cudaStreamSynchronize(s));
+  if (sc->ext) cudaFree(sc->ext);
+  sc->ext = nullptr;
+  DG_CUDA(cudaMalloc(&sc->ext, n));
+  sc->ext_cap = n;
   return DG_OK;
 }
 
@@ -1114,6 +1130,7 @@ dg_status dg_destroy(dg_ctx* ctx) {
   for (auto& kv : ctx->scratch) {
     cudaFree(kv.second.base);
     if (kv.second.means) cudaFree(kv.second.means);
+    if (kv.second.ext) cudaFree(kv.second.ext);
     if (kv.second.perm) cudaFree(kv.second.perm);
   }
   delete ctx;
@@ -1269,6 +1286,80 @@ dg_status dg_argmax_f64(dg_ctx* ctx, const double* values, int64_t n, dg_grid_re
   if (st != DG_OK) return st;
   DG_CUDA(cudaMemsetAsync(sc->ticket(), 0, 4, s));
   DG_CUDA(dg::launch_argmax(values, n, sc->partials(), sc->ticket(), result, s));
+  return DG_OK;
+}
+
+dg_status dg_run_episodes(dg_model* m, const dg_episode_desc* d, const dg_episode_out* o,
+                          void* stream) {
+  if (!m || !d || !o || !o->outcome || !o->steps)
+    return fail(DG_E_ARG, "dg_run_episodes: null model, desc or outputs");
+  if (m->kind != K_PP)
+    return fail(DG_E_UNSUPPORTED, "dg_run_episodes: model is not a predator-prey model");
+  if (d->n_episodes < 1) return fail(DG_E_ARG, "dg_run_episodes: n_episodes must be >= 1");
+  if (d->n_trials < 1 || d->n_trials > 1024)
+    return fail(DG_E_ARG, "dg_run_episodes: n_trials %d out of [1, 1024]", d->n_trials);
+  if (d->max_steps < 1 || (long long)d->max_steps * d->n_trials > (1ll << 32))
+    return fail(DG_E_ARG, "dg_run_episodes: max_steps must be >= 1 with max_steps n_trials <= 2^32");
+  for (int i = 0; i < 3; ++i) {
+    if (d->n_levels[i] < 1 || d->n_levels[i] > 4096 || !d->levels[i])
+      return fail(DG_E_ARG, "dg_run_episodes: levels of signal %d", i);
+    if (!(d->speed[i] >= 0.f) || !std::isfinite(d->speed[i]))
+      return fail(DG_E_ARG, "dg_run_episodes: speed %d must be finite and >= 0", i);
+  }
+  if (!(d->capture_radius >= 0.f) || !std::isfinite(d->capture_radius))
+    return fail(DG_E_ARG, "dg_run_episodes: capture_radius must be finite and >= 0");
+  if (!d->start) return fail(DG_E_ARG, "dg_run_episodes: null start positions");
+  const long long n_cand = (long long)d->n_levels[0] * d->n_levels[1] * d->n_levels[2];
+  if (n_cand > 0xFFFFFFFFll) return fail(DG_E_ARG, "dg_run_episodes: more than 2^32 - 1 candidates");
+  const long long cpe = (n_cand + dg::kEpisodeChunk - 1) / dg::kEpisodeChunk;
+  const long long E = d->n_episodes;
+  if (E * cpe > (1ll << 40)) return fail(DG_E_ARG, "dg_run_episodes: too much work per step");
+  if (E > (1ll << 30)) return fail(DG_E_ARG, "dg_run_episodes: too many episodes");
+  DG_CUDA(cudaSetDevice(m->ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch* sc = nullptr;
+  dg_status st = get_scratch(m->ctx, s, &sc);
+  if (st != DG_OK) return st;
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t b_state = up(sizeof(float) * 6 * E), b_active = up(sizeof(int) * 3 * E),
+               b_count = 256, b_ticket = up(sizeof(unsigned) * E),
+               b_part = up(sizeof(dg::TopTwo) * (size_t)(E * cpe));
+  st = scratch_ext(m->ctx, sc, b_state + b_active + b_count + b_ticket + b_part, s);
+  if (st != DG_OK) return st;
+  unsigned char* x = sc->ext;
+  dg::EpisodeParams p{};
+  for (int i = 0; i < 3; ++i) {
+    p.lv[i] = d->levels[i];
+    p.L[i] = d->n_levels[i];
+    p.speed[i] = d->speed[i];
+  }
+  p.n_cand = n_cand;
+  p.cpe = (int)cpe;
+  p.n_trials = d->n_trials;
+  p.k0 = (uint32_t)d->seed;
+  p.k1 = (uint32_t)(d->seed >> 32);
+  p.offset = m->offset;
+  p.weight = m->weight;
+  p.radius = d->capture_radius;
+  p.E = (int)E;
+  p.T = d->max_steps;
+  p.start = d->start;
+  p.state = reinterpret_cast<float*>(x);
+  p.active = reinterpret_cast<int*>(x + b_state);
+  p.count = reinterpret_cast<int*>(x + b_state + b_active);
+  p.ticket = reinterpret_cast<unsigned int*>(x + b_state + b_active + b_count);
+  p.partials = reinterpret_cast<dg::TopTwo*>(x + b_state + b_active + b_count + b_ticket);
+  p.outcome = o->outcome;
+  p.steps = o->steps;
+  p.final_pos = o->final_pos;
+  p.traj_best = o->best;
+  p.traj_value = o->value;
+  p.traj_pos = o->pos;
+  DG_CUDA(dg::launch_episode_init(p, s));
+  for (int t = 0; t < p.T; ++t) {
+    p.t = t;
+    DG_CUDA(dg::launch_episode_step(p, s));
+  }
   return DG_OK;
 }
 
