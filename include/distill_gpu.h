@@ -230,7 +230,9 @@ dg_status dg_grid_search(dg_model* model, const dg_grid_desc* desc, dg_grid_resu
        (trial t, cand 0xFFFFFFFF), same blocks) and moves speed[0] times the
        Action node's unit step; the predator moves speed[1] unit(P - D) toward
        the player and the prey speed[2] unit(Y - P) away from it, all from the
-       positions at the start of the step (FP32);
+       positions at the start of the step. The simulations run in FP32 with
+       FP64 means; this one perception and the moves are computed in FP64
+       from the FP32 positions and rounded to FP32 (the positions' format);
      - then |P - Y| <= radius ends the episode with +1 (prey caught), else
        |P - D| <= radius with -1 (player caught); after max_steps steps, 0. */
 typedef struct {
@@ -241,8 +243,8 @@ typedef struct {
   const float* levels[3];     /* device, allocation values of each signal */
   const float* start;         /* device, [E][6] start positions */
   uint64_t seed;
-  float speed[3];             /* step lengths of player, predator, prey (>= 0) */
-  float capture_radius;       /* >= 0 */
+  double speed[3];            /* step lengths of player, predator, prey (>= 0) */
+  double capture_radius;      /* >= 0 */
 } dg_episode_desc;
 
 /* Outputs of dg_run_episodes (device pointers, caller-owned). */

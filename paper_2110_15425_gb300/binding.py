@@ -69,7 +69,7 @@ class dg_episode_desc(C.Structure):
     _fields_ = [("n_episodes", C.c_int32), ("max_steps", C.c_int32),
                 ("n_levels", C.c_int32 * 3), ("n_trials", C.c_int32),
                 ("levels", C.c_void_p * 3), ("start", C.c_void_p), ("seed", C.c_uint64),
-                ("speed", C.c_float * 3), ("capture_radius", C.c_float)]
+                ("speed", C.c_double * 3), ("capture_radius", C.c_double)]
 
 
 class dg_episode_out(C.Structure):

@@ -155,9 +155,10 @@ struct EpisodeParams {
   int cpe;                       // work items (candidate chunks) per episode
   int n_trials;
   uint32_t k0, k1;
-  float offset, weight;
-  float speed[3];                // player, predator, prey
-  float radius;
+  float offset, weight;          // FP32 copies for the candidate simulations
+  double offset_d, weight_d;     // the model's values, for the FP64 moves
+  double speed[3];               // player, predator, prey
+  double radius;
   int E, T;                      // episodes, maximum steps
   int t;                         // the step a launch performs
   const float* start;            // [E][6]

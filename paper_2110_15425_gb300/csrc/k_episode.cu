@@ -10,7 +10,8 @@
 //   - the player perceives S once more with the best allocation (stream
 //     (trial t, cand 0xFFFFFFFF)) and moves speed[0] act; the predator steps
 //     speed[1] unit(P - D) toward it, the prey speed[2] unit(Y - P) away, all
-//     from the positions at the start of the step;
+//     from the positions at the start of the step (this step runs in FP64 and
+//     rounds the new positions to FP32);
 //   - with the new positions, |P - Y| <= radius ends the episode with +1, else
 //     |P - D| <= radius with -1; after T steps, 0.
 //
@@ -28,6 +29,40 @@
 namespace dg {
 
 namespace {
+
+// The move of the player, predator and prey is computed once per episode and
+// step, by one thread, in FP64 with every operation rounded as written (no
+// contraction), so the positions carried across steps stay as exact as their
+// FP32 format allows.
+__device__ __forceinline__ void unit2_f64(double vx, double vy, double& ox, double& oy) {
+  const double n = __dsqrt_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)));
+  if (n > 0.0) {
+    ox = __ddiv_rn(vx, n);
+    oy = __ddiv_rn(vy, n);
+  } else {
+    ox = 0.0;
+    oy = 0.0;
+  }
+}
+
+// Normals 0..5 of stream (trial, cand) from Philox blocks block0, block0 + 1,
+// by the Box-Muller transform in FP64.
+__device__ __forceinline__ void normals6_f64(uint32_t k0, uint32_t k1, uint32_t trial,
+                                             uint32_t cand, uint32_t block0, double z[6]) {
+  const double two_pi = 6.283185307179586476925286766559;
+  const uint4 a = noise_block(k0, k1, trial, cand, block0);
+  const uint4 b = noise_block(k0, k1, trial, cand, block0 + 1u);
+  const uint32_t w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+  for (int pair = 0; pair < 3; ++pair) {
+    const double ua = __dmul_rn(__dadd_rn((double)(w[2 * pair] >> 9), 0.5), 1.0 / 8388608.0);
+    const double ub = __dmul_rn(__dadd_rn((double)(w[2 * pair + 1] >> 9), 0.5), 1.0 / 8388608.0);
+    const double r = __dsqrt_rn(__dmul_rn(-2.0, log(ua)));
+    double sn, cs;
+    sincos(__dmul_rn(two_pi, ub), &sn, &cs);
+    z[2 * pair] = __dmul_rn(r, cs);
+    z[2 * pair + 1] = __dmul_rn(r, sn);
+  }
+}
 
 __global__ void episode_init(EpisodeParams p) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -74,35 +109,48 @@ __device__ void finish_episode(const EpisodeParams& p, int e) {
   const int l2 = (int)(b % p.L[2]);
   const int l1 = (int)((b / p.L[2]) % p.L[1]);
   const int l0 = (int)(b / ((long long)p.L[2] * p.L[1]));
-  const float a0 = p.lv[0][l0], a1 = p.lv[1][l1], a2 = p.lv[2][l2];
+  const float a[3] = {p.lv[0][l0], p.lv[1][l1], p.lv[2][l2]};
   float S[6];
   for (int d = 0; d < 6; ++d) S[d] = __ldcg(p.state + 6 * e + d);
-  float ax, ay, ux, uy, vx, vy;
-  pp_act(p.k0, p.k1, (uint32_t)p.t, 0xFFFFFFFFu, 2u * (uint32_t)e, S, 1.0f / (p.offset + a0),
-         1.0f / (p.offset + a1), 1.0f / (p.offset + a2), p.weight, ax, ay);
-  unit2(S[0] - S[2], S[1] - S[3], ux, uy);
-  unit2(S[4] - S[0], S[5] - S[1], vx, vy);
+  // the player's perception with the chosen allocation, and its Action step
+  double z[6], ph[6];
+  normals6_f64(p.k0, p.k1, (uint32_t)p.t, 0xFFFFFFFFu, 2u * (uint32_t)e, z);
+  for (int en = 0; en < 3; ++en) {
+    const double sd = __ddiv_rn(1.0, __dadd_rn(p.offset_d, (double)a[en]));
+    for (int c = 0; c < 2; ++c)
+      ph[2 * en + c] = __dadd_rn((double)S[2 * en + c], __dmul_rn(sd, z[2 * en + c]));
+  }
+  double uyx, uyy, udx, udy, ax, ay, ux, uy, vx, vy;
+  unit2_f64(__dsub_rn(ph[4], ph[0]), __dsub_rn(ph[5], ph[1]), uyx, uyy);
+  unit2_f64(__dsub_rn(ph[2], ph[0]), __dsub_rn(ph[3], ph[1]), udx, udy);
+  unit2_f64(__dsub_rn(uyx, __dmul_rn(p.weight_d, udx)), __dsub_rn(uyy, __dmul_rn(p.weight_d, udy)),
+            ax, ay);
+  // the predator pursues the player, the prey flees it
+  unit2_f64(__dsub_rn((double)S[0], (double)S[2]), __dsub_rn((double)S[1], (double)S[3]), ux, uy);
+  unit2_f64(__dsub_rn((double)S[4], (double)S[0]), __dsub_rn((double)S[5], (double)S[1]), vx, vy);
   float N[6];
-  N[0] = fmaf(p.speed[0], ax, S[0]);
-  N[1] = fmaf(p.speed[0], ay, S[1]);
-  N[2] = fmaf(p.speed[1], ux, S[2]);
-  N[3] = fmaf(p.speed[1], uy, S[3]);
-  N[4] = fmaf(p.speed[2], vx, S[4]);
-  N[5] = fmaf(p.speed[2], vy, S[5]);
+  N[0] = __double2float_rn(__dadd_rn((double)S[0], __dmul_rn(p.speed[0], ax)));
+  N[1] = __double2float_rn(__dadd_rn((double)S[1], __dmul_rn(p.speed[0], ay)));
+  N[2] = __double2float_rn(__dadd_rn((double)S[2], __dmul_rn(p.speed[1], ux)));
+  N[3] = __double2float_rn(__dadd_rn((double)S[3], __dmul_rn(p.speed[1], uy)));
+  N[4] = __double2float_rn(__dadd_rn((double)S[4], __dmul_rn(p.speed[2], vx)));
+  N[5] = __double2float_rn(__dadd_rn((double)S[5], __dmul_rn(p.speed[2], vy)));
   for (int d = 0; d < 6; ++d) p.state[6 * e + d] = N[d];
   const size_t k = (size_t)e * p.T + p.t;
   if (p.traj_best) p.traj_best[k] = (int32_t)b;
   if (p.traj_value) p.traj_value[k] = r.v1;
   if (p.traj_pos)
     for (int d = 0; d < 6; ++d) p.traj_pos[k * 6 + d] = N[d];
-  const float pyx = N[0] - N[4], pyy = N[1] - N[5];
-  const float pdx = N[0] - N[2], pdy = N[1] - N[3];
+  const double pyx = __dsub_rn((double)N[0], (double)N[4]);
+  const double pyy = __dsub_rn((double)N[1], (double)N[5]);
+  const double pdx = __dsub_rn((double)N[0], (double)N[2]);
+  const double pdy = __dsub_rn((double)N[1], (double)N[3]);
   int8_t out = 0;
   bool done = false;
-  if (sqrtf(pyx * pyx + pyy * pyy) <= p.radius) {
+  if (__dsqrt_rn(__dadd_rn(__dmul_rn(pyx, pyx), __dmul_rn(pyy, pyy))) <= p.radius) {
     out = 1;
     done = true;
-  } else if (sqrtf(pdx * pdx + pdy * pdy) <= p.radius) {
+  } else if (__dsqrt_rn(__dadd_rn(__dmul_rn(pdx, pdx), __dmul_rn(pdy, pdy))) <= p.radius) {
     out = -1;
     done = true;
   }

@@ -120,6 +120,7 @@ struct dg_model {
   float* d_w_resp_f32 = nullptr;
   // predator-prey
   float offset = 0.f, weight = 0.f;
+  double offset_d = 0.0, weight_d = 0.0;  // as given, for the FP64 episode moves
   int state_size = 0;
   int n_inputs = 0;  // TRANSFER: input units per condition row
 };
@@ -1226,6 +1227,8 @@ dg_status dg_compose(dg_ctx* ctx, const dg_mechanism* mechs, int32_t n_mech,
     m->kind = K_PP;
     m->offset = (float)off;
     m->weight = (float)mechs[idx[DG_PP_ACTION]].weight;
+    m->offset_d = off;
+    m->weight_d = mechs[idx[DG_PP_ACTION]].weight;
     m->max_steps = stop->max_steps;
     *out = m.release();
     return DG_OK;
@@ -1303,10 +1306,10 @@ dg_status dg_run_episodes(dg_model* m, const dg_episode_desc* d, const dg_episod
   for (int i = 0; i < 3; ++i) {
     if (d->n_levels[i] < 1 || d->n_levels[i] > 4096 || !d->levels[i])
       return fail(DG_E_ARG, "dg_run_episodes: levels of signal %d", i);
-    if (!(d->speed[i] >= 0.f) || !std::isfinite(d->speed[i]))
+    if (!(d->speed[i] >= 0.0) || !std::isfinite(d->speed[i]))
       return fail(DG_E_ARG, "dg_run_episodes: speed %d must be finite and >= 0", i);
   }
-  if (!(d->capture_radius >= 0.f) || !std::isfinite(d->capture_radius))
+  if (!(d->capture_radius >= 0.0) || !std::isfinite(d->capture_radius))
     return fail(DG_E_ARG, "dg_run_episodes: capture_radius must be finite and >= 0");
   if (!d->start) return fail(DG_E_ARG, "dg_run_episodes: null start positions");
   const long long n_cand = (long long)d->n_levels[0] * d->n_levels[1] * d->n_levels[2];
@@ -1340,6 +1343,8 @@ dg_status dg_run_episodes(dg_model* m, const dg_episode_desc* d, const dg_episod
   p.k1 = (uint32_t)(d->seed >> 32);
   p.offset = m->offset;
   p.weight = m->weight;
+  p.offset_d = m->offset_d;
+  p.weight_d = m->weight_d;
   p.radius = d->capture_radius;
   p.E = (int)E;
   p.T = d->max_steps;
