@@ -165,6 +165,7 @@ struct EpisodeParams {
   float* state;                  // [E][6] positions at the start of the step
   int* active;                   // [3][E] active episode lists, rotating by step
   int* count;                    // [3] list lengths
+  unsigned long long* cursor;    // [3] next work item of the step
   unsigned int* ticket;          // [E] finished work items of the step
   TopTwo* partials;              // [E][cpe]
   int8_t* outcome;               // [E]

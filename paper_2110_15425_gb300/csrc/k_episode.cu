@@ -16,8 +16,8 @@
 //     |P - D| <= radius with -1; after T steps, 0.
 //
 // One launch per step over all episodes still running: the work is the list
-// of (active episode, chunk of 64 candidates) pairs, taken by persistent
-// blocks in order; each chunk's top-2 goes to a per-episode slot, and the
+// of (active episode, chunk of 64 candidates) pairs, taken in order by
+// persistent blocks from an atomic cursor; each chunk's top-2 goes to a per-episode slot, and the
 // block that completes an episode's last chunk merges them, moves the
 // entities and appends the episode to the next step's list if it goes on.
 // Three rotating lists: step t reads list t mod 3, appends to (t + 1) mod 3
@@ -45,23 +45,16 @@ __device__ __forceinline__ void unit2_f64(double vx, double vy, double& ox, doub
   }
 }
 
-// Normals 0..5 of stream (trial, cand) from Philox blocks block0, block0 + 1,
-// by the Box-Muller transform in FP64.
-__device__ __forceinline__ void normals6_f64(uint32_t k0, uint32_t k1, uint32_t trial,
-                                             uint32_t cand, uint32_t block0, double z[6]) {
+// Box-Muller pair in FP64 from words (wa, wb).
+__device__ __forceinline__ void box_muller_f64(uint32_t wa, uint32_t wb, double& z0, double& z1) {
   const double two_pi = 6.283185307179586476925286766559;
-  const uint4 a = noise_block(k0, k1, trial, cand, block0);
-  const uint4 b = noise_block(k0, k1, trial, cand, block0 + 1u);
-  const uint32_t w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
-  for (int pair = 0; pair < 3; ++pair) {
-    const double ua = __dmul_rn(__dadd_rn((double)(w[2 * pair] >> 9), 0.5), 1.0 / 8388608.0);
-    const double ub = __dmul_rn(__dadd_rn((double)(w[2 * pair + 1] >> 9), 0.5), 1.0 / 8388608.0);
-    const double r = __dsqrt_rn(__dmul_rn(-2.0, log(ua)));
-    double sn, cs;
-    sincos(__dmul_rn(two_pi, ub), &sn, &cs);
-    z[2 * pair] = __dmul_rn(r, cs);
-    z[2 * pair + 1] = __dmul_rn(r, sn);
-  }
+  const double ua = __dmul_rn(__dadd_rn((double)(wa >> 9), 0.5), 1.0 / 8388608.0);
+  const double ub = __dmul_rn(__dadd_rn((double)(wb >> 9), 0.5), 1.0 / 8388608.0);
+  const double r = __dsqrt_rn(__dmul_rn(-2.0, log(ua)));
+  double sn, cs;
+  sincos(__dmul_rn(two_pi, ub), &sn, &cs);
+  z0 = __dmul_rn(r, cs);
+  z1 = __dmul_rn(r, sn);
 }
 
 __global__ void episode_init(EpisodeParams p) {
@@ -83,10 +76,16 @@ __global__ void episode_init(EpisodeParams p) {
     p.count[0] = p.E;
     p.count[1] = 0;
     p.count[2] = 0;
+    for (int k = 0; k < 3; ++k) p.cursor[k] = 0ull;
   }
 }
 
 // Merge the episode's chunk summaries, move the entities, test for capture.
+// Merge the episode's chunk summaries, move the entities, test for capture.
+// The move runs on warp 0: lanes 0-2 draw and apply the perception noise of
+// player, predator and prey (normal pair k of the step's stream is entity
+// k's), lanes 3-4 the predator's and prey's directions, lanes 0-1 the two
+// unit vectors of the Action node, lane 0 the rest.
 __device__ void finish_episode(const EpisodeParams& p, int e) {
   __shared__ TopTwo warp_best[8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -102,32 +101,46 @@ __device__ void finish_episode(const EpisodeParams& p, int e) {
   t = top_warp(t);
   if (lane == 0) warp_best[warp] = t;
   __syncthreads();
-  if (threadIdx.x != 0) return;
+  if (warp != 0) return;
   TopTwo r = warp_best[0];
   for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = top_merge(r, warp_best[w]);
   const long long b = r.i1;
   const int l2 = (int)(b % p.L[2]);
   const int l1 = (int)((b / p.L[2]) % p.L[1]);
   const int l0 = (int)(b / ((long long)p.L[2] * p.L[1]));
-  const float a[3] = {p.lv[0][l0], p.lv[1][l1], p.lv[2][l2]};
   float S[6];
   for (int d = 0; d < 6; ++d) S[d] = __ldcg(p.state + 6 * e + d);
-  // the player's perception with the chosen allocation, and its Action step
-  double z[6], ph[6];
-  normals6_f64(p.k0, p.k1, (uint32_t)p.t, 0xFFFFFFFFu, 2u * (uint32_t)e, z);
-  for (int en = 0; en < 3; ++en) {
-    const double sd = __ddiv_rn(1.0, __dadd_rn(p.offset_d, (double)a[en]));
-    for (int c = 0; c < 2; ++c)
-      ph[2 * en + c] = __dadd_rn((double)S[2 * en + c], __dmul_rn(sd, z[2 * en + c]));
+  double mx = 0.0, my = 0.0;
+  if (lane < 3) {
+    // perceived position of entity `lane` with the chosen allocation
+    const float a = lane == 0 ? p.lv[0][l0] : (lane == 1 ? p.lv[1][l1] : p.lv[2][l2]);
+    const uint4 w = noise_block(p.k0, p.k1, (uint32_t)p.t, 0xFFFFFFFFu,
+                                2u * (uint32_t)e + (lane == 2 ? 1u : 0u));
+    double z0, z1;
+    box_muller_f64(lane == 1 ? w.z : w.x, lane == 1 ? w.w : w.y, z0, z1);
+    const double sd = __ddiv_rn(1.0, __dadd_rn(p.offset_d, (double)a));
+    mx = __dadd_rn((double)S[2 * lane], __dmul_rn(sd, z0));
+    my = __dadd_rn((double)S[2 * lane + 1], __dmul_rn(sd, z1));
+  } else if (lane == 3) {  // the predator pursues the player
+    unit2_f64(__dsub_rn((double)S[0], (double)S[2]), __dsub_rn((double)S[1], (double)S[3]), mx,
+              my);
+  } else if (lane == 4) {  // the prey flees it
+    unit2_f64(__dsub_rn((double)S[4], (double)S[0]), __dsub_rn((double)S[5], (double)S[1]), mx,
+              my);
   }
-  double uyx, uyy, udx, udy, ax, ay, ux, uy, vx, vy;
-  unit2_f64(__dsub_rn(ph[4], ph[0]), __dsub_rn(ph[5], ph[1]), uyx, uyy);
-  unit2_f64(__dsub_rn(ph[2], ph[0]), __dsub_rn(ph[3], ph[1]), udx, udy);
-  unit2_f64(__dsub_rn(uyx, __dmul_rn(p.weight_d, udx)), __dsub_rn(uyy, __dmul_rn(p.weight_d, udy)),
+  const double ppx = __shfl_sync(kFull, mx, 0), ppy = __shfl_sync(kFull, my, 0);
+  const double pdx = __shfl_sync(kFull, mx, 1), pdy = __shfl_sync(kFull, my, 1);
+  const double pyx = __shfl_sync(kFull, mx, 2), pyy = __shfl_sync(kFull, my, 2);
+  const double ux = __shfl_sync(kFull, mx, 3), uy = __shfl_sync(kFull, my, 3);
+  const double vx = __shfl_sync(kFull, mx, 4), vy = __shfl_sync(kFull, my, 4);
+  double qx = 0.0, qy = 0.0;
+  if (lane == 0) unit2_f64(__dsub_rn(pyx, ppx), __dsub_rn(pyy, ppy), qx, qy);
+  if (lane == 1) unit2_f64(__dsub_rn(pdx, ppx), __dsub_rn(pdy, ppy), qx, qy);
+  const double udx = __shfl_sync(kFull, qx, 1), udy = __shfl_sync(kFull, qy, 1);
+  if (lane != 0) return;
+  double ax, ay;
+  unit2_f64(__dsub_rn(qx, __dmul_rn(p.weight_d, udx)), __dsub_rn(qy, __dmul_rn(p.weight_d, udy)),
             ax, ay);
-  // the predator pursues the player, the prey flees it
-  unit2_f64(__dsub_rn((double)S[0], (double)S[2]), __dsub_rn((double)S[1], (double)S[3]), ux, uy);
-  unit2_f64(__dsub_rn((double)S[4], (double)S[0]), __dsub_rn((double)S[5], (double)S[1]), vx, vy);
   float N[6];
   N[0] = __double2float_rn(__dadd_rn((double)S[0], __dmul_rn(p.speed[0], ax)));
   N[1] = __double2float_rn(__dadd_rn((double)S[1], __dmul_rn(p.speed[0], ay)));
@@ -141,16 +154,16 @@ __device__ void finish_episode(const EpisodeParams& p, int e) {
   if (p.traj_value) p.traj_value[k] = r.v1;
   if (p.traj_pos)
     for (int d = 0; d < 6; ++d) p.traj_pos[k * 6 + d] = N[d];
-  const double pyx = __dsub_rn((double)N[0], (double)N[4]);
-  const double pyy = __dsub_rn((double)N[1], (double)N[5]);
-  const double pdx = __dsub_rn((double)N[0], (double)N[2]);
-  const double pdy = __dsub_rn((double)N[1], (double)N[3]);
+  const double cyx = __dsub_rn((double)N[0], (double)N[4]);
+  const double cyy = __dsub_rn((double)N[1], (double)N[5]);
+  const double cdx = __dsub_rn((double)N[0], (double)N[2]);
+  const double cdy = __dsub_rn((double)N[1], (double)N[3]);
   int8_t out = 0;
   bool done = false;
-  if (__dsqrt_rn(__dadd_rn(__dmul_rn(pyx, pyx), __dmul_rn(pyy, pyy))) <= p.radius) {
+  if (__dsqrt_rn(__dadd_rn(__dmul_rn(cyx, cyx), __dmul_rn(cyy, cyy))) <= p.radius) {
     out = 1;
     done = true;
-  } else if (__dsqrt_rn(__dadd_rn(__dmul_rn(pdx, pdx), __dmul_rn(pdy, pdy))) <= p.radius) {
+  } else if (__dsqrt_rn(__dadd_rn(__dmul_rn(cdx, cdx), __dmul_rn(cdy, cdy))) <= p.radius) {
     out = -1;
     done = true;
   }
@@ -171,14 +184,24 @@ __global__ void __launch_bounds__(256) episode_step(EpisodeParams p) {
   __shared__ TopTwo warp_best[8];
   __shared__ bool last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ long long item;
   const int cur = p.t % 3;
-  if (blockIdx.x == 0 && threadIdx.x == 0) p.count[(p.t + 2) % 3] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    p.count[(p.t + 2) % 3] = 0;
+    p.cursor[(p.t + 2) % 3] = 0ull;
+  }
   const int na = __ldcg(p.count + cur);
   const int* act = p.active + (size_t)cur * p.E;
   const long long items = (long long)na * p.cpe;
   const double inv = 1.0 / (double)p.n_trials;
   const uint32_t trial0 = (uint32_t)p.t * (uint32_t)p.n_trials;
-  for (long long w = blockIdx.x; w < items; w += gridDim.x) {
+  for (;;) {
+    // items are taken in order from the step's cursor, so a block that
+    // finishes an episode does not hold up the items after it
+    if (threadIdx.x == 0) item = (long long)atomicAdd(p.cursor + cur, 1ull);
+    __syncthreads();
+    const long long w = item;
+    if (w >= items) break;
     const int e = __ldcg(act + w / p.cpe);
     const int chunk = (int)(w % p.cpe);
     float S[6];

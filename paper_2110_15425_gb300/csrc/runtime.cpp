@@ -1352,6 +1352,7 @@ dg_status dg_run_episodes(dg_model* m, const dg_episode_desc* d, const dg_episod
   p.state = reinterpret_cast<float*>(x);
   p.active = reinterpret_cast<int*>(x + b_state);
   p.count = reinterpret_cast<int*>(x + b_state + b_active);
+  p.cursor = reinterpret_cast<unsigned long long*>(x + b_state + b_active + 64);
   p.ticket = reinterpret_cast<unsigned int*>(x + b_state + b_active + b_count);
   p.partials = reinterpret_cast<dg::TopTwo*>(x + b_state + b_active + b_count + b_ticket);
   p.outcome = o->outcome;
