@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-extensions", action="store_true",
+                    help="skip the episode / coarse-to-fine / tie-break measurements")
     ap.add_argument("--profile-once", action="store_true",
                     help="run warmup + 1 step only (for ncu launch lists)")
     ap.add_argument("--only", default=None,
@@ -535,6 +537,9 @@ def main():
 
     gpu_launches = step.kernels_per_step() * K
     clocks = clk.summary()
+    ext = None
+    if rank == 0 and world == 1 and not args.no_extensions:
+        ext = extensions(B, W, torch, ctx, per_job["grid"]["ms"])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = cpu_baseline()
@@ -553,7 +558,7 @@ def main():
             "per_job": per_job,
             "grid_candidates_per_s": per_job["grid"]["candidates_per_s"],
             "roofline": roofline, "e2e": e2e, "serving": serving, "gpu_launches": gpu_launches,
-            "clocks": clocks, "cpu_baseline": cpu,
+            "clocks": clocks, "cpu_baseline": cpu, "extensions": ext,
         }
         print(json.dumps(line), flush=True)
     for j in step.jobs:
@@ -561,6 +566,106 @@ def main():
     B.dg_destroy(ctx)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _time_ms(torch, fn, reps=3, stream=None):
+    """Mean CUDA-event time of fn() on `stream` (torch's current stream if None)."""
+    s = stream or torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0.record(s)
+        fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return statistics.mean(out)
+
+
+def extensions(B, W, torch, ctx, grid_ms):
+    """Measurements of the paths beyond the hot-path pass: time-stepped
+    predator-prey episodes, the coarse-to-fine grid search, and the reservoir
+    tie-break. Each is timed alone with CUDA events after a warm-up call."""
+    cuda = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    out = {}
+    pp = B.compose_predator_prey(ctx)
+    try:
+        # episodes: 64 x up to 100 steps, each step a 27,000 x 64 search per episode
+        w = W.predator_prey_episodes()
+        E, T = w["start"].shape[0], w["max_steps"]
+        d = B.episode_desc([cuda(x) for x in w["levels"]], cuda(w["start"]), w["n_trials"], T,
+                           w["seed"], speed=w["speed"], radius=w["radius"])
+        oc = torch.zeros(E, dtype=torch.int8, device="cuda")
+        st = torch.zeros(E, dtype=torch.int32, device="cuda")
+        o = B.episode_out(oc, st)
+        B.dg_run_episodes(pp, d, o)
+        ms = _time_ms(torch, lambda: B.dg_run_episodes(pp, d, o))
+        steps = int(st.sum().item())
+        nc = 30 ** 3
+        res = oc.cpu().numpy()
+        out["episodes"] = {
+            "episodes": E, "max_steps": T, "candidates": nc, "trials": w["n_trials"],
+            "episode_steps": steps, "ms": ms, "episode_steps_per_s": steps / (ms / 1e3),
+            "evaluations_per_s": steps * nc * w["n_trials"] / (ms / 1e3),
+            "outcomes": {"prey_caught": int((res == 1).sum()),
+                         "player_caught": int((res == -1).sum()), "none": int((res == 0).sum())},
+            "kernel_launches": 1 + T}
+        # coarse-to-fine: 5 points x 7 rounds against the 30^3 grid, same positions
+        g = W.predator_prey()
+        pos = cuda(g["pos"])
+        G, R = 5, 7
+        rounds = torch.zeros(64 * R, dtype=torch.uint8, device="cuda")
+        rd = B.refine_desc(pos, [0, 0, 0], [1, 1, 1], G, R, g["seed"])
+        side = torch.cuda.Stream()
+        with torch.cuda.stream(side):
+            B.dg_grid_refine(pp, rd, rounds, stream=side)
+        side.synchronize()
+        ms_eager = _time_ms(torch, lambda: B.dg_grid_refine(pp, rd, rounds, stream=side),
+                            stream=side)
+        try:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=side):
+                B.dg_grid_refine(pp, rd, rounds, stream=side)
+            graph.replay()
+            ms_graph = _time_ms(torch, graph.replay, stream=side)
+        except Exception as exc:  # capture refused: report it, keep the eager number
+            ms_graph = f"capture failed: {exc}"
+        rr = B.refine_rounds(rounds.cpu().numpy())
+        full = torch.zeros(3, dtype=torch.float64, device="cuda")
+        lv = [cuda(x) for x in g["levels"]]
+        B.dg_grid_search(pp, B.grid_desc(lv, pos, g["seed"]), full)
+        fb = int(full.cpu().numpy()[:1].view(np.int64)[0])
+        L = g["levels"][0].shape[0]
+        full_alloc = [g["levels"][0][fb // (L * L)], g["levels"][1][(fb // L) % L],
+                      g["levels"][2][fb % L]]
+        # both answers re-evaluated on 1,024 fresh perceptions per position set
+        ev = W.predator_prey(n_trials=1024, pos_seed=31)
+        evpos = cuda(ev["pos"])
+
+        def value_of(alloc):
+            r = torch.zeros(3, dtype=torch.float64, device="cuda")
+            B.dg_grid_search(pp, B.grid_desc([cuda(np.array([a], np.float32)) for a in alloc],
+                                             evpos, 4242), r)
+            return float(r.cpu().numpy()[1])
+        out["coarse_to_fine"] = {
+            "points": G, "rounds": R, "trials": 64, "candidates": R * G ** 3,
+            "ms_eager": ms_eager, "ms_graph": ms_graph, "kernel_launches": 1 + 2 * R,
+            "full_grid_candidates": nc, "full_grid_ms": grid_ms,
+            "alloc": [float(a) for a in rr["alloc"][-1]], "full_grid_alloc": [float(a) for a in full_alloc],
+            "value_fresh_1024": value_of(rr["alloc"][-1]),
+            "full_grid_value_fresh_1024": value_of(full_alloc)}
+        # reservoir tie-break: the 30^3 search with either rule
+        res0 = torch.zeros(3, dtype=torch.float64, device="cuda")
+        d0 = B.grid_desc(lv, pos, g["seed"])
+        d1 = B.grid_desc(lv, pos, g["seed"], tie_break=B.DG_TIE_RESERVOIR)
+        B.dg_grid_search(pp, d1, res0)
+        out["tie_break"] = {
+            "ms_lowest_index": _time_ms(torch, lambda: B.dg_grid_search(pp, d0, res0)),
+            "ms_reservoir": _time_ms(torch, lambda: B.dg_grid_search(pp, d1, res0))}
+    finally:
+        B.dg_model_free(pp)
+    return out
 
 
 def _pinned(torch, a):
