@@ -627,8 +627,8 @@ def extensions(B, W, torch, ctx, grid_ms):
             graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(graph, stream=side):
                 B.dg_grid_refine(pp, rd, rounds, stream=side)
-            graph.replay()
-            ms_graph = _time_ms(torch, graph.replay, stream=side)
+            graph.replay()  # replays on torch's current stream
+            ms_graph = _time_ms(torch, graph.replay)
         except Exception as exc:  # capture refused: report it, keep the eager number
             ms_graph = f"capture failed: {exc}"
         rr = B.refine_rounds(rounds.cpu().numpy())
