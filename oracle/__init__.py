@@ -99,6 +99,9 @@ def _bind(L):
                               C.c_int64, C.c_uint64, C.c_double, C.c_double, P]
     L.or_argmax.argtypes = [P, C.c_int64, P, P, P]
     L.or_argmax_reservoir.argtypes = [P, C.c_int64, C.c_uint64, P, P, P, P]
+    L.or_extended_run.argtypes = [C.POINTER(OrNet), P, C.c_int, C.c_int, P, C.c_int64,
+                                  C.c_uint64, C.c_int, P, P, P, P, P, P, P, P, P, P, P, P, P,
+                                  P, P, P, P]
     L.or_pp_episode.argtypes = [P, C.c_uint32, P, C.c_int32, P, C.c_int32, P, C.c_int32,
                                 C.c_int32, C.c_int32, C.c_uint64, C.c_double, C.c_double, P,
                                 C.c_double, P, P, P, P, P, P, P, P]
@@ -270,6 +273,46 @@ def transfer_run(layers, projections, cond_inputs, cond_block, seed, rate=0.1, n
         L.or_transfer_run(C.byref(net), _p(cin), n_cond, cond_block, _p(ids[lo:]), hi - lo,
                           seed, _p(out["choice"][lo:]), _p(out["step"][lo:]),
                           _p(out["y"][lo:]), _p(out["margin"][lo:]), tr, trace_steps)
+    _threaded(run, n, threads)
+    del keep
+    return out
+
+
+def extended_run(layers, projections, cond_inputs, cond_block, seed, ddm_W, ddm_bias, ddm_dt,
+                 ddm_sigma, ddm_bound, ddm_max, rate=0.1, noise_sd=0.01, stop_layer=None,
+                 stop_threshold=0.7, max_steps=500, trial_ids=None, n_trials=None, threads=1):
+    """Extended Stroop (Sec. 5): the network, then DDM nodes driven by its
+    response layer. ddm_W [n_ddm][stop size], per-DDM bias, dt, sigma, bound,
+    max steps."""
+    if stop_layer is None:
+        stop_layer = len(layers) - 1
+    net, keep = _net(layers, projections, rate, noise_sd, stop_layer, stop_threshold, max_steps)
+    cin = _c(cond_inputs, np.float32)
+    n_cond = cin.shape[0]
+    ids = _ids(trial_ids, n_trials if n_trials is not None else n_cond * cond_block)
+    n = ids.shape[0]
+    W = _c(ddm_W, np.float32)
+    q = W.shape[0]
+    ss = layers[stop_layer]["size"]
+    assert W.shape == (q, ss)
+    b = _c(ddm_bias, np.float32)
+    dt, sg, bd = (_c(v, np.float64) for v in (ddm_dt, ddm_sigma, ddm_bound))
+    mx = _c(ddm_max, np.int32)
+    out = dict(choice=np.zeros(n, np.int8), step=np.zeros(n, np.int32),
+               s_choice=np.zeros(n, np.int8), s_step=np.zeros(n, np.int32),
+               y=np.zeros((n, ss)), s_margin=np.zeros(n), drift=np.zeros((n, q)),
+               d_choice=np.zeros((n, q), np.int8), d_step=np.zeros((n, q), np.int32),
+               d_x=np.zeros((n, q)), d_margin=np.zeros((n, q)))
+    L = lib()
+
+    def run(lo, hi):
+        if hi <= lo:
+            return
+        L.or_extended_run(C.byref(net), _p(cin), n_cond, cond_block, _p(ids[lo:]), hi - lo, seed,
+                          q, _p(W), _p(b), _p(dt), _p(sg), _p(bd), _p(mx),
+                          *[_p(out[k][lo:]) for k in ("choice", "step", "s_choice", "s_step", "y",
+                                                      "s_margin", "drift", "d_choice", "d_step",
+                                                      "d_x", "d_margin")])
     _threaded(run, n, threads)
     del keep
     return out

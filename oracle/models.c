@@ -40,33 +40,47 @@ static double noise_at(noise_stream* s, uint64_t d) {
 
 /* ------------------------------------------------------------------ DDM --- */
 
+/* One DDM trial on noise stream (seed, trial, cand): x_j = x_{j-1} +
+   (drift dt + sigma sqrt(dt) eps_j) until |x_j| >= bound or max_steps;
+   margin = min_j | |x_j| - bound |. */
+static void ddm_trial(double drift, double bound, uint64_t seed, uint32_t trial, uint32_t cand,
+                      double dt, double sigma, double x0, int32_t max_steps, int8_t* choice,
+                      int32_t* step, double* x_final, double* margin) {
+  const double diffusion = sigma * sqrt(dt);
+  noise_stream ns;
+  noise_open(&ns, seed, trial, cand);
+  double x = x0;
+  double m = INFINITY;
+  int8_t c = -1;
+  int32_t s = max_steps;
+  for (int32_t j = 1; j <= max_steps; ++j) {
+    double eps = noise_at(&ns, (uint64_t)(j - 1));
+    x = x + (drift * dt + diffusion * eps);
+    double d = fabs(fabs(x) - bound);
+    if (d < m) m = d;
+    if (fabs(x) >= bound) {
+      c = (x > 0.0) ? 1 : 0;
+      s = j;
+      break;
+    }
+  }
+  *choice = c;
+  *step = s;
+  *x_final = x;
+  *margin = m;
+}
+
 void or_ddm_run(const float* A, const float* z, const uint32_t* trial_ids, int64_t n_ids,
                 uint64_t seed, double dt, double sigma, double x0, int32_t max_steps,
                 int8_t* choice, int32_t* step, double* x_final, double* margin) {
-  const double diffusion = sigma * sqrt(dt);
   for (int64_t k = 0; k < n_ids; ++k) {
     uint32_t t = trial_ids[k];
-    double drift = (double)A[t];
-    double bound = (double)z[t];
-    noise_stream ns;
-    noise_open(&ns, seed, t, 0u);
-    double x = x0;
-    double m = INFINITY;
-    int8_t c = -1;
-    int32_t s = max_steps;
-    for (int32_t j = 1; j <= max_steps; ++j) {
-      double eps = noise_at(&ns, (uint64_t)(j - 1));
-      x = x + (drift * dt + diffusion * eps);
-      double d = fabs(fabs(x) - bound);
-      if (d < m) m = d;
-      if (fabs(x) >= bound) {
-        c = (x > 0.0) ? 1 : 0;
-        s = j;
-        break;
-      }
-    }
+    int8_t c;
+    int32_t st;
+    double x, m;
+    ddm_trial((double)A[t], (double)z[t], seed, t, 0u, dt, sigma, x0, max_steps, &c, &st, &x, &m);
     if (choice) choice[k] = c;
-    if (step) step[k] = s;
+    if (step) step[k] = st;
     if (x_final) x_final[k] = x;
     if (margin) margin[k] = m;
   }
@@ -509,4 +523,50 @@ void or_pp_episode(const float start[6], uint32_t episode, const float* lv0, int
   *steps = (t < max_steps) ? t + 1 : max_steps;
   for (int d = 0; d < 6; ++d) final_pos[d] = S[d];
   free(means);
+}
+
+void or_extended_run(const or_net* net, const float* cond_inputs, int n_cond, int cond_block,
+                     const uint32_t* trial_ids, int64_t n_ids, uint64_t seed, int n_ddm,
+                     const float* W, const float* bias, const double* dt, const double* sigma,
+                     const double* bound, const int32_t* ddm_max, int8_t* choice, int32_t* step,
+                     int8_t* s_choice, int32_t* s_step, double* y_final, double* s_margin,
+                     double* drift, int8_t* d_choice, int32_t* d_step, double* d_x,
+                     double* d_margin) {
+  const int ss = net->size[net->stop_layer];
+  double y[64];
+  for (int64_t k = 0; k < n_ids; ++k) {
+    /* the Stroop network to its own stop */
+    int8_t sc;
+    int32_t st;
+    double sm;
+    or_transfer_run(net, cond_inputs, n_cond, cond_block, trial_ids + k, 1, seed, &sc, &st, y,
+                    &sm, NULL, 0);
+    s_choice[k] = sc;
+    s_step[k] = st;
+    s_margin[k] = sm;
+    for (int i = 0; i < ss; ++i) y_final[k * ss + i] = y[i];
+    /* the DDM nodes, driven by the response layer at that step */
+    int first = -1;
+    for (int q = 0; q < n_ddm; ++q) {
+      double A = (double)bias[q];
+      for (int i = 0; i < ss; ++i) A += (double)W[q * ss + i] * y[i];
+      drift[k * n_ddm + q] = A;
+      const size_t o = (size_t)k * n_ddm + q;
+      ddm_trial(A, bound[q], seed, trial_ids[k], 1u + (uint32_t)q, dt[q], sigma[q], 0.0, ddm_max[q],
+                &d_choice[o], &d_step[o], &d_x[o], &d_margin[o]);
+      if (d_choice[o] >= 0 && (first < 0 || d_step[o] < d_step[(size_t)k * n_ddm + first]))
+        first = q;
+    }
+    /* the trial's response: the first DDM to reach a bound (lower index on
+       equal steps) */
+    if (first >= 0) {
+      choice[k] = (int8_t)(2 * first + d_choice[(size_t)k * n_ddm + first]);
+      step[k] = st + d_step[(size_t)k * n_ddm + first];
+    } else {
+      int32_t mx = 0;
+      for (int q = 0; q < n_ddm; ++q) mx = ddm_max[q] > mx ? ddm_max[q] : mx;
+      choice[k] = -1;
+      step[k] = st + mx;
+    }
+  }
 }

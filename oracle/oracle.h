@@ -25,6 +25,8 @@
  *     candidate index layout, lowest-index argmax.
  *   - Coarse-to-fine grid: round 0 equals the full grid search; noise-free
  *     closed forms of the shrinking box; convergence to the known optimum.
+ *   - Extended Stroop: its network part equals the Stroop run, its DDM part
+ *     equals the DDM run on the network's drift; noise-free closed forms.
  *   - Episodes: one step equals the grid search on the start positions; the
  *     moves' geometry (pursuit, evasion, unit steps); capture rules.
  *   - Reservoir tie-break: a rank-based restatement (the last tied index whose
@@ -135,6 +137,26 @@ void or_transfer_run(const or_net* net, const float* cond_inputs, int n_cond, in
                      const uint32_t* trial_ids, int64_t n_ids, uint64_t seed,
                      int8_t* choice, int32_t* step, double* y_final, double* margin,
                      double* trace, int32_t trace_steps);
+
+/* Extended Stroop (Sec. 5): the Stroop network adds DDM nodes (colour naming,
+   finger pointing) on its response layer. For each trial: the network runs
+   to its own stop (or_transfer_run); then DDM q is driven by
+   drift_q = bias_q + sum_i W[q][i] y_i of the stop layer's outputs y at that
+   step (FP64), starts at 0 and runs x_j = x_{j-1} + drift dt_q +
+   sigma_q sqrt(dt_q) eps_j to |x| >= bound_q or ddm_max[q] steps, with noise
+   stream (seed, trial, cand 1 + q). The trial's response is the first DDM to
+   reach a bound (fewest steps, lower q on equal steps):
+   choice = 2 q + (upper bound), step = network steps + that DDM's steps; with
+   none, choice = -1 and step = network steps + max_q ddm_max[q].
+   Per trial: s_choice, s_step, y_final [ss], s_margin of the network;
+   per (trial, q): drift, d_choice, d_step, d_x, d_margin. n_ddm <= 8. */
+void or_extended_run(const or_net* net, const float* cond_inputs, int n_cond, int cond_block,
+                     const uint32_t* trial_ids, int64_t n_ids, uint64_t seed, int n_ddm,
+                     const float* W, const float* bias, const double* dt, const double* sigma,
+                     const double* bound, const int32_t* ddm_max, int8_t* choice, int32_t* step,
+                     int8_t* s_choice, int32_t* s_step, double* y_final, double* s_margin,
+                     double* drift, int8_t* d_choice, int32_t* d_step, double* d_x,
+                     double* d_margin);
 
 /* ------------------------------------------------- predator-prey grid --- */
 

@@ -153,3 +153,18 @@ def predator_prey_episodes(n_episodes: int = 64, levels: int = 30, n_trials: int
     return dict(start=start, levels=[lv.copy(), lv.copy(), lv.copy()], n_trials=n_trials,
                 max_steps=max_steps, obs_offset=0.1, pred_weight=0.5, speed=(1.0, 0.6, 0.5),
                 radius=1.0, seed=noise_seed)
+
+
+def extended_stroop(weight_seed: int = 0, noise_seed: int = 1, trials_per_condition: int = 1000):
+    """Extended Stroop (Sec. 5): the Stroop network plus two DDM nodes on its
+    response layer, colour naming and finger pointing, with drifts
+    W [2][2] . y_response + 0.2, dt 1e-3, sigma 1, bound 1, at most 10,000 steps."""
+    w = stroop_small(weight_seed=weight_seed, noise_seed=noise_seed,
+                     trials_per_condition=trials_per_condition)
+    w["ddm_W"] = np.array([[2.0, -2.0], [-1.5, 1.5]], F32)
+    w["ddm_bias"] = 0.2
+    w["ddm_dt"] = 1e-3
+    w["ddm_sigma"] = 1.0
+    w["ddm_bound"] = 1.0
+    w["ddm_max"] = 10000
+    return w
