@@ -93,6 +93,9 @@ typedef struct {
   double weight;      /* PP_ACTION: act = unit(unit(prey - player) - weight unit(predator - player)) */
   int32_t flags;      /* DG_LCA_* */
   int32_t reserved;
+  double threshold;   /* DDM node of a TRANSFER graph: bound z (> 0) */
+  int32_t max_steps;  /* DDM node of a TRANSFER graph: steps at most (>= 1) */
+  int32_t reserved2;
 } dg_mechanism;
 
 typedef struct {
@@ -173,7 +176,14 @@ const char* dg_version(void);
                  the same size through an identity projection with NULL weights).
      - TRANSFER: DG_INPUT and DG_TRANSFER_LOGISTIC layers; every projection runs
                  from an earlier mechanism to a logistic layer; the stop mechanism is
-                 a logistic layer of size 2..16. Up to 32 logistic units run on the
+                 a logistic layer of size 2..16. Extended Stroop form (Sec. 5): up to
+                 8 DG_DDM units in total (any number of DDM mechanisms) fed only by
+                 F32 projections from the stop layer; when the network stops, DDM
+                 unit q (mechanisms in array order, units in order) integrates
+                 drift_q = bias + sum_i W[q][i] y_i with its mechanism's dt, noise,
+                 threshold and max_steps from 0 (start must be 0), noise stream
+                 (trial, cand 1 + q). Graphs that list the same DDM units through
+                 different mechanisms or projections compose to the same layout. Up to 32 logistic units run on the
                  small-network kernel; the wide form (two one-hot input layers ->
                  hidden of 64..256 units, multiple of 64 -> response of 16 units with a
                  DG_BF16 hidden->response projection) runs on the tensor-core kernel.
@@ -198,9 +208,14 @@ dg_status dg_model_info(const dg_model* model, int32_t* kind, int32_t* state_siz
    Outputs (device, caller-owned, n_trials entries):
      choice: DDM 1 = upper bound, 0 = lower; LCA winner index; TRANSFER index
              of the largest stop-layer output; -1 = no decision by max_steps.
+             Extended Stroop: 2 q + (upper bound) of the first DDM unit q to
+             reach a bound (fewest steps, lower q on equal steps), -1 if none.
      step:   iteration at which the trial ended (1-based), max_steps on timeout.
+             Extended Stroop: network steps + that unit's steps (+ the largest
+             DDM max_steps if none decided).
      final_state (may be NULL): [n_trials][state_size] FP32 state at the end
-             (DDM x; LCA x_0..x_{N-1}; TRANSFER stop-layer outputs).
+             (DDM x; LCA x_0..x_{N-1}; TRANSFER stop-layer outputs; Extended
+             Stroop: stop-layer outputs, then per DDM unit x, choice, steps).
    Errors: DG_E_ARG, DG_E_UNSUPPORTED (PREDATOR_PREY model), DG_E_CUDA. */
 dg_status dg_run(dg_model* model, const dg_run_desc* desc, int8_t* choice, int32_t* step,
                  float* final_state, void* stream);

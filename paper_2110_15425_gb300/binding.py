@@ -39,7 +39,8 @@ class dg_mechanism(C.Structure):
                 ("bias", C.c_double), ("rate", C.c_double), ("noise", C.c_double),
                 ("dt", C.c_double), ("leak", C.c_double), ("inhibition", C.c_double),
                 ("start", C.c_double), ("offset", C.c_double), ("weight", C.c_double),
-                ("flags", C.c_int32), ("reserved", C.c_int32)]
+                ("flags", C.c_int32), ("reserved", C.c_int32), ("threshold", C.c_double),
+                ("max_steps", C.c_int32), ("reserved2", C.c_int32)]
 
 
 class dg_projection(C.Structure):
@@ -428,6 +429,36 @@ def compose_network(ctx, layers, projections, rate=0.1, noise_sd=0.01, stop_laye
           for i, (s, r, _) in enumerate(projections)]
     if stop_layer is None:
         stop_layer = len(layers) - 1
+    model = dg_compose(ctx, ms, ps, stop(stop_layer, max_steps, stop_threshold))
+    del keep
+    return model
+
+
+def compose_extended_stroop(ctx, layers, projections, ddm_nodes, rate=0.1, noise_sd=0.01,
+                            stop_layer=None, stop_threshold=0.7, max_steps=500):
+    """The Stroop network plus DDM nodes on its stop layer (Sec. 5).
+    ddm_nodes: list of mechanisms, each dict(W [units][stop size], bias, dt,
+    sigma, bound, max_steps), appended after the layers in order; each is fed
+    by one projection from the stop layer with weights W."""
+    import numpy as np
+    if stop_layer is None:
+        stop_layer = len(layers) - 1
+    ms = []
+    for l in layers:
+        if l.get("input", False):
+            ms.append(mech(DG_INPUT, int(l["size"])))
+        else:
+            ms.append(mech(DG_TRANSFER_LOGISTIC, int(l["size"]), gain=float(l.get("gain", 1.0)),
+                           bias=float(l.get("bias", 0.0)), rate=rate, noise=noise_sd))
+    keep = [np.ascontiguousarray(W, dtype=np.float32) for (_, _, W) in projections]
+    ps = [proj(s, r, keep[i]) for i, (s, r, _) in enumerate(projections)]
+    for nd in ddm_nodes:
+        W = np.ascontiguousarray(nd["W"], dtype=np.float32)
+        keep.append(W)
+        ms.append(mech(DG_DDM, W.shape[0], bias=float(nd.get("bias", 0.0)), dt=float(nd["dt"]),
+                       noise=float(nd["sigma"]), threshold=float(nd["bound"]),
+                       max_steps=int(nd["max_steps"])))
+        ps.append(proj(stop_layer, len(ms) - 1, W))
     model = dg_compose(ctx, ms, ps, stop(stop_layer, max_steps, stop_threshold))
     del keep
     return model

@@ -92,16 +92,17 @@ __device__ __forceinline__ float pick4(const float4& z, uint32_t lane) {
   return (lane & 2u) ? b : a;
 }
 
-// Error-free sum (Knuth's TwoSum): x + inc = s + err exactly. The state is
-// carried as x + c, so FP32 drift over thousands of steps stays at the level
-// of the increments' own rounding.
-__device__ __forceinline__ void comp_add(float& x, float& c, float inc) {
-  const float s = x + inc;
-  const float bp = s - x;
-  const float err = (x - (s - bp)) + (inc - bp);
-  x = s;
-  c += err;
-}
+// Drift-diffusion state in 64-bit fixed point with 40 fractional bits: FP32
+// sums inside each 4-step Philox block are rounded once to fixed point and
+// added exactly, so the state does not depend on the order of those additions.
+// The conversions run on the double-precision unit of this GPU; exact
+// single-precision constructions of the same roundings were measured slower.
+constexpr float kFixScale = 1099511627776.0f;       // 2^40
+constexpr float kFixInv = 9.094947017729282e-13f;   // 2^-40
+
+__device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * kFixScale); }
+
+__device__ __forceinline__ float from_fix(long long v) { return __ll2float_rn(v) * kFixInv; }
 
 // Warp-aggregated fetch of trial ids from a global cursor: every lane of the
 // warp must call it; lanes with `need` get consecutive new ids (or -1 when no

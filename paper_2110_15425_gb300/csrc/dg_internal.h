@@ -58,6 +58,8 @@ int lca_max_blocks_per_sm(int N, int tpt, int block);
 constexpr int kNetMaxUnits = 32;     // logistic units
 constexpr int kNetMaxInputs = 64;    // input units
 constexpr int kNetMaxInDegree = 32;  // incoming edges from logistic units, per unit
+constexpr int kNetMaxDdm = 8;        // DDM nodes on the stop layer (Extended Stroop)
+constexpr int kNetMaxStop = 16;      // stop-layer units
 
 // Static layout of a small network (Sec. 3.3): logistic units numbered in
 // mechanism order; unit u's incoming edges from logistic units are the dense
@@ -75,6 +77,15 @@ struct NetLayout {
   float bias[kNetMaxUnits];
   float w[kNetMaxUnits][kNetMaxInDegree];
   int8_t src[kNetMaxUnits][kNetMaxInDegree];
+  // DDM nodes driven by the stop layer once the network stops (0 = none):
+  // drift_q = ddm_bias[q] + sum_i ddm_w[q][i] y_i, then x += drift dt + diffusion eps
+  int n_ddm;
+  float ddm_w[kNetMaxDdm][kNetMaxStop];
+  float ddm_bias[kNetMaxDdm];
+  float ddm_dt[kNetMaxDdm];
+  float ddm_diffusion[kNetMaxDdm];   // sigma sqrt(dt)
+  float ddm_z[kNetMaxDdm];           // bound
+  int ddm_max[kNetMaxDdm];           // steps
 };
 
 struct NetParams {
@@ -86,9 +97,11 @@ struct NetParams {
   uint32_t trial0;
   uint32_t k0, k1;
   int U, n_in, stop_size;        // host copies for launch sizing
+  int n_ddm;                     // host copy
+  int state_size;                // floats per trial in yout: stop_size (+ 3 per DDM node)
   int8_t* choice;
   int32_t* step;
-  float* yout;                   // [n][stop_size], may be null
+  float* yout;                   // [n][state_size], may be null
   unsigned long long* cursor;
 };
 cudaError_t launch_net(const NetParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);

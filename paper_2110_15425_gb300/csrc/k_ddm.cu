@@ -23,17 +23,6 @@ namespace dg {
 
 namespace {
 
-constexpr float kFixScale = 1099511627776.0f;       // 2^40
-constexpr float kFixInv = 9.094947017729282e-13f;   // 2^-40
-
-// Conversions between FP32 and the fixed-point state: two per four steps per
-// lane. They run on the double-precision unit of this GPU; exact
-// single-precision constructions of the same roundings were measured slower
-// (more issue slots than the conversions they replace).
-__device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * kFixScale); }
-
-__device__ __forceinline__ float from_fix(long long v) { return __ll2float_rn(v) * kFixInv; }
-
 struct DdmTrial {
   float adt;        // A dt
   float z;          // threshold

@@ -18,6 +18,16 @@
 // unit updates; groups refill from the trial cursor.
 // Plain form (net_plain): one thread per trial with the unit state in shared
 // memory laid out [unit][thread].
+//
+// Extended Stroop (Sec. 5): DDM nodes on the stop layer. When the network
+// stops, node q takes drift_q = bias_q + sum_i w_qi y_i from the stop layer's
+// outputs and integrates x += drift dt + sigma sqrt(dt) eps from 0 to |x| >= z_q
+// (noise stream (trial, cand 1 + q); FP32 sums within each 4-step Philox block,
+// 64-bit fixed point across blocks, as the DDM kernel). The trial's response
+// is the first node to reach a bound (fewest steps, lower q on equal steps):
+// choice 2 q + (upper bound), step = network steps + node steps; none: -1 and
+// network steps + max_q node max. In the batched form lane q of the trial's
+// group runs node q, one Philox block per loop iteration.
 #include <cfloat>
 
 #include "dg_device.cuh"
@@ -52,15 +62,75 @@ __device__ __forceinline__ void stage_layout(const NetParams& p, unsigned char* 
   __syncthreads();
 }
 
+struct DdmNode {
+  float adt, diff, z;
+  int max;
+  long long X;      // state before block b, fixed point
+  int b;
+};
+
+__device__ __forceinline__ DdmNode ddm_node_begin(const NetLayout& L, int q, float drift) {
+  return DdmNode{drift * L.ddm_dt[q], L.ddm_diffusion[q], L.ddm_z[q], L.ddm_max[q], 0ll, 0};
+}
+
+// Four steps of node q (one Philox block); true when the node has ended.
+__device__ __forceinline__ bool ddm_node_block(const NetParams& p, uint32_t trial, int q,
+                                               DdmNode& d, int& choice, int& step, float& x) {
+  const float4 e = normals4(noise_block(p.k0, p.k1, trial, 1u + (uint32_t)q, (uint32_t)d.b));
+  float pre[4];
+  pre[0] = fmaf(d.diff, e.x, d.adt);
+  pre[1] = pre[0] + fmaf(d.diff, e.y, d.adt);
+  pre[2] = pre[1] + fmaf(d.diff, e.z, d.adt);
+  pre[3] = pre[2] + fmaf(d.diff, e.w, d.adt);
+  const float xb = from_fix(d.X);
+  const int k = 4 * d.b;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float v = xb + pre[j];
+    if (fabsf(v) >= d.z) {
+      choice = v > 0.0f ? 1 : 0;
+      step = k + j + 1;
+      x = v;
+      return true;
+    }
+    if (k + j + 1 == d.max) {
+      choice = -1;
+      step = d.max;
+      x = v;
+      return true;
+    }
+  }
+  d.X += to_fix(pre[3]);
+  ++d.b;
+  return false;
+}
+
+// The trial's response from the nodes' (choice, step).
+__device__ __forceinline__ void ddm_response(const NetLayout& L, const int* c, const int* st,
+                                             int net_step, int8_t& choice, int32_t& step) {
+  int first = -1;
+  for (int q = 0; q < L.n_ddm; ++q)
+    if (c[q] >= 0 && (first < 0 || st[q] < st[first])) first = q;
+  if (first >= 0) {
+    choice = (int8_t)(2 * first + c[first]);
+    step = net_step + st[first];
+  } else {
+    int mx = 0;
+    for (int q = 0; q < L.n_ddm; ++q) mx = max(mx, L.ddm_max[q]);
+    choice = -1;
+    step = net_step + mx;
+  }
+}
+
 // ------------------------------------------------------------- batched ---
 
-template <int G>
+template <int G, bool EXT>
 __global__ void __launch_bounds__(256) net_group(NetParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   stage_layout(p, smem);
   const NetLayout& L = *reinterpret_cast<const NetLayout*>(smem);
   const int lane = threadIdx.x & 31;
-  const int u = lane % G;                 // unit of this lane
+  const int u = lane % G;                 // unit of this lane (and DDM node, phase 1)
   const int root = lane - u;
   const unsigned gmask = (G == 32 ? kFull : ((1u << G) - 1u)) << root;
   const bool real = u < L.U;
@@ -74,9 +144,15 @@ __global__ void __launch_bounds__(256) net_group(NetParams p) {
   int k = 0;
   float s = 0.f, y = lg(0.f), netc = 0.f;
   if (active && real) netc = const_net(p, L, t, u);
+  // phase 1 (EXT): the DDM nodes
+  int phase = 0, net_step = 0;
+  bool ddone = true;
+  DdmNode dn{};
+  int dchoice = -1, dstep = 0;
+  float dx = 0.f;
   while (__any_sync(kFull, active)) {
     bool finished = false;
-    if (active) {
+    if (active && (!EXT || phase == 0)) {
       // synchronous: every lane reads the step k outputs before any update
       float net = netc;
       for (int d = 0; d < L.D; ++d) {
@@ -108,11 +184,41 @@ __global__ void __launch_bounds__(256) net_group(NetParams p) {
       ++k;
       const bool hit = v1 - v2 > L.stop_threshold;
       if (hit || k >= L.max_steps) {
-        if (u == 0) {
-          p.choice[t] = hit ? (int8_t)i1 : (int8_t)-1;
-          p.step[t] = hit ? k : L.max_steps;
+        if (p.yout && in_stop) p.yout[(size_t)t * p.state_size + (u - L.stop_off)] = y;
+        if (!EXT || L.n_ddm == 0) {
+          if (u == 0) {
+            p.choice[t] = hit ? (int8_t)i1 : (int8_t)-1;
+            p.step[t] = hit ? k : L.max_steps;
+          }
+          finished = true;
+        } else {
+          // drifts of the DDM nodes from the stop layer's outputs
+          net_step = hit ? k : L.max_steps;
+          float drift = u < L.n_ddm ? L.ddm_bias[u] : 0.f;
+          for (int i = 0; i < L.stop_size; ++i) {
+            const float yi = __shfl_sync(gmask, y, root + L.stop_off + i);
+            if (u < L.n_ddm) drift = fmaf(L.ddm_w[u][i], yi, drift);
+          }
+          ddone = u >= L.n_ddm;
+          if (!ddone) dn = ddm_node_begin(L, u, drift);
+          phase = 1;
         }
-        if (p.yout && in_stop) p.yout[(size_t)t * L.stop_size + (u - L.stop_off)] = y;
+      }
+    } else if (EXT && active) {
+      if (!ddone) ddone = ddm_node_block(p, p.trial0 + (uint32_t)t, u, dn, dchoice, dstep, dx);
+      if ((__ballot_sync(gmask, !ddone) & gmask) == 0u) {
+        int cs[kNetMaxDdm], ss[kNetMaxDdm];
+        for (int q = 0; q < L.n_ddm; ++q) {
+          cs[q] = __shfl_sync(gmask, dchoice, root + q);
+          ss[q] = __shfl_sync(gmask, dstep, root + q);
+        }
+        if (u == 0) ddm_response(L, cs, ss, net_step, p.choice[t], p.step[t]);
+        if (p.yout && u < L.n_ddm) {
+          float* o = p.yout + (size_t)t * p.state_size + L.stop_size + 3 * u;
+          o[0] = dx;
+          o[1] = (float)dchoice;
+          o[2] = (float)dstep;
+        }
         finished = true;
       }
     }
@@ -125,6 +231,8 @@ __global__ void __launch_bounds__(256) net_group(NetParams p) {
       s = 0.f;
       y = lg(0.f);
       netc = (active && real) ? const_net(p, L, t, u) : 0.f;
+      phase = 0;
+      ddone = true;
     }
   }
 }
@@ -150,7 +258,10 @@ __global__ void __launch_bounds__(128) net_plain(NetParams p) {
     y[u * B + tid] = Logistic::of(L.gain[u], L.bias[u])(0.f);
   }
   const uint32_t trial = p.trial0 + (uint32_t)t;
-  for (int k = 0; k < L.max_steps; ++k) {
+  bool hit = false;
+  int best = 0, k = 0;
+  const float* ys = y + L.stop_off * B + tid;
+  while (k < L.max_steps) {
     float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int u = 0; u < U; ++u) {
       float net = netc[u * B + tid];
@@ -166,8 +277,9 @@ __global__ void __launch_bounds__(128) net_plain(NetParams p) {
     float* tmp = y;
     y = yn;
     yn = tmp;
-    const float* ys = y + L.stop_off * B + tid;
-    int best = 0;
+    ys = y + L.stop_off * B + tid;
+    ++k;
+    best = 0;
     float v1 = ys[0];
     for (int i = 1; i < L.stop_size; ++i)
       if (ys[i * B] > v1) {
@@ -177,32 +289,50 @@ __global__ void __launch_bounds__(128) net_plain(NetParams p) {
     float v2 = -FLT_MAX;
     for (int i = 0; i < L.stop_size; ++i)
       if (i != best) v2 = fmaxf(v2, ys[i * B]);
-    const bool hit = v1 - v2 > L.stop_threshold;
-    if (hit || k + 1 >= L.max_steps) {
-      p.choice[t] = hit ? (int8_t)best : (int8_t)-1;
-      p.step[t] = hit ? k + 1 : L.max_steps;
-      if (p.yout)
-        for (int i = 0; i < L.stop_size; ++i) p.yout[(size_t)t * L.stop_size + i] = ys[i * B];
-      return;
+    hit = v1 - v2 > L.stop_threshold;
+    if (hit) break;
+  }
+  const int net_step = hit ? k : L.max_steps;
+  if (p.yout)
+    for (int i = 0; i < L.stop_size; ++i) p.yout[(size_t)t * p.state_size + i] = ys[i * B];
+  if (L.n_ddm == 0) {
+    p.choice[t] = hit ? (int8_t)best : (int8_t)-1;
+    p.step[t] = net_step;
+    return;
+  }
+  int cs[kNetMaxDdm], ss[kNetMaxDdm];
+  for (int q = 0; q < L.n_ddm; ++q) {
+    float drift = L.ddm_bias[q];
+    for (int i = 0; i < L.stop_size; ++i) drift = fmaf(L.ddm_w[q][i], ys[i * B], drift);
+    DdmNode dn = ddm_node_begin(L, q, drift);
+    float dx = 0.f;
+    while (!ddm_node_block(p, trial, q, dn, cs[q], ss[q], dx)) {
+    }
+    if (p.yout) {
+      float* o = p.yout + (size_t)t * p.state_size + L.stop_size + 3 * q;
+      o[0] = dx;
+      o[1] = (float)cs[q];
+      o[2] = (float)ss[q];
     }
   }
+  ddm_response(L, cs, ss, net_step, p.choice[t], p.step[t]);
 }
 
 size_t layout_smem() { return ((sizeof(NetLayout) + 15) / 16) * 16; }
 
-template <int G>
+template <int G, bool EXT>
 cudaError_t launch_group(const NetParams& p, const LaunchCfg& cfg, cudaStream_t s) {
   const size_t smem = layout_smem();
-  cudaError_t e =
-      cudaFuncSetAttribute(net_group<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(net_group<G, EXT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, net_group<G>, 256, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, net_group<G, EXT>, 256, smem);
   if (nb < 1) nb = 1;
   long long grid = cfg.grid > 0 ? cfg.grid : (long long)num_sms() * nb;
   const long long need = (p.n * G + 255) / 256;
   if (grid > need) grid = need;
-  net_group<G><<<(unsigned)grid, 256, smem, s>>>(p);
+  net_group<G, EXT><<<(unsigned)grid, 256, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -219,11 +349,17 @@ cudaError_t launch_net(const NetParams& p, int mode, const LaunchCfg& cfg, cudaS
     net_plain<<<(unsigned)((p.n + B - 1) / B), B, smem, s>>>(p);
     return cudaGetLastError();
   }
-  if (p.U <= 2) return launch_group<2>(p, cfg, s);
-  if (p.U <= 4) return launch_group<4>(p, cfg, s);
-  if (p.U <= 8) return launch_group<8>(p, cfg, s);
-  if (p.U <= 16) return launch_group<16>(p, cfg, s);
-  return launch_group<32>(p, cfg, s);
+  const int lanes = p.U > p.n_ddm ? p.U : p.n_ddm;   // a lane per unit and per DDM node
+  if (p.n_ddm > 0) {
+    if (lanes <= 8) return launch_group<8, true>(p, cfg, s);
+    if (lanes <= 16) return launch_group<16, true>(p, cfg, s);
+    return launch_group<32, true>(p, cfg, s);
+  }
+  if (lanes <= 2) return launch_group<2, false>(p, cfg, s);
+  if (lanes <= 4) return launch_group<4, false>(p, cfg, s);
+  if (lanes <= 8) return launch_group<8, false>(p, cfg, s);
+  if (lanes <= 16) return launch_group<16, false>(p, cfg, s);
+  return launch_group<32, false>(p, cfg, s);
 }
 
 }  // namespace dg

@@ -493,6 +493,8 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
     p.U = m->layout.U;
     p.n_in = m->layout.n_in;
     p.stop_size = m->layout.stop_size;
+    p.n_ddm = m->layout.n_ddm;
+    p.state_size = m->state_size;
     p.choice = choice;
     p.step = step;
     p.yout = fs;
@@ -907,18 +909,25 @@ dg_status upload(T** dst, const std::vector<T>& v) {
 
 dg_status compose_transfer(dg_model* m, const dg_mechanism* mechs, int n_mech,
                            const dg_projection* projs, int n_proj, const dg_stop* stop) {
-  std::vector<int> noff(n_mech, -1), ioff(n_mech, -1);
-  int U = 0, n_in = 0, n_logistic = 0;
+  std::vector<int> noff(n_mech, -1), ioff(n_mech, -1), doff(n_mech, -1);
+  int U = 0, n_in = 0, n_logistic = 0, n_ddm = 0;
   for (int i = 0; i < n_mech; ++i) {
     if (mechs[i].kind == DG_INPUT) {
       ioff[i] = n_in;
       n_in += mechs[i].size;
-    } else {
+    } else if (mechs[i].kind == DG_DDM) {
+      doff[i] = n_ddm;
+      n_ddm += mechs[i].size;
+    } else if (mechs[i].kind == DG_TRANSFER_LOGISTIC) {
       noff[i] = U;
       U += mechs[i].size;
       ++n_logistic;
+    } else {
+      return fail(DG_E_SHAPE, "compose: mechanism %d cannot be part of a transfer network", i);
     }
   }
+  if (n_ddm > dg::kNetMaxDdm)
+    return fail(DG_E_UNSUPPORTED, "compose: at most %d DDM units on the stop layer", dg::kNetMaxDdm);
   if (n_logistic == 0) return fail(DG_E_SHAPE, "compose: no logistic layer");
   if (stop->mech < 0 || stop->mech >= n_mech || mechs[stop->mech].kind != DG_TRANSFER_LOGISTIC)
     return fail(DG_E_SHAPE, "compose: stop mechanism must be a logistic layer");
@@ -941,14 +950,28 @@ dg_status compose_transfer(dg_model* m, const dg_mechanism* mechs, int n_mech,
     const auto& e = projs[p];
     if (e.sender < 0 || e.sender >= n_mech || e.receiver < 0 || e.receiver >= n_mech)
       return fail(DG_E_SHAPE, "compose: projection %d has an invalid endpoint", p);
-    if (mechs[e.receiver].kind != DG_TRANSFER_LOGISTIC)
+    if (mechs[e.sender].kind == DG_DDM)
+      return fail(DG_E_SHAPE, "compose: projection %d leaves a DDM node (DDM nodes send nothing)", p);
+    if (mechs[e.receiver].kind == DG_DDM) {
+      if (e.sender != stop->mech || e.dtype != DG_F32)
+        return fail(DG_E_SHAPE, "compose: DDM node inputs are F32 projections from the stop layer (projection %d)", p);
+    } else if (mechs[e.receiver].kind != DG_TRANSFER_LOGISTIC) {
       return fail(DG_E_SHAPE, "compose: projection %d must end at a logistic layer", p);
+    }
     if (!e.weights) return fail(DG_E_ARG, "compose: projection %d has no weights", p);
     if (e.dtype != DG_F32 && e.dtype != DG_BF16)
       return fail(DG_E_ARG, "compose: projection %d has unknown dtype", p);
   }
+  for (int i = 0; i < n_mech; ++i) {
+    if (mechs[i].kind != DG_DDM) continue;
+    const auto& g = mechs[i];
+    if (!(g.dt > 0.0) || !(g.noise >= 0.0) || !(g.threshold > 0.0) || g.max_steps < 1 ||
+        g.start != 0.0)
+      return fail(DG_E_ARG, "compose: DDM node %d needs dt > 0, noise >= 0, threshold > 0, "
+                  "max_steps >= 1 and start 0", i);
+  }
   m->max_steps = stop->max_steps;
-  m->state_size = mechs[stop->mech].size;
+  m->state_size = mechs[stop->mech].size + 3 * n_ddm;
   m->n_inputs = n_in;
   m->rate = (float)rate;
   m->noise = (float)noise;
@@ -957,7 +980,7 @@ dg_status compose_transfer(dg_model* m, const dg_mechanism* mechs, int n_mech,
   // wide form: stim, task (inputs) -> hidden -> response (BF16 edge)
   int n_inputs = 0;
   for (int i = 0; i < n_mech; ++i) n_inputs += mechs[i].kind == DG_INPUT;
-  if (n_inputs == 2 && n_logistic == 2 && n_proj == 3) {
+  if (n_inputs == 2 && n_logistic == 2 && n_proj == 3 && n_ddm == 0) {
     int in0 = -1, in1 = -1, hid = -1, resp = stop->mech;
     for (int i = 0; i < n_mech; ++i) {
       if (mechs[i].kind == DG_INPUT) (in0 < 0 ? in0 : in1) = i;
@@ -1031,9 +1054,26 @@ dg_status compose_transfer(dg_model* m, const dg_mechanism* mechs, int n_mech,
       }
   std::vector<float> w_in((size_t)U * std::max(1, n_in), 0.f);
   std::vector<int> deg(U, 0);
+  L.n_ddm = n_ddm;
+  for (int i = 0; i < n_mech; ++i)
+    if (doff[i] >= 0)
+      for (int u = 0; u < mechs[i].size; ++u) {
+        const int q = doff[i] + u;
+        L.ddm_bias[q] = (float)mechs[i].bias;
+        L.ddm_dt[q] = (float)mechs[i].dt;
+        L.ddm_diffusion[q] = (float)(mechs[i].noise * std::sqrt(mechs[i].dt));
+        L.ddm_z[q] = (float)mechs[i].threshold;
+        L.ddm_max[q] = mechs[i].max_steps;
+      }
   for (int p = 0; p < n_proj; ++p) {
     const auto& e = projs[p];
     const int rs = mechs[e.receiver].size, ss = mechs[e.sender].size;
+    if (doff[e.receiver] >= 0) {  // into DDM nodes: weights over the stop layer's units
+      for (int i = 0; i < rs; ++i)
+        for (int j = 0; j < ss; ++j)
+          L.ddm_w[doff[e.receiver] + i][j] += e.weights[(size_t)i * ss + j];
+      continue;
+    }
     for (int i = 0; i < rs; ++i)
       for (int j = 0; j < ss; ++j) {
         const float w = e.weights[(size_t)i * ss + j];
@@ -1157,8 +1197,8 @@ dg_status dg_compose(dg_ctx* ctx, const dg_mechanism* mechs, int32_t n_mech,
   const int integrators = counts[DG_DDM] + counts[DG_LCA];
   const int pp = counts[DG_PP_OBSERVE] + counts[DG_PP_ACTION] + counts[DG_PP_OBJECTIVE];
 
-  if (integrators > 0) {
-    if (integrators != 1 || counts[DG_TRANSFER_LOGISTIC] || pp || counts[DG_INPUT] > 1)
+  if (integrators > 0 && counts[DG_TRANSFER_LOGISTIC] == 0) {
+    if (integrators != 1 || pp || counts[DG_INPUT] > 1)
       return fail(DG_E_SHAPE, "dg_compose: an integrator model has one DDM or LCA (and at most one input)");
     int im = -1, in = -1;
     for (int i = 0; i < n_mech; ++i) {
