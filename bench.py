@@ -655,6 +655,38 @@ def extensions(B, W, torch, ctx, grid_ms):
             "alloc": [float(a) for a in rr["alloc"][-1]], "full_grid_alloc": [float(a) for a in full_alloc],
             "value_fresh_1024": value_of(rr["alloc"][-1]),
             "full_grid_value_fresh_1024": value_of(full_alloc)}
+        # Extended Stroop: the 4 x 1,000 Stroop trials, then two DDM nodes each
+        ex = W.extended_stroop()
+        xm = B.compose_extended_stroop(
+            ctx, ex["layers"], ex["projections"],
+            [dict(W=ex["ddm_W"][q:q + 1], bias=ex["ddm_bias"], dt=ex["ddm_dt"],
+                  sigma=ex["ddm_sigma"], bound=ex["ddm_bound"], max_steps=ex["ddm_max"])
+             for q in range(2)],
+            rate=ex["rate"], noise_sd=ex["noise_sd"], stop_layer=ex["stop_layer"],
+            stop_threshold=ex["stop_threshold"], max_steps=ex["max_steps"])
+        try:
+            n = ex["n_trials"]
+            cond = cuda(ex["cond_inputs"])
+            xc = torch.zeros(n, dtype=torch.int8, device="cuda")
+            xs = torch.zeros(n, dtype=torch.int32, device="cuda")
+            xf = torch.zeros(n * 8, dtype=torch.float32, device="cuda")
+            xd = B.run_desc(n, ex["seed"], cond_inputs=cond, n_cond=cond.shape[0],
+                            cond_block=ex["cond_block"])
+            B.dg_run(xm, xd, xc, xs, xf)
+            xms = _time_ms(torch, lambda: B.dg_run(xm, xd, xc, xs, xf))
+            # final state per trial: y_0, y_1, then (x, choice, steps) per node
+            f = xf.cpu().numpy().reshape(n, 8).astype(np.int64)
+            ch, st = xc.cpu().numpy(), xs.cpu().numpy().astype(np.int64)
+            winner = np.maximum(ch, 0) // 2
+            winner_steps = np.where(ch >= 0, f[np.arange(n), 4 + 3 * winner], ex["ddm_max"])
+            net_steps = int((st - winner_steps).sum())
+            node_steps = int(f[:, 4].sum() + f[:, 7].sum())
+            out["extended_stroop"] = {
+                "trials": n, "ddm_nodes": 2, "ms": xms, "network_trial_steps": net_steps,
+                "ddm_node_steps": node_steps,
+                "trial_steps_per_s": (net_steps + node_steps) / (xms / 1e3)}
+        finally:
+            B.dg_model_free(xm)
         # reservoir tie-break: the 30^3 search with either rule
         res0 = torch.zeros(3, dtype=torch.float64, device="cuda")
         d0 = B.grid_desc(lv, pos, g["seed"])
