@@ -34,6 +34,19 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
+// The same block with the round keys precomputed (dg::PhiloxKeys).
+template <typename Keys>
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const Keys& rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53ull;
+    const unsigned long long p1 = (unsigned long long)c.z * 0xCD9E8D57ull;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k[2 * r], (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ rk.k[2 * r + 1], (uint32_t)p0);
+  }
+  return c;
+}
+
 __device__ __forceinline__ uint4 noise_block(uint32_t k0, uint32_t k1, uint32_t trial,
                                              uint32_t cand, uint32_t block) {
   return philox(make_uint4(trial, cand, block, 0u), k0, k1);

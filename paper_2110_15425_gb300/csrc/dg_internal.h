@@ -15,6 +15,21 @@ struct LaunchCfg {
 };
 
 // ------------------------------------------------------------------ DDM ---
+// The ten round keys of Philox4x32-10 for key (k0, k1): round r uses
+// (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85). Passed in a kernel's parameters, a
+// round's key words are constant-bank operands of its xor instructions.
+struct PhiloxKeys {
+  uint32_t k[20];
+};
+inline PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
+  PhiloxKeys r;
+  for (int i = 0; i < 10; ++i) {
+    r.k[2 * i] = k0 + (uint32_t)i * 0x9E3779B9u;
+    r.k[2 * i + 1] = k1 + (uint32_t)i * 0xBB67AE85u;
+  }
+  return r;
+}
+
 struct DdmParams {
   const float* A;      // [n] drift
   const float* z;      // [n] threshold
@@ -30,6 +45,7 @@ struct DdmParams {
   float* xout;         // may be null
   unsigned long long* cursor;  // batched form: global trial cursor (zeroed per launch)
   const unsigned int* perm;    // batched form: order in which trials are handed out (or null)
+  PhiloxKeys rk;               // round keys of (k0, k1)
 };
 cudaError_t launch_ddm(const DdmParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
 int ddm_max_blocks_per_sm(int block);

@@ -7,10 +7,13 @@
 // Arithmetic (the same operations in both forms below, so they agree bit for
 // bit): inside block b the increments are summed in FP32 in step order,
 // p_0 = inc_0, p_j = p_{j-1} + inc_j; the block sums p_3 are rounded once to
-// 64-bit fixed point (40 fractional bits) and added exactly, so the state
-// before block b, X_b, does not depend on the order of those additions; the
-// bound test at step j of block b is |float(X_b) + p_j| >= z in FP32.
-// Error against exact arithmetic stays near 1e-6 after 10,000 steps.
+// fixed point and added exactly, so the state before block b, X_b, does not
+// depend on the order of those additions; the bound test at step j of block b
+// is |float(X_b) + p_j| >= z in FP32. A trial whose bound is at most 6 keeps
+// X in 32 bits with 28 fractional bits (the states it uses stay below 8 in
+// magnitude; sums past a crossing may wrap and are never used); others in 64
+// bits with 40. Error against exact arithmetic stays near 1e-6 after 10,000
+// steps.
 //
 // Batched form: one trial per warp, 128 steps per iteration - lane i draws
 // block k/4 + i, an exact int64 warp scan gives every lane its X_b, and a
@@ -23,24 +26,42 @@ namespace dg {
 
 namespace {
 
+// Fixed-point formats of the state: 32 bits with 28 fractional bits (two's
+// complement, additions wrap), or 64 bits with 40.
+struct Fix32 {
+  using T = unsigned int;
+  __device__ __forceinline__ static T of(float v) {
+    return (T)__float2int_rn(v * 268435456.0f);   // 2^28
+  }
+  __device__ __forceinline__ static float val(T x) {
+    return __int2float_rn((int)x) * 3.7252902984619140625e-9f;   // 2^-28
+  }
+};
+struct Fix64 {
+  using T = long long;
+  __device__ __forceinline__ static T of(float v) { return to_fix(v); }
+  __device__ __forceinline__ static float val(T x) { return from_fix(x); }
+};
+constexpr float kFix32MaxBound = 6.0f;
+
 struct DdmTrial {
   float adt;        // A dt
   float z;          // threshold
-  long long x;      // state before the current block, fixed point
+  bool narrow;      // the state fits the 32-bit format
 };
 
 __device__ __forceinline__ DdmTrial ddm_begin(const DdmParams& p, long long t) {
   DdmTrial d;
   d.adt = __ldg(p.A + t) * p.dt;
   d.z = __ldg(p.z + t);
-  d.x = to_fix(p.x0);
+  d.narrow = d.z <= kFix32MaxBound && fabsf(p.x0) <= kFix32MaxBound;
   return d;
 }
 
 // In-block partial sums p_0 .. p_3 of block `block`.
 __device__ __forceinline__ void block_partials(const DdmParams& p, long long t, uint32_t block,
                                                float adt, float (&pre)[4]) {
-  const float4 e = normals4(noise_block(p.k0, p.k1, p.trial0 + (uint32_t)t, 0u, block));
+  const float4 e = normals4(philox_rk(make_uint4(p.trial0 + (uint32_t)t, 0u, block, 0u), p.rk));
   pre[0] = fmaf(p.diffusion, e.x, adt);
   pre[1] = pre[0] + fmaf(p.diffusion, e.y, adt);
   pre[2] = pre[1] + fmaf(p.diffusion, e.z, adt);
@@ -63,29 +84,45 @@ __device__ __forceinline__ void ddm_write(const DdmParams& p, long long t, bool 
 }
 
 // One trial per warp, 128 steps per iteration (the batched form).
-__device__ void ddm_trial_warp(const DdmParams& p, long long t) {
+template <typename F>
+__device__ __forceinline__ void ddm_trial_warp(const DdmParams& p, long long t,
+                                               const DdmTrial& d) {
+  using T = typename F::T;
   const int lane = threadIdx.x & 31;
-  const DdmTrial d = ddm_begin(p, t);
-  long long x = d.x;
+  T x = F::of(p.x0);
   for (int k = 0; k < p.max_steps; k += 128) {
     float pre[4];
     block_partials(p, t, (uint32_t)(k >> 2) + (uint32_t)lane, d.adt, pre);
-    const long long q = to_fix(pre[3]);
-    long long incl = q;   // exact scan of the block sums
+    const T q = F::of(pre[3]);
+    T incl = q;   // exact scan of the block sums
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const long long v = __shfl_up_sync(kFull, incl, o);
+      const T v = __shfl_up_sync(kFull, incl, o);
       if (lane >= o) incl += v;
     }
-    const float xb = from_fix(x + (incl - q));   // state before this lane's block
+    const float xb = F::val(x + (incl - q));   // state before this lane's block
     const int s0 = k + 4 * lane;
-    int first = 4;
+    // does any of this lane's four steps reach the bound? (the step cap only
+    // matters in the last chunk, a warp-uniform case)
+    bool hit;
+    if (k + 128 <= p.max_steps) {
+      const float m = fmaxf(fmaxf(fabsf(xb + pre[0]), fabsf(xb + pre[1])),
+                            fmaxf(fabsf(xb + pre[2]), fabsf(xb + pre[3])));
+      hit = m >= d.z;
+    } else {
+      hit = false;
 #pragma unroll
-    for (int j = 3; j >= 0; --j)
-      if (s0 + j < p.max_steps && fabsf(xb + pre[j]) >= d.z) first = j;
-    const unsigned hit_lanes = __ballot_sync(kFull, first < 4);
+      for (int j = 0; j < 4; ++j) hit |= s0 + j < p.max_steps && fabsf(xb + pre[j]) >= d.z;
+    }
+    const unsigned hit_lanes = __ballot_sync(kFull, hit);
     if (hit_lanes) {
-      if (lane == __ffs(hit_lanes) - 1) ddm_write(p, t, true, s0 + first + 1, xb + pick(pre, first));
+      if (lane == __ffs(hit_lanes) - 1) {
+        int first = 3;
+#pragma unroll
+        for (int j = 2; j >= 0; --j)
+          if (fabsf(xb + pre[j]) >= d.z) first = j;
+        ddm_write(p, t, true, s0 + first + 1, xb + pick(pre, first));
+      }
       return;
     }
     const int last = p.max_steps - 1 - k;   // step index of max_steps within this chunk
@@ -99,7 +136,7 @@ __device__ void ddm_trial_warp(const DdmParams& p, long long t) {
 
 // Persistent grid: each warp takes the next trial (in the hand-out order)
 // until none is left.
-__global__ void __launch_bounds__(256) ddm_batched(DdmParams p) {
+__global__ void __launch_bounds__(256, 8) ddm_batched(DdmParams p) {
   const int lane = threadIdx.x & 31;
   while (true) {
     unsigned long long f = 0;
@@ -107,20 +144,23 @@ __global__ void __launch_bounds__(256) ddm_batched(DdmParams p) {
     f = __shfl_sync(kFull, f, 0);
     if (f >= (unsigned long long)p.n) return;
     const long long t = p.perm ? (long long)__ldg(p.perm + f) : (long long)f;
-    ddm_trial_warp(p, t);
+    const DdmTrial d = ddm_begin(p, t);
+    if (d.narrow)
+      ddm_trial_warp<Fix32>(p, t, d);
+    else
+      ddm_trial_warp<Fix64>(p, t, d);
   }
 }
 
 // One thread per trial, one block after another (the plain form).
-__global__ void __launch_bounds__(256) ddm_plain(DdmParams p) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= p.n) return;
-  const DdmTrial d = ddm_begin(p, t);
-  long long x = d.x;
+template <typename F>
+__device__ __forceinline__ void ddm_trial_plain(const DdmParams& p, long long t,
+                                                const DdmTrial& d) {
+  typename F::T x = F::of(p.x0);
   for (int k = 0; k < p.max_steps; k += 4) {
     float pre[4];
     block_partials(p, t, (uint32_t)(k >> 2), d.adt, pre);
-    const float xb = from_fix(x);
+    const float xb = F::val(x);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if (k + j >= p.max_steps) break;
@@ -133,8 +173,18 @@ __global__ void __launch_bounds__(256) ddm_plain(DdmParams p) {
         return;
       }
     }
-    x += to_fix(pre[3]);
+    x += F::of(pre[3]);
   }
+}
+
+__global__ void __launch_bounds__(256) ddm_plain(DdmParams p) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.n) return;
+  const DdmTrial d = ddm_begin(p, t);
+  if (d.narrow)
+    ddm_trial_plain<Fix32>(p, t, d);
+  else
+    ddm_trial_plain<Fix64>(p, t, d);
 }
 
 }  // namespace

@@ -395,6 +395,7 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
     p.trial0 = (uint32_t)d->trial_offset;
     p.k0 = k0;
     p.k1 = k1;
+    p.rk = dg::philox_keys(k0, k1);
     p.dt = m->dt;
     p.diffusion = m->diffusion;
     p.x0 = m->x0;

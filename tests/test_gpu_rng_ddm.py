@@ -87,6 +87,28 @@ def test_ddm_short_caps(ctx, orc, max_steps):
         assert np.all(s <= max_steps)
 
 
+def test_ddm_bounds_on_both_state_formats(ctx, orc, threads):
+    """Bounds up to 6 keep the state in 32-bit fixed point, larger ones in 64
+    bits: a mix of both (and bounds right at the switch) against the oracle,
+    and the two forms bit for bit."""
+    rng = np.random.default_rng(11)
+    n = 3000
+    A = rng.uniform(2.0, 5.0, n).astype(np.float32)
+    z = rng.uniform(4.0, 9.0, n).astype(np.float32)
+    z[:50] = 6.0
+    z[50:100] = np.nextafter(np.float32(6.0), np.float32(7.0))
+    out = []
+    for mode in (0, 1):
+        c, s, x = _ddm_run(ctx, A, z, 21, mode)
+        ref = orc.ddm_run(A, z, 21, threads=threads)
+        assert compare_decisions(c, s, ref, f"wide bounds mode={mode}") <= n // 200
+        keep = ref["margin"] >= 1e-5
+        assert rel_err(x[keep], ref["x"][keep], z[keep]) < FLOAT_RTOL
+        out.append((c, s, x))
+    for u, v in zip(*out):
+        assert np.array_equal(u, v)
+
+
 def test_ddm_empty(ctx):
     c, s, x = _ddm_run(ctx, np.zeros(0, np.float32), np.zeros(0, np.float32), 1, 0)
     assert c.size == 0
