@@ -47,6 +47,12 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const Keys& rk) {
   return c;
 }
 
+template <typename Keys>
+__device__ __forceinline__ uint4 noise_block_rk(const Keys& rk, uint32_t trial, uint32_t cand,
+                                                uint32_t block) {
+  return philox_rk(make_uint4(trial, cand, block, 0u), rk);
+}
+
 __device__ __forceinline__ uint4 noise_block(uint32_t k0, uint32_t k1, uint32_t trial,
                                              uint32_t cand, uint32_t block) {
   return philox(make_uint4(trial, cand, block, 0u), k0, k1);

@@ -65,11 +65,11 @@ __device__ __forceinline__ void unit2(float vx, float vy, float& ox, float& oy) 
 // Perception and Action nodes: X^_e = X_e + sd_e eps_{2e+c} (normals 0..5 of
 // stream (trial, cand) starting at Philox block block0), then
 // act = unit(unit(Y^ - P^) - weight unit(D^ - P^)).
-__device__ __forceinline__ void pp_act(uint32_t k0, uint32_t k1, uint32_t trial, uint32_t cand,
+__device__ __forceinline__ void pp_act(const PhiloxKeys& rk, uint32_t trial, uint32_t cand,
                                        uint32_t block0, const float* X, float sd0, float sd1,
                                        float sd2, float weight, float& ax, float& ay) {
-  const float4 z = normals4(noise_block(k0, k1, trial, cand, block0));
-  const uint4 w1 = noise_block(k0, k1, trial, cand, block0 + 1u);
+  const float4 z = normals4(noise_block_rk(rk, trial, cand, block0));
+  const uint4 w1 = noise_block_rk(rk, trial, cand, block0 + 1u);
   float z4, z5;
   box_muller(w1.x, w1.y, z4, z5);
   const float phx = fmaf(sd0, z.x, X[0]), phy = fmaf(sd0, z.y, X[1]);
@@ -82,12 +82,12 @@ __device__ __forceinline__ void pp_act(uint32_t k0, uint32_t k1, uint32_t trial,
 }
 
 // Objective node: -|P + act - Y| - sum_e a_e^2 (cost given), true P and Y.
-__device__ __forceinline__ float pp_outcome_at(uint32_t k0, uint32_t k1, uint32_t trial,
+__device__ __forceinline__ float pp_outcome_at(const PhiloxKeys& rk, uint32_t trial,
                                                uint32_t cand, uint32_t block0, const float* X,
                                                float sd0, float sd1, float sd2, float weight,
                                                float cost) {
   float ax, ay;
-  pp_act(k0, k1, trial, cand, block0, X, sd0, sd1, sd2, weight, ax, ay);
+  pp_act(rk, trial, cand, block0, X, sd0, sd1, sd2, weight, ax, ay);
   const float nx = (X[0] + ax) - X[4];
   const float ny = (X[1] + ay) - X[5];
   return -sqrtf(nx * nx + ny * ny) - cost;

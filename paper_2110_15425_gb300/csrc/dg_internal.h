@@ -65,6 +65,7 @@ struct LcaParams {
   float* xout;         // [n][N], may be null
   unsigned long long* cursor;
   const unsigned int* perm;    // batched form: hand-out order (or null)
+  PhiloxKeys rk;                 // round keys of (k0, k1)
 };
 cudaError_t launch_lca(const LcaParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
 bool lca_tpt_supported(int N, int tpt);
@@ -119,6 +120,7 @@ struct NetParams {
   int32_t* step;
   float* yout;                   // [n][state_size], may be null
   unsigned long long* cursor;
+  PhiloxKeys rk;                 // round keys of (k0, k1)
 };
 cudaError_t launch_net(const NetParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
 
@@ -141,6 +143,7 @@ struct WideParams {
   float* yout;                   // [n][R], may be null
   unsigned long long* cursor;
   int* status;                   // device status word (bounded mbarrier waits)
+  PhiloxKeys rk;                 // round keys of (k0, k1)
 };
 cudaError_t launch_wide(const WideParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
 size_t wide_smem_bytes(int H, int nin, bool tc);
@@ -169,6 +172,7 @@ struct GridParams {
   TopTwo* partials;              // scratch, one per block
   unsigned int* ticket;          // scratch, zeroed per launch
   void* result;                  // dg_grid_result*
+  PhiloxKeys rk;                 // round keys of (k0, k1)
 };
 cudaError_t launch_grid(const GridParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
 int grid_blocks(int mode, long long n_cand, int n_trials);
@@ -203,6 +207,7 @@ struct EpisodeParams {
   int32_t* traj_best;            // [E][T] or null
   double* traj_value;            // [E][T] or null
   float* traj_pos;               // [E][T][6] or null
+  PhiloxKeys rk;                 // round keys of (k0, k1)
 };
 cudaError_t launch_episode_init(const EpisodeParams& p, cudaStream_t s);
 cudaError_t launch_episode_step(const EpisodeParams& p, cudaStream_t s);

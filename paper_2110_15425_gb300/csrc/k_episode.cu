@@ -114,7 +114,7 @@ __device__ void finish_episode(const EpisodeParams& p, int e) {
   if (lane < 3) {
     // perceived position of entity `lane` with the chosen allocation
     const float a = lane == 0 ? p.lv[0][l0] : (lane == 1 ? p.lv[1][l1] : p.lv[2][l2]);
-    const uint4 w = noise_block(p.k0, p.k1, (uint32_t)p.t, 0xFFFFFFFFu,
+    const uint4 w = noise_block_rk(p.rk, (uint32_t)p.t, 0xFFFFFFFFu,
                                 2u * (uint32_t)e + (lane == 2 ? 1u : 0u));
     double z0, z1;
     box_muller_f64(lane == 1 ? w.z : w.x, lane == 1 ? w.w : w.y, z0, z1);
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(256) episode_step(EpisodeParams p) {
       const float cost = a0 * a0 + a1 * a1 + a2 * a2;
       double acc = 0.0;
       for (int j = lane; j < p.n_trials; j += 32)
-        acc += (double)pp_outcome_at(p.k0, p.k1, trial0 + (uint32_t)j, (uint32_t)c,
+        acc += (double)pp_outcome_at(p.rk, trial0 + (uint32_t)j, (uint32_t)c,
                                      2u * (uint32_t)e, S, sd0, sd1, sd2, p.weight, cost);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);

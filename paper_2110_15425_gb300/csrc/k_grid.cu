@@ -37,8 +37,7 @@ namespace {
 __device__ __forceinline__ float pp_outcome(const GridParams& p, const float* pos, int j,
                                             uint32_t c, float sd0, float sd1, float sd2,
                                             float cost) {
-  return pp_outcome_at(p.k0, p.k1, (uint32_t)j, c, 0u, pos + 6 * j, sd0, sd1, sd2, p.weight,
-                       cost);
+  return pp_outcome_at(p.rk, (uint32_t)j, c, 0u, pos + 6 * j, sd0, sd1, sd2, p.weight, cost);
 }
 
 // c: global candidate index

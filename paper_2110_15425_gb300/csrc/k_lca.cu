@@ -28,7 +28,7 @@ struct Lca {
       const uint32_t b0 = (uint32_t)k * (uint32_t)(N / 4) + (uint32_t)(g * (NU / 4));
 #pragma unroll
       for (int b = 0; b < NU / 4; ++b) {
-        const float4 z = normals4(noise_block(p.k0, p.k1, trial, 0u, b0 + (uint32_t)b));
+        const float4 z = normals4(noise_block_rk(p.rk, trial, 0u, b0 + (uint32_t)b));
         e[4 * b + 0] = z.x;
         e[4 * b + 1] = z.y;
         e[4 * b + 2] = z.z;
@@ -41,7 +41,7 @@ struct Lca {
 #pragma unroll
       for (int i = 0; i < NU; ++i) {
         const uint32_t d = d0 + (uint32_t)i;
-        if (i == 0 || (d & 3u) == 0u) z = normals4(noise_block(p.k0, p.k1, trial, 0u, d >> 2));
+        if (i == 0 || (d & 3u) == 0u) z = normals4(noise_block_rk(p.rk, trial, 0u, d >> 2));
         e[i] = pick4(z, d & 3u);
       }
     }

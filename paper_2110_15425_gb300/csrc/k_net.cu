@@ -40,7 +40,7 @@ namespace {
 __device__ __forceinline__ float unit_noise(const NetParams& p, uint32_t trial, int k, int U,
                                             int u) {
   const uint32_t d = (uint32_t)k * (uint32_t)U + (uint32_t)u;
-  return pick4(normals4(noise_block(p.k0, p.k1, trial, 0u, d >> 2)), d & 3u);
+  return pick4(normals4(noise_block_rk(p.rk, trial, 0u, d >> 2)), d & 3u);
 }
 
 __device__ __forceinline__ float const_net(const NetParams& p, const NetLayout& L, long long t,
@@ -76,7 +76,7 @@ __device__ __forceinline__ DdmNode ddm_node_begin(const NetLayout& L, int q, flo
 // Four steps of node q (one Philox block); true when the node has ended.
 __device__ __forceinline__ bool ddm_node_block(const NetParams& p, uint32_t trial, int q,
                                                DdmNode& d, int& choice, int& step, float& x) {
-  const float4 e = normals4(noise_block(p.k0, p.k1, trial, 1u + (uint32_t)q, (uint32_t)d.b));
+  const float4 e = normals4(noise_block_rk(p.rk, trial, 1u + (uint32_t)q, (uint32_t)d.b));
   float pre[4];
   pre[0] = fmaf(d.diff, e.x, d.adt);
   pre[1] = pre[0] + fmaf(d.diff, e.y, d.adt);
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(128) net_plain(NetParams p) {
       for (int d = 0; d < L.D; ++d) net = fmaf(L.w[u][d], y[L.src[u][d] * B + tid], net);
       // the same normal as unit_noise, reusing a block across consecutive units
       const uint32_t dn = (uint32_t)k * (uint32_t)U + (uint32_t)u;
-      if (u == 0 || (dn & 3u) == 0u) z = normals4(noise_block(p.k0, p.k1, trial, 0u, dn >> 2));
+      if (u == 0 || (dn & 3u) == 0u) z = normals4(noise_block_rk(p.rk, trial, 0u, dn >> 2));
       const float e = pick4(z, dn & 3u);
       const float sv = fmaf(1.0f - L.rate, s[u * B + tid], fmaf(L.rate, net, L.noise * e));
       s[u * B + tid] = sv;

@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, 1) wide_kernel(WideParams p) {
       float e[8];
 #pragma unroll
       for (int b = 0; b < 2; ++b) {
-        const float4 z = normals4(noise_block(p.k0, p.k1, tg, 0u, blk0 + (uint32_t)(2 * c + b)));
+        const float4 z = normals4(noise_block_rk(p.rk, tg, 0u, blk0 + (uint32_t)(2 * c + b)));
         e[4 * b] = z.x;
         e[4 * b + 1] = z.y;
         e[4 * b + 2] = z.z;
@@ -283,8 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1) wide_kernel(WideParams p) {
                     part[(2 * kR + n) * kRows + r]) + part[(3 * kR + n) * kRows + r];
         }
       }
-      const float4 z = normals4(noise_block(
-          p.k0, p.k1, tg, 0u, (uint32_t)k * (uint32_t)(L::U / 4) + (uint32_t)(H / 4 + q)));
+      const float4 z = normals4(noise_block_rk(p.rk, tg, 0u, (uint32_t)k * (uint32_t)(L::U / 4) + (uint32_t)(H / 4 + q)));
       const float e4[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
       for (int j = 0; j < 4; ++j) {

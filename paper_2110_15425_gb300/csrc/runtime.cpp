@@ -437,6 +437,7 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
     p.N = m->N;
     p.k0 = k0;
     p.k1 = k1;
+    p.rk = dg::philox_keys(k0, k1);
     p.dt = m->dt;
     p.diffusion = m->diffusion;
     p.leak = m->leak;
@@ -491,6 +492,7 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
     p.trial0 = (uint32_t)d->trial_offset;
     p.k0 = k0;
     p.k1 = k1;
+    p.rk = dg::philox_keys(k0, k1);
     p.U = m->layout.U;
     p.n_in = m->layout.n_in;
     p.stop_size = m->layout.stop_size;
@@ -528,6 +530,7 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
     p.trial0 = (uint32_t)d->trial_offset;
     p.k0 = k0;
     p.k1 = k1;
+    p.rk = dg::philox_keys(k0, k1);
     p.choice = choice;
     p.step = step;
     p.yout = fs;
@@ -617,6 +620,7 @@ dg_status grid_device(dg_model* m, const dg_grid_desc* d, dg_grid_result* result
   p.n_trials = d->n_trials;
   p.k0 = (uint32_t)d->seed;
   p.k1 = (uint32_t)(d->seed >> 32);
+  p.rk = dg::philox_keys(p.k0, p.k1);
   p.offset = m->offset;
   p.weight = m->weight;
   const long long total = (long long)d->n_levels[0] * d->n_levels[1] * d->n_levels[2];
@@ -1121,6 +1125,7 @@ dg_status grid_params_noalloc(dg_model* m, const dg_grid_desc* d, dg_grid_result
   p->n_trials = d->n_trials;
   p->k0 = (uint32_t)d->seed;
   p->k1 = (uint32_t)(d->seed >> 32);
+  p->rk = dg::philox_keys(p->k0, p->k1);
   p->offset = m->offset;
   p->weight = m->weight;
   const long long total = (long long)d->n_levels[0] * d->n_levels[1] * d->n_levels[2];
@@ -1382,6 +1387,7 @@ dg_status dg_run_episodes(dg_model* m, const dg_episode_desc* d, const dg_episod
   p.n_trials = d->n_trials;
   p.k0 = (uint32_t)d->seed;
   p.k1 = (uint32_t)(d->seed >> 32);
+  p.rk = dg::philox_keys(p.k0, p.k1);
   p.offset = m->offset;
   p.weight = m->weight;
   p.offset_d = m->offset_d;
@@ -1447,6 +1453,7 @@ dg_status dg_grid_refine(dg_model* m, const dg_refine_desc* d, dg_refine_round* 
   p.n_trials = d->n_trials;
   p.k0 = (uint32_t)d->seed;
   p.k1 = (uint32_t)(d->seed >> 32);
+  p.rk = dg::philox_keys(p.k0, p.k1);
   p.offset = m->offset;
   p.weight = m->weight;
   p.cand0 = 0;
