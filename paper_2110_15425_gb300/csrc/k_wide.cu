@@ -194,9 +194,12 @@ __global__ void __launch_bounds__(kThreads, 1) wide_kernel(WideParams p) {
     float acc[kR];
 #pragma unroll
     for (int n = 0; n < kR; ++n) acc[n] = 0.f;
-    // eight hidden units (two Philox blocks) at a time
+    // eight hidden units (two Philox blocks) at a time; a warp whose 32 rows
+    // hold no running trial skips the work (its rows of D are not read)
+    const bool warp_live = __any_sync(kFull, active);
 #pragma unroll
     for (int c = 0; c < HQ / 8; ++c) {
+      if (!warp_live) break;
       float nv[8];
       if (TC) {
         tmem_ld8(tmem + lane_base + (uint32_t)(q * HQ + 8 * c), nv);
@@ -283,12 +286,15 @@ __global__ void __launch_bounds__(kThreads, 1) wide_kernel(WideParams p) {
                     part[(2 * kR + n) * kRows + r]) + part[(3 * kR + n) * kRows + r];
         }
       }
-      const float4 z = normals4(noise_block_rk(p.rk, tg, 0u, (uint32_t)k * (uint32_t)(L::U / 4) + (uint32_t)(H / 4 + q)));
-      const float e4[4] = {z.x, z.y, z.z, z.w};
+      if (warp_live) {
+        const float4 z = normals4(noise_block_rk(
+            p.rk, tg, 0u, (uint32_t)k * (uint32_t)(L::U / 4) + (uint32_t)(H / 4 + q)));
+        const float e4[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        sr[j] = fmaf(keep, sr[j], fmaf(p.rate, net[j], p.noise * e4[j]));
-        sh.yr[4 * q + j][r] = lg_r(sr[j]);
+        for (int j = 0; j < 4; ++j) {
+          sr[j] = fmaf(keep, sr[j], fmaf(p.rate, net[j], p.noise * e4[j]));
+          sh.yr[4 * q + j][r] = lg_r(sr[j]);
+        }
       }
     }
     phase ^= 1u;
