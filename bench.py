@@ -37,9 +37,21 @@ METRIC = "trial-steps/sec (hot-path pass: DDM, LCA, Stroop, wide Stroop, grid se
 UNIT = "trial-steps/s"
 WORKLOAD = ("hot-path pass: Stroop 4x1000 (weights seed 0) + DDM 2^20 + LCA 262144 x N{4,8,16} "
             "+ predator-prey grid 27000 cand x 64 trials + wide Stroop 16384 (16+16 -> 256 -> 16)")
-# algorithmic lane-operations per DDM trial-step (Philox4x32-10 quarter block,
-# one uniform and half a Box-Muller pair, the compensated update and the test)
+# Algorithmic FP32/INT32 lane-operations per unit of each kernel (the count a
+# minimal implementation of the same arithmetic needs; the kernels' own
+# instruction counts are higher):
+#   normal (a quarter Philox4x32-10 block: 10 rounds x 4 ops / 4 = 10; one
+#   uniform and half a Box-Muller pair: 9)                          19
+#   DDM trial-step: normal + fixed-point update, bound test         32
+#   LCA unit-step: normal + drive, update, rectify, sum and max     31
+#   logistic unit-step: normal + integrate (3) + logistic (4)       26
+#   Stroop trial-step: 6 logistic units, 24 edges, stop test        200
+#   wide trial-step: 272 logistic units + bf16 hi/lo split (3 each),
+#     16-way stop test; the 256 x 16 response GEMM runs on tensor cores  7,900
+#   grid evaluation: 6 normals, 3 normalisations, distance, FP64 add   120
 DDM_OPS_PER_TRIAL_STEP = 32
+OPS_PER_UNIT = {"ddm": 32, "lca4": 4 * 31, "lca8": 8 * 31, "lca16": 16 * 31, "stroop": 200,
+                "wide": 7900, "grid": 120}
 # DRAM bytes (read + write) of one ddm_batched launch over the 2^20-trial job,
 # from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
 # -k regex:ddm_batched -s 1 -c 1 python bench.py --only ddm` on the current
@@ -518,14 +530,27 @@ def main():
     dominant = max(per_job, key=lambda k: per_job[k]["ms"])
     sm_max = pk.get("sm_max_mhz", 2070.0)
     peak_ops = sms * LANES_PER_SM * sm_max * 1e6
-    ddm_ops = ts["ddm"] * DDM_OPS_PER_TRIAL_STEP
-    achieved = ddm_ops / (ddm_ms / 1000.0)
-    roofline = {"bound": "alu", "kernel": "ddm_batched", "achieved": achieved / 1e12,
-                "peak": peak_ops / 1e12, "unit": "Tlane-op/s", "frac": achieved / peak_ops,
-                "traffic": DDM_TRAFFIC_BYTES, "traffic_unit": "bytes per launch",
-                "peak_source": f"{sms} SMs x {LANES_PER_SM} FP32/INT32 lanes x {sm_max:.0f} MHz "
-                               f"({pk_kind} max SM clock)",
-                "ops_per_trial_step": DDM_OPS_PER_TRIAL_STEP, "dominant_in_pass": dominant}
+    peak_src = (f"{sms} SMs x {LANES_PER_SM} FP32/INT32 lanes x {sm_max:.0f} MHz "
+                f"({pk_kind} max SM clock)")
+    by_kernel = {}
+    for name, job in per_job.items():
+        ach = ts[name] * OPS_PER_UNIT[name] / (job["ms"] / 1000.0)
+        by_kernel[name] = {"achieved": ach / 1e12, "frac": ach / peak_ops,
+                           "ops_per_unit": OPS_PER_UNIT[name]}
+    kernel_names = {"ddm": "ddm_batched", "wide": "wide_kernel<256, tensor cores>",
+                    "lca4": "lca_batched<4,*>", "lca8": "lca_batched<8,*>",
+                    "lca16": "lca_batched<16,*>", "stroop": "net_group<8>",
+                    "grid": "grid_batched"}
+    # the dominant kernel of the pass (the longest job); DRAM traffic is known
+    # for the DDM kernel from the ncu capture named above
+    roofline = {"bound": "alu", "kernel": kernel_names[dominant],
+                "achieved": by_kernel[dominant]["achieved"], "peak": peak_ops / 1e12,
+                "unit": "Tlane-op/s", "frac": by_kernel[dominant]["frac"],
+                "traffic": DDM_TRAFFIC_BYTES if dominant == "ddm" else None,
+                "peak_source": peak_src, "ops_per_unit": OPS_PER_UNIT[dominant],
+                "by_kernel": by_kernel,
+                "ddm": {"kernel": "ddm_batched", "frac": by_kernel["ddm"]["frac"],
+                        "traffic": DDM_TRAFFIC_BYTES, "traffic_unit": "bytes per launch"}}
 
     # end to end through the serving API with pinned host buffers
     e2e = None
