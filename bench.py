@@ -55,10 +55,10 @@ OPS_PER_UNIT = {"ddm": 32, "lca4": 4 * 31, "lca8": 8 * 31, "lca16": 16 * 31, "st
 # DRAM bytes (read + write) of one ddm_batched launch over the 2^20-trial job,
 # from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
 # -k regex:ddm_batched -s 1 -c 1 python bench.py --only ddm` on the current
-# kernel (profiles/ddm_batched_2p20_trials.md): 12,593,408 read + 0 written
+# kernel (profiles/ddm_batched_2p20_trials.md): 12,598,784 read + 0 written
 # (the 5 MB of outputs stay in L2 within the launch). Algorithmic: 8 B of
 # parameters in and 5 B out per trial = 13.6 MB.
-DDM_TRAFFIC_BYTES = 12_593_408
+DDM_TRAFFIC_BYTES = 12_598_784
 LANES_PER_SM = 128
 WIDE_TRIALS = 16384
 

@@ -49,6 +49,34 @@ __device__ __forceinline__ TopTwo top_warp(TopTwo t) {
   return t;
 }
 
+// Candidate sums. Each lane adds its trials' FP32 outcomes into a compensated
+// pair (hi, lo): Knuth's TwoSum keeps the rounding error of every addition
+// exactly and lo collects them, so hi + lo carries the sum to about 2^-48 of
+// its magnitude. The warp combines the pairs the same way and hi + lo is
+// converted to FP64 once per candidate, for up to 32 candidates in one
+// instruction: the double-precision unit, slow on this GPU, does a handful of
+// operations per 32 candidates instead of two per trial.
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (v - bp);
+  hi = s;
+}
+
+// Warp total of the lanes' pairs, returned to every lane (tree toward lane 0,
+// then broadcast, so every lane holds the same pair).
+__device__ __forceinline__ void warp_pair_sum(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_down_sync(kFull, hi, o);
+    const float ol = __shfl_down_sync(kFull, lo, o);
+    two_sum_add(hi, lo, oh);
+    lo += ol;
+  }
+  hi = __shfl_sync(kFull, hi, 0);
+  lo = __shfl_sync(kFull, lo, 0);
+}
+
 // unit(v), with unit(0) = 0
 __device__ __forceinline__ void unit2(float vx, float vy, float& ox, float& oy) {
   const float n2 = vx * vx + vy * vy;

@@ -209,7 +209,12 @@ __global__ void __launch_bounds__(256) episode_step(EpisodeParams p) {
     for (int d = 0; d < 6; ++d) S[d] = __ldcg(p.state + 6 * e + d);
     TopTwo best = top_init();
     const long long c_end = min((long long)(chunk + 1) * kEpisodeChunk, p.n_cand);
-    for (long long c = (long long)chunk * kEpisodeChunk + warp; c < c_end; c += 8) {
+    // the warp's candidates c0 + 8 i: lane i keeps candidate i's pair, and the
+    // eight means are formed in FP64 together at the end
+    const long long c0 = (long long)chunk * kEpisodeChunk + warp;
+    float kh = 0.f, kl = 0.f;
+    long long kc = -1;
+    for (long long c = c0; c < c_end; c += 8) {
       const int l2 = (int)(c % p.L[2]);
       const int l1 = (int)((c / p.L[2]) % p.L[1]);
       const int l0 = (int)(c / ((long long)p.L[2] * p.L[1]));
@@ -217,15 +222,18 @@ __global__ void __launch_bounds__(256) episode_step(EpisodeParams p) {
       const float sd0 = 1.0f / (p.offset + a0), sd1 = 1.0f / (p.offset + a1),
                   sd2 = 1.0f / (p.offset + a2);
       const float cost = a0 * a0 + a1 * a1 + a2 * a2;
-      double acc = 0.0;
+      float hi = 0.f, lo = 0.f;
       for (int j = lane; j < p.n_trials; j += 32)
-        acc += (double)pp_outcome_at(p.rk, trial0 + (uint32_t)j, (uint32_t)c,
-                                     2u * (uint32_t)e, S, sd0, sd1, sd2, p.weight, cost);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
-      const double mean = __shfl_sync(kFull, acc, 0) * inv;
-      best = top_merge(best, TopTwo{mean, c, -DBL_MAX});
+        two_sum_add(hi, lo, pp_outcome_at(p.rk, trial0 + (uint32_t)j, (uint32_t)c,
+                                          2u * (uint32_t)e, S, sd0, sd1, sd2, p.weight, cost));
+      warp_pair_sum(hi, lo);
+      if (lane == (int)((c - c0) / 8)) {
+        kh = hi;
+        kl = lo;
+        kc = c;
+      }
     }
+    if (kc >= 0) best = TopTwo{((double)kh + (double)kl) * inv, kc, -DBL_MAX};
     best = top_warp(best);
     if (lane == 0) warp_best[warp] = best;
     __syncthreads();

@@ -8,10 +8,10 @@
 //   outcome = -|P + act - Y| - sum_e a_e^2                      (true P, Y)
 // mean_c = FP64 mean of the outcomes; best = argmax_c mean_c, lowest c on ties.
 //
-// Batched form: one warp per candidate (trials spread over the lanes), FP64
-// shuffle reduction, running top-2 per warp, block merge, then the last block
-// to finish merges the per-block partials (no second launch, no atomics on
-// the values). Plain form (the paper's mapping): one thread per candidate
+// Batched form: one warp per candidate (trials spread over the lanes), a
+// compensated FP32 pair sum across the lanes converted to the FP64 mean,
+// running top-2 per warp, block merge, then the last block to finish merges
+// the per-block partials (no second launch, no atomics on the values). Plain form (the paper's mapping): one thread per candidate
 // with a sequential FP64 sum, then a separate argmax launch.
 //
 // Random tie-break (Sec. 3.3: one of several equally good choices is picked at
@@ -114,6 +114,19 @@ __global__ void __launch_bounds__(256) grid_batched(GridParams p) {
   const int wpb = blockDim.x >> 5;
   TopTwo best = top_init();
   const double inv = 1.0 / (double)p.n_trials;
+  // lane `slot` keeps the pair of the warp's slot-th pending candidate; every
+  // 32 candidates (and at the end) all lanes convert theirs to FP64 at once
+  float kh = 0.f, kl = 0.f;
+  long long kc = -1;
+  int slot = 0;
+  auto flush = [&]() {
+    if (kc >= 0) {
+      const double mean = ((double)kh + (double)kl) * inv;
+      if (p.means) p.means[kc] = mean;
+      best = top_merge(best, TopTwo{mean, p.cand0 + kc, -DBL_MAX});
+    }
+    kc = -1;
+  };
   for (long long c = (long long)blockIdx.x * wpb + warp; c < p.n_cand;
        c += (long long)gridDim.x * wpb) {
     const long long cg = p.cand0 + c;
@@ -122,17 +135,21 @@ __global__ void __launch_bounds__(256) grid_batched(GridParams p) {
     const float sd0 = 1.0f / (p.offset + a0), sd1 = 1.0f / (p.offset + a1),
                 sd2 = 1.0f / (p.offset + a2);
     const float cost = a0 * a0 + a1 * a1 + a2 * a2;
-    double acc = 0.0;
+    float hi = 0.f, lo = 0.f;
     for (int j = lane; j < p.n_trials; j += 32)
-      acc += (double)pp_outcome(p, pos, j, p.stream0 + (uint32_t)cg, sd0, sd1, sd2, cost);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
-    const double mean = __shfl_sync(kFull, acc, 0) * inv;
-    if (lane == 0) {
-      if (p.means) p.means[c] = mean;
-      best = top_merge(best, TopTwo{mean, cg, -DBL_MAX});
+      two_sum_add(hi, lo, pp_outcome(p, pos, j, p.stream0 + (uint32_t)cg, sd0, sd1, sd2, cost));
+    warp_pair_sum(hi, lo);
+    if (lane == slot) {
+      kh = hi;
+      kl = lo;
+      kc = c;
+    }
+    if (++slot == 32) {
+      flush();
+      slot = 0;
     }
   }
+  flush();
   finish_argmax(best, p.partials, p.ticket, p.result);
 }
 
