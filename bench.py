@@ -220,7 +220,12 @@ class Step:
         return ts
 
     def kernels_per_step(self):
-        return len(self.jobs)
+        """Kernels of one pass: one per job, plus the three-kernel trial-order
+        sort (histogram, scan, scatter) before each DDM and LCA job of at
+        least 4,096 trials."""
+        sorted_jobs = sum(1 for j in self.jobs
+                          if (j["name"] == "ddm" or j["name"].startswith("lca")) and j["n"] >= 4096)
+        return len(self.jobs) + 3 * sorted_jobs
 
 
 # ---------------------------------------------------------------- clocks ---
