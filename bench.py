@@ -661,6 +661,22 @@ def extensions(B, W, torch, ctx, grid_ms):
             ms_graph = _time_ms(torch, graph.replay)
         except Exception as exc:  # capture refused: report it, keep the eager number
             ms_graph = f"capture failed: {exc}"
+        # the launch-per-round form of the same search, for comparison
+        os.environ["DG_REFINE_FUSED"] = "0"
+        try:
+            B.dg_grid_refine(pp, rd, rounds, stream=side)
+            side.synchronize()
+            graph2 = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph2, stream=side):
+                B.dg_grid_refine(pp, rd, rounds, stream=side)
+            graph2.replay()
+            ms_graph_rounds = _time_ms(torch, graph2.replay)
+        except Exception as exc:
+            ms_graph_rounds = f"capture failed: {exc}"
+        finally:
+            del os.environ["DG_REFINE_FUSED"]
+        B.dg_grid_refine(pp, rd, rounds, stream=side)
+        side.synchronize()
         rr = B.refine_rounds(rounds.cpu().numpy())
         full = torch.zeros(3, dtype=torch.float64, device="cuda")
         lv = [cuda(x) for x in g["levels"]]
@@ -680,7 +696,8 @@ def extensions(B, W, torch, ctx, grid_ms):
             return float(r.cpu().numpy()[1])
         out["coarse_to_fine"] = {
             "points": G, "rounds": R, "trials": 64, "candidates": R * G ** 3,
-            "ms_eager": ms_eager, "ms_graph": ms_graph, "kernel_launches": 1 + 2 * R,
+            "ms_eager": ms_eager, "ms_graph": ms_graph, "kernel_launches": 1,
+            "form": "one 8-CTA cluster launch", "ms_graph_launch_per_round": ms_graph_rounds,
             "full_grid_candidates": nc, "full_grid_ms": grid_ms,
             "alloc": [float(a) for a in rr["alloc"][-1]], "full_grid_alloc": [float(a) for a in full_alloc],
             "value_fresh_1024": value_of(rr["alloc"][-1]),

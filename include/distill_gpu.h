@@ -314,7 +314,9 @@ typedef struct {
 
 /* Run a coarse-to-fine search on a PREDATOR_PREY model. rounds: device,
    dg_refine_round[desc->rounds], written in order (entry rounds-1 holds the
-   answer). 1 + 2 R kernel launches, no host synchronisation (capturable).
+   answer). Up to 8,192 candidates per round (G <= 20) the search is one
+   launch of one 8-CTA thread-block cluster; larger grids take 1 + 2 R
+   launches. No host synchronisation (capturable).
    Errors: DG_E_ARG (bad sizes, domain or pointers), DG_E_UNSUPPORTED (not a
    PREDATOR_PREY model), DG_E_CUDA. */
 dg_status dg_grid_refine(dg_model* model, const dg_refine_desc* desc, dg_refine_round* rounds,

@@ -222,6 +222,17 @@ struct RefineParams {
   void* rounds;                  // dg_refine_round[R]
   unsigned int* ticket;          // the grid launch's argmax ticket, reset for the next round
 };
+// The whole refinement in one launch of one thread-block cluster.
+constexpr int kRefineCluster = 8;
+struct RefineFusedParams {
+  float lo0[3], hi0[3];
+  int G, R, n_trials;
+  const float* pos;              // [n_trials][6]
+  PhiloxKeys rk;
+  float offset, weight;
+  void* rounds;                  // dg_refine_round[R]
+};
+cudaError_t launch_refine_fused(const RefineFusedParams& p, cudaStream_t s);
 // Levels and box of round 0.
 cudaError_t launch_refine_init(const RefineParams& p, cudaStream_t s);
 // After round r's grid launch: record the best allocation and lay out round r + 1.

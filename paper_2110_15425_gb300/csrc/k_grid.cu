@@ -256,6 +256,17 @@ __device__ __forceinline__ float refine_level(float lo, float hi, int l, int G) 
   return __double2float_rn(__dadd_rn((double)lo, t));
 }
 
+// The next interval: the best level +- one grid spacing, clipped to the domain.
+__device__ __forceinline__ void refine_next(float center, float lo, float hi, float lo0,
+                                            float hi0, int G, float& nlo, float& nhi) {
+  const double sp = __ddiv_rn(__dsub_rn((double)hi, (double)lo), (double)(G - 1));
+  double a = __dsub_rn((double)center, sp), z = __dadd_rn((double)center, sp);
+  if (a < (double)lo0) a = (double)lo0;
+  if (z > (double)hi0) z = (double)hi0;
+  nlo = __double2float_rn(a);
+  nhi = __double2float_rn(z);
+}
+
 __device__ __forceinline__ void refine_layout(const RefineParams& p, const float* lo,
                                               const float* hi, float* lv) {
   const int l = threadIdx.x;
@@ -284,16 +295,9 @@ __global__ void refine_step(RefineParams p, int r) {
   if (b < 0 || b >= (long long)G * G * G) b = 0;  // only after a failed round
   const int lb[3] = {(int)(b / ((long long)G * G)), (int)((b / G) % G), (int)(b % G)};
   float nlo[3], nhi[3];
-  for (int e = 0; e < 3; ++e) {
-    const float center = cur[e * kRefineMaxPoints + lb[e]];
-    const double lo = rounds[r].lo[e], hi = rounds[r].hi[e];
-    const double sp = __ddiv_rn(__dsub_rn(hi, lo), (double)(G - 1));
-    double a = __dsub_rn((double)center, sp), z = __dadd_rn((double)center, sp);
-    if (a < (double)p.lo0[e]) a = (double)p.lo0[e];
-    if (z > (double)p.hi0[e]) z = (double)p.hi0[e];
-    nlo[e] = __double2float_rn(a);
-    nhi[e] = __double2float_rn(z);
-  }
+  for (int e = 0; e < 3; ++e)
+    refine_next(cur[e * kRefineMaxPoints + lb[e]], rounds[r].lo[e], rounds[r].hi[e], p.lo0[e],
+                p.hi0[e], G, nlo[e], nhi[e]);
   __syncthreads();  // every thread has read round r before round r + 1 is written
   if (threadIdx.x == 0) {
     for (int e = 0; e < 3; ++e) rounds[r].alloc[e] = cur[e * kRefineMaxPoints + lb[e]];
@@ -307,6 +311,149 @@ __global__ void refine_step(RefineParams p, int r) {
       rounds[r + 1].hi[e] = nhi[e];
     }
     rounds[r + 1].round = r + 1;
+  }
+}
+
+// ------------------------------------------- coarse-to-fine, one cluster ---
+// The whole refinement in one launch: a cluster of kRefineCluster CTAs (1,024
+// threads each) evaluates a round's candidates, one warp per candidate as
+// grid_batched does; each CTA publishes its top-2 in shared memory, every CTA
+// reads all of them through distributed shared memory after a cluster
+// barrier, and each lays out the next round itself (the same arithmetic, so
+// the CTAs agree). A second cluster barrier keeps a round's top-2 readable
+// until every CTA has read it. Results equal the launch-per-round form bit
+// for bit; the per-round launches and their gaps disappear.
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+
+// Address of `local` (a shared variable) in the shared memory of cluster CTA `rank`.
+__device__ __forceinline__ uint32_t cluster_addr(const void* local, uint32_t rank) {
+  uint32_t a = (uint32_t)__cvta_generic_to_shared(local), r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ TopTwo load_remote_top(const TopTwo* local, uint32_t rank) {
+  const uint32_t a = cluster_addr(local, rank);
+  TopTwo t;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(t.v1) : "r"(a) : "memory");
+  asm volatile("ld.shared::cluster.s64 %0, [%1];" : "=l"(t.i1) : "r"(a + 8u) : "memory");
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(t.v2) : "r"(a + 16u) : "memory");
+  return t;
+}
+
+__global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(1024, 1)
+    refine_fused(RefineFusedParams p) {
+  extern __shared__ float sm[];              // positions [n_trials][6]
+  __shared__ float lv[3][kRefineMaxPoints];  // this round's levels
+  __shared__ float box[6];                   // this round's lo[3], hi[3]
+  __shared__ TopTwo warp_best[32];
+  __shared__ TopTwo cta_best;
+  const uint32_t rank = cluster_rank();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int W = 32 * kRefineCluster, gw = (int)rank * 32 + warp;
+  const int G = p.G;
+  RefineRoundDev* rounds = reinterpret_cast<RefineRoundDev*>(p.rounds);
+  for (int i = tid; i < 6 * p.n_trials; i += blockDim.x) sm[i] = __ldg(p.pos + i);
+  if (tid < 3) {
+    box[tid] = p.lo0[tid];
+    box[3 + tid] = p.hi0[tid];
+  }
+  __syncthreads();
+  if (tid < G)
+    for (int e = 0; e < 3; ++e) lv[e][tid] = refine_level(box[e], box[3 + e], tid, G);
+  __syncthreads();
+  const long long n_cand = (long long)G * G * G;
+  const double inv = 1.0 / (double)p.n_trials;
+  for (int r = 0; r < p.R; ++r) {
+    const uint32_t stream0 = (uint32_t)((long long)r * n_cand);
+    TopTwo best = top_init();
+    float kh = 0.f, kl = 0.f;
+    long long kc = -1;
+    int slot = 0;
+    auto flush = [&]() {
+      if (kc >= 0) best = top_merge(best, TopTwo{((double)kh + (double)kl) * inv, kc, -DBL_MAX});
+      kc = -1;
+    };
+    for (long long c = gw; c < n_cand; c += W) {
+      const int l2 = (int)(c % G), l1 = (int)((c / G) % G), l0 = (int)(c / ((long long)G * G));
+      const float a0 = lv[0][l0], a1 = lv[1][l1], a2 = lv[2][l2];
+      const float sd0 = 1.0f / (p.offset + a0), sd1 = 1.0f / (p.offset + a1),
+                  sd2 = 1.0f / (p.offset + a2);
+      const float cost = a0 * a0 + a1 * a1 + a2 * a2;
+      float hi = 0.f, lo = 0.f;
+      for (int j = lane; j < p.n_trials; j += 32)
+        two_sum_add(hi, lo, pp_outcome_at(p.rk, (uint32_t)j, stream0 + (uint32_t)c, 0u, sm + 6 * j,
+                                          sd0, sd1, sd2, p.weight, cost));
+      warp_pair_sum(hi, lo);
+      if (lane == slot) {
+        kh = hi;
+        kl = lo;
+        kc = c;
+      }
+      if (++slot == 32) {
+        flush();
+        slot = 0;
+      }
+    }
+    flush();
+    best = top_warp(best);
+    if (lane == 0) warp_best[warp] = best;
+    __syncthreads();
+    if (warp == 0) {
+      const TopTwo t = top_warp(warp_best[lane]);
+      if (lane == 0) cta_best = t;
+    }
+    cluster_sync_all();   // every CTA's top-2 is published
+    if (warp == 0) {
+      // lane q reads CTA q's top-2; the warp merges them
+      TopTwo t = lane < kRefineCluster ? load_remote_top(&cta_best, (uint32_t)lane) : top_init();
+      t = top_warp(t);
+      long long b = t.i1;
+      if (b < 0 || b >= n_cand) b = 0;
+      const int lb[3] = {(int)(b / ((long long)G * G)), (int)((b / G) % G), (int)(b % G)};
+      // lanes 0-2: the best level of signal `lane` and its next interval
+      const int e = lane < 3 ? lane : 0;
+      const float center = lv[e][lb[e]];
+      float nlo = 0.f, nhi = 0.f;
+      if (lane < 3) refine_next(center, box[e], box[3 + e], p.lo0[e], p.hi0[e], G, nlo, nhi);
+      const float c0 = __shfl_sync(kFull, center, 0), c1 = __shfl_sync(kFull, center, 1),
+                  c2 = __shfl_sync(kFull, center, 2);
+      if (rank == 0 && lane == 0) {
+        RefineRoundDev& o = rounds[r];
+        o.alloc[0] = c0;
+        o.alloc[1] = c1;
+        o.alloc[2] = c2;
+        for (int q = 0; q < 3; ++q) {
+          o.lo[q] = box[q];
+          o.hi[q] = box[3 + q];
+        }
+        o.round = r;
+        o.best_index = t.i1;
+        o.value = t.v1;
+        o.gap = (t.v2 == -DBL_MAX) ? 0.0 : t.v1 - t.v2;
+      }
+      __syncwarp();
+      if (lane < 3) {
+        box[e] = nlo;
+        box[3 + e] = nhi;
+      }
+    }
+    cluster_sync_all();   // every CTA has read this round's top-2 (and this CTA's box is set)
+    if (r + 1 < p.R) {
+      if (tid < G)
+        for (int e = 0; e < 3; ++e) lv[e][tid] = refine_level(box[e], box[3 + e], tid, G);
+      __syncthreads();
+    }
   }
 }
 
@@ -354,6 +501,12 @@ cudaError_t launch_grid(const GridParams& p, int mode, const LaunchCfg& cfg, cud
   const long long need = (p.n_cand + block / 32 - 1) / (block / 32);
   if (grid > need) grid = (int)need;
   grid_batched<<<grid, block, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_fused(const RefineFusedParams& p, cudaStream_t s) {
+  const size_t smem = sizeof(float) * 6 * (size_t)p.n_trials;
+  refine_fused<<<kRefineCluster, 1024, smem, s>>>(p);
   return cudaGetLastError();
 }
 

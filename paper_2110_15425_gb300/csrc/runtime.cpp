@@ -1435,6 +1435,26 @@ dg_status dg_grid_refine(dg_model* m, const dg_refine_desc* d, dg_refine_round* 
       return fail(DG_E_ARG, "dg_grid_refine: domain of signal %d is not a finite lo <= hi", e);
   DG_CUDA(cudaSetDevice(m->ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
+  // up to 8,192 candidates a round: the whole search as one cluster launch
+  // (DG_REFINE_FUSED=0 selects the launch-per-round form)
+  const char* fe = getenv("DG_REFINE_FUSED");
+  if (n_cand <= 8192 && !(fe && atoi(fe) == 0)) {
+    dg::RefineFusedParams fp{};
+    for (int e = 0; e < 3; ++e) {
+      fp.lo0[e] = d->lo[e];
+      fp.hi0[e] = d->hi[e];
+    }
+    fp.G = G;
+    fp.R = R;
+    fp.n_trials = d->n_trials;
+    fp.pos = d->positions;
+    fp.rk = dg::philox_keys((uint32_t)d->seed, (uint32_t)(d->seed >> 32));
+    fp.offset = m->offset;
+    fp.weight = m->weight;
+    fp.rounds = rounds;
+    DG_CUDA(dg::launch_refine_fused(fp, s));
+    return DG_OK;
+  }
   Scratch* sc = nullptr;
   dg_status st = get_scratch(m->ctx, s, &sc);
   if (st != DG_OK) return st;

@@ -108,3 +108,15 @@ def test_refine_rejects_bad_arguments(ctx):
                 B.dg_grid_refine(model, B.refine_desc(pos, lo, hi, G, R, 1), out)
     finally:
         B.dg_model_free(model)
+
+
+@pytest.mark.parametrize("G,R,n_trials", [(5, 7, 64), (4, 3, 1), (9, 4, 100), (20, 2, 33)])
+def test_refine_cluster_form_equals_launch_per_round(ctx, monkeypatch, G, R, n_trials):
+    """The one-cluster search and the launch-per-round search agree bit for bit."""
+    from paper_2110_15425_gb300 import workloads as W
+    w = W.predator_prey(n_trials=n_trials)
+    monkeypatch.setenv("DG_REFINE_FUSED", "0")
+    a = _refine(ctx, w["pos"], [0, 0.1, 0], [1, 0.9, 2], G, R, w["seed"])
+    monkeypatch.setenv("DG_REFINE_FUSED", "1")
+    b = _refine(ctx, w["pos"], [0, 0.1, 0], [1, 0.9, 2], G, R, w["seed"])
+    assert a.tobytes() == b.tobytes()
