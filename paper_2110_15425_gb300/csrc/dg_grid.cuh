@@ -18,19 +18,32 @@ struct GridResultDev {           // dg_grid_result
 
 __device__ __forceinline__ TopTwo top_init() { return TopTwo{-DBL_MAX, LLONG_MAX, -DBL_MAX}; }
 
+// Order of doubles as 64-bit integers: for every non-NaN x, y,
+// okey(x) < okey(y) exactly when x < y (zero of either sign maps to 0, so the
+// two zeros compare equal as they do in IEEE arithmetic). The merges below
+// compare and select through these keys on the integer units: the
+// double-precision unit of this GPU is a small fraction of its FP32 rate, and
+// in the small, latency-bound searches its compares dominated.
+__device__ __forceinline__ long long okey(double v) {
+  long long b = __double_as_longlong(v);
+  if (b == (long long)0x8000000000000000ull) b = 0;
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
+
 // Merge two running top-2 summaries: best value with lowest index on ties,
 // and the largest value among the rest.
 __device__ __forceinline__ TopTwo top_merge(TopTwo a, TopTwo b) {
-  const bool b_wins = (b.v1 > a.v1) || (b.v1 == a.v1 && b.i1 < a.i1);
+  const long long ka = okey(a.v1), kb = okey(b.v1);
+  const bool b_wins = (kb > ka) || (kb == ka && b.i1 < a.i1);
   TopTwo r;
   if (b_wins) {
     r.v1 = b.v1;
     r.i1 = b.i1;
-    r.v2 = fmax(a.v1, b.v2);
+    r.v2 = okey(a.v1) > okey(b.v2) ? a.v1 : b.v2;
   } else {
     r.v1 = a.v1;
     r.i1 = a.i1;
-    r.v2 = fmax(b.v1, a.v2);
+    r.v2 = okey(b.v1) > okey(a.v2) ? b.v1 : a.v2;
   }
   return r;
 }

@@ -250,16 +250,28 @@ struct RefineRoundDev {          // dg_refine_round
 };
 static_assert(sizeof(RefineRoundDev) == 64, "dg_refine_round layout");
 
+// x / (G - 1), correctly rounded. A power-of-two divisor has an exact
+// reciprocal, and the product then rounds exactly as the quotient does; the
+// double-precision divide, a long sequence on this GPU, is left for other G.
+__device__ __forceinline__ double div_g1(double x, int G) {
+  const int d = G - 1;
+  if ((d & (d - 1)) == 0) {
+    const long long k = __ffs(d) - 1;   // d = 2^k
+    return __dmul_rn(x, __longlong_as_double((1023ll - k) << 52));   // 2^-k
+  }
+  return __ddiv_rn(x, (double)d);
+}
+
 __device__ __forceinline__ float refine_level(float lo, float hi, int l, int G) {
   const double w = __dsub_rn((double)hi, (double)lo);
-  const double t = __ddiv_rn(__dmul_rn(w, (double)l), (double)(G - 1));
+  const double t = div_g1(__dmul_rn(w, (double)l), G);
   return __double2float_rn(__dadd_rn((double)lo, t));
 }
 
 // The next interval: the best level +- one grid spacing, clipped to the domain.
 __device__ __forceinline__ void refine_next(float center, float lo, float hi, float lo0,
                                             float hi0, int G, float& nlo, float& nhi) {
-  const double sp = __ddiv_rn(__dsub_rn((double)hi, (double)lo), (double)(G - 1));
+  const double sp = div_g1(__dsub_rn((double)hi, (double)lo), G);
   double a = __dsub_rn((double)center, sp), z = __dadd_rn((double)center, sp);
   if (a < (double)lo0) a = (double)lo0;
   if (z > (double)hi0) z = (double)hi0;
@@ -369,8 +381,8 @@ __global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(1024, 1
     box[3 + tid] = p.hi0[tid];
   }
   __syncthreads();
-  if (tid < G)
-    for (int e = 0; e < 3; ++e) lv[e][tid] = refine_level(box[e], box[3 + e], tid, G);
+  // one level per thread: thread e G + l computes level l of signal e
+  if (tid < 3 * G) lv[tid / G][tid % G] = refine_level(box[tid / G], box[3 + tid / G], tid % G, G);
   __syncthreads();
   const long long n_cand = (long long)G * G * G;
   const double inv = 1.0 / (double)p.n_trials;
@@ -450,8 +462,8 @@ __global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(1024, 1
     }
     cluster_sync_all();   // every CTA has read this round's top-2 (and this CTA's box is set)
     if (r + 1 < p.R) {
-      if (tid < G)
-        for (int e = 0; e < 3; ++e) lv[e][tid] = refine_level(box[e], box[3 + e], tid, G);
+      if (tid < 3 * G)
+        lv[tid / G][tid % G] = refine_level(box[tid / G], box[3 + tid / G], tid % G, G);
       __syncthreads();
     }
   }
