@@ -66,6 +66,7 @@ struct LcaParams {
   unsigned long long* cursor;
   const unsigned int* perm;    // batched form: hand-out order (or null)
   PhiloxKeys rk;                 // round keys of (k0, k1)
+  int chunk;                     // compacting form: steps between compactions
 };
 cudaError_t launch_lca(const LcaParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
 bool lca_tpt_supported(int N, int tpt);

@@ -196,6 +196,105 @@ __global__ void __launch_bounds__(256) lca_batched(LcaParams p) {
   }
 }
 
+// Batched form with block-level compaction (one lane per trial). With about
+// as many lanes as trials every trial starts at once and a warp would run
+// until its slowest lane ends. Here the block runs in chunks of p.chunk steps;
+// after each chunk the trials still running are packed into the block's
+// leading lanes through shared memory (trial, step, state, next noise), the
+// freed lanes take new trials from the cursor, and warps left without a trial
+// sit out the next chunk. Lanes change trials, never results.
+// Shared memory of lca_compact<N>: x, I and next-step noise per lane, trial and step.
+inline size_t compact_smem(int N) { return (3 * (size_t)N * 256) * sizeof(float) + 256 * (8 + 4); }
+
+template <int N>
+__global__ void __launch_bounds__(256) lca_compact(LcaParams p) {
+  using L = Lca<N, 1>;
+  extern __shared__ __align__(16) float csm[];
+  float* s_x = csm;                          // [N][256]
+  float* s_I = csm + N * 256;                // [N][256]
+  float* s_e = csm + 2 * N * 256;            // [N][256]
+  long long* s_t = reinterpret_cast<long long*>(csm + 3 * N * 256);   // [256]
+  int* s_k = reinterpret_cast<int*>(s_t + 256);                        // [256]
+  __shared__ int warp_cnt[8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned self = 1u << lane;
+  float x[N], I[N], e[N];
+  long long t = 0;
+  int k = 0;
+  long long f = fetch_trial(p.cursor, true);
+  bool active = f >= 0 && f < p.n;
+  if (active) {
+    t = p.perm ? (long long)__ldg(p.perm + f) : f;
+    L::load(p, t, 0, x, I);
+    L::noise(p, p.trial0 + (uint32_t)t, 0, 0, e);
+  }
+  while (true) {
+    // ---- a chunk of steps
+    if (__any_sync(kFull, active)) {
+      for (int s = 0; s < p.chunk; ++s) {
+        if (active) {
+          float en[N];
+          L::noise(p, p.trial0 + (uint32_t)t, k + 1, 0, en);
+          int8_t c = -1;
+          const bool hit = L::step(p, e, 0, self, x, I, c);
+          ++k;
+          if (hit || k >= p.max_steps) {
+            L::store(p, t, 0, hit ? c : (int8_t)-1, hit ? k : p.max_steps, x);
+            active = false;
+          }
+#pragma unroll
+          for (int i = 0; i < N; ++i) e[i] = en[i];
+        }
+        if (!__any_sync(kFull, active)) break;
+      }
+    }
+    // ---- pack the running trials into the leading lanes
+    const unsigned live = __ballot_sync(kFull, active);
+    if (lane == 0) warp_cnt[warp] = __popc(live);
+    __syncthreads();
+    int before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const int c = warp_cnt[w];
+      if (w < warp) before += c;
+      total += c;
+    }
+    if (active) {
+      const int d = before + __popc(live & (self - 1u));
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        s_x[i * 256 + d] = x[i];
+        s_I[i * 256 + d] = I[i];
+        s_e[i * 256 + d] = e[i];
+      }
+      s_t[d] = t;
+      s_k[d] = k;
+    }
+    __syncthreads();
+    active = tid < total;
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        x[i] = s_x[i * 256 + tid];
+        I[i] = s_I[i * 256 + tid];
+        e[i] = s_e[i * 256 + tid];
+      }
+      t = s_t[tid];
+      k = s_k[tid];
+    }
+    // ---- the free lanes take new trials
+    f = fetch_trial(p.cursor, !active);
+    if (!active && f >= 0 && f < p.n) {
+      active = true;
+      t = p.perm ? (long long)__ldg(p.perm + f) : f;
+      k = 0;
+      L::load(p, t, 0, x, I);
+      L::noise(p, p.trial0 + (uint32_t)t, 0, 0, e);
+    }
+    if (!__syncthreads_or(active ? 1 : 0)) break;
+  }
+}
+
 template <int N>
 __global__ void __launch_bounds__(256) lca_plain(LcaParams p) {
   using L = Lca<N, 1>;
@@ -233,10 +332,24 @@ cudaError_t launch_n(const LcaParams& p, int mode, const LaunchCfg& cfg, cudaStr
   const int block = cfg.block;
   int grid = cfg.grid;
   if (grid <= 0) grid = num_sms() * lca_max_blocks_per_sm(N, cfg.tpt, block);
-  const long long need = (p.n * cfg.tpt + block - 1) / block;
+  const long long need = (p.n * (cfg.tpt > 0 ? cfg.tpt : 1) + block - 1) / block;
   if (grid > need) grid = (int)need;
   if (grid < 1) grid = 1;
   switch (cfg.tpt) {
+    case 0: {   // block-level compaction, one lane per trial (256 threads)
+      if constexpr (N <= 16) {
+        const size_t smem = compact_smem(N);
+        static bool attr = false;
+        if (!attr) {
+          cudaFuncSetAttribute(lca_compact<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+          attr = true;
+        }
+        lca_compact<N><<<grid, 256, smem, s>>>(p);
+        break;
+      }
+      return cudaErrorInvalidValue;
+    }
     case 1: lca_batched<N, 1><<<grid, block, 0, s>>>(p); break;
     case 2:
       if constexpr (N % 8 == 0) { lca_batched<N, 2><<<grid, block, 0, s>>>(p); break; }
@@ -249,8 +362,22 @@ cudaError_t launch_n(const LcaParams& p, int mode, const LaunchCfg& cfg, cudaStr
   return cudaGetLastError();
 }
 
+template <int N>
+void* compact_fn() {
+  return (void*)lca_compact<N>;
+}
+
 void* kernel_for(int N, int tpt) {
   switch (tpt) {
+    case 0:
+      switch (N) {
+#define DG_CASE(n) case n: return compact_fn<n>();
+        DG_CASE(1) DG_CASE(2) DG_CASE(3) DG_CASE(4) DG_CASE(5) DG_CASE(6) DG_CASE(7) DG_CASE(8)
+        DG_CASE(9) DG_CASE(10) DG_CASE(11) DG_CASE(12) DG_CASE(13) DG_CASE(14) DG_CASE(15)
+        DG_CASE(16)
+#undef DG_CASE
+      }
+      return nullptr;
     case 1:
       switch (N) {
 #define DG_CASE(n) case n: return batched_fn<n, 1>();
@@ -279,7 +406,12 @@ int lca_max_blocks_per_sm(int N, int tpt, int block) {
   void* fn = kernel_for(N, tpt);
   if (!fn) return 0;
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0);
+  if (tpt == 0) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)compact_smem(N));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, compact_smem(N));
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0);
+  }
   return nb;
 }
 

@@ -342,8 +342,10 @@ int forced_tpt() {
 std::vector<dg::LaunchCfg> lca_candidates(int N) {
   std::vector<dg::LaunchCfg> v;
   const int only = forced_tpt();
-  for (int tpt : {1, 2, 4}) {
-    if (!dg::lca_tpt_supported(N, tpt) || (only && tpt != only)) continue;
+  // tpt 0: one lane per trial with block-level compaction of running trials
+  for (int tpt : {0, 1, 2, 4}) {
+    if (!dg::lca_tpt_supported(N, tpt) || (only > 0 && tpt != only) || (only < 0 && tpt != 0))
+      continue;
     const int occ = std::max(1, dg::lca_max_blocks_per_sm(N, tpt, 256));
     for (int div : {1, 2, 4}) {
       if (div > 1 && occ / div < 1) continue;
@@ -446,6 +448,10 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
     p.max_steps = m->max_steps;
     p.rectify = m->rectify;
     p.two_sided = m->two_sided;
+    {
+      const char* e = getenv("DG_LCA_CHUNK");   // steps between compactions
+      p.chunk = e && atoi(e) > 0 ? atoi(e) : 32;
+    }
     p.choice = choice;
     p.step = step;
     p.xout = fs;

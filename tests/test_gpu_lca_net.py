@@ -36,13 +36,14 @@ def _lca(ctx, I, seed, mode, **kw):
 
 
 @pytest.mark.parametrize("N,tpt", [(4, 1), (8, 1), (8, 2), (16, 1), (16, 2), (16, 4), (5, 1),
-                                   (3, 1), (1, 1)])
+                                   (3, 1), (1, 1), (4, -1), (8, -1), (16, -1), (5, -1), (1, -1)])
 def test_lca_parity(ctx, orc, threads, monkeypatch, N, tpt):
     from paper_2110_15425_gb300 import workloads as W
     monkeypatch.setenv("DG_LCA_TPT", str(tpt))
     w = W.lca(n_trials=3000 + 7, N=N)
     kw = dict(leak=w["leak"], inhibition=w["inhibition"], sigma=w["sigma"], dt=w["dt"],
               threshold=w["threshold"], max_steps=w["max_steps"])
+    # tpt -1: one lane per trial with block-level compaction of the running trials
     for mode in ((0, 1) if tpt == 1 else (0,)):
         c, s, x = _lca(ctx, w["I"], w["seed"], mode, **kw)
         ref = orc.lca_run(w["I"], w["seed"], threads=threads, **kw)
@@ -52,10 +53,13 @@ def test_lca_parity(ctx, orc, threads, monkeypatch, N, tpt):
         assert np.all(x >= 0)
 
 
-def test_lca_batched_equals_plain_bitwise(ctx):
-    """The batched form hands trials out longest-expected-first and splits a
-    trial over several lanes; neither changes any result bit."""
+@pytest.mark.parametrize("tpt", ["1", "-1"])
+def test_lca_batched_equals_plain_bitwise(ctx, monkeypatch, tpt):
+    """The batched form hands trials out longest-expected-first, splits a
+    trial over several lanes or moves it between lanes when it compacts the
+    running trials; none of this changes any result bit."""
     from paper_2110_15425_gb300 import workloads as W
+    monkeypatch.setenv("DG_LCA_TPT", tpt)
     for N in (4, 8, 16):
         w = W.lca(n_trials=30000, N=N)
         a = _lca(ctx, w["I"], w["seed"], 0)
