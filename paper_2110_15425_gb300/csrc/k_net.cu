@@ -37,10 +37,15 @@ namespace dg {
 
 namespace {
 
+// Normal k U + u of the trial's stream: only the Box-Muller pair that holds it.
 __device__ __forceinline__ float unit_noise(const NetParams& p, uint32_t trial, int k, int U,
                                             int u) {
   const uint32_t d = (uint32_t)k * (uint32_t)U + (uint32_t)u;
-  return pick4(normals4(noise_block_rk(p.rk, trial, 0u, d >> 2)), d & 3u);
+  const uint4 w = noise_block_rk(p.rk, trial, 0u, d >> 2);
+  const bool second = (d & 2u) != 0u;
+  float z0, z1;
+  box_muller(second ? w.z : w.x, second ? w.w : w.y, z0, z1);
+  return (d & 1u) ? z1 : z0;
 }
 
 __device__ __forceinline__ float const_net(const NetParams& p, const NetLayout& L, long long t,
@@ -143,7 +148,13 @@ __global__ void __launch_bounds__(256) net_group(NetParams p) {
   long long t = f;
   int k = 0;
   float s = 0.f, y = lg(0.f), netc = 0.f;
-  if (active && real) netc = const_net(p, L, t, u);
+  // the noise of step k is drawn during step k - 1 (it does not depend on the
+  // state), off the step's chain of shuffles and updates
+  float e_next = 0.f;
+  if (active && real) {
+    netc = const_net(p, L, t, u);
+    e_next = unit_noise(p, p.trial0 + (uint32_t)t, 0, L.U, u);
+  }
   // phase 1 (EXT): the DDM nodes
   int phase = 0, net_step = 0;
   bool ddone = true;
@@ -161,7 +172,8 @@ __global__ void __launch_bounds__(256) net_group(NetParams p) {
         if (real) net = fmaf(L.w[u][d], yv, net);
       }
       if (real) {
-        const float e = unit_noise(p, p.trial0 + (uint32_t)t, k, L.U, u);
+        const float e = e_next;
+        e_next = unit_noise(p, p.trial0 + (uint32_t)t, k + 1, L.U, u);
         s = fmaf(1.0f - L.rate, s, fmaf(L.rate, net, L.noise * e));
         y = lg(s);
       }
@@ -231,6 +243,7 @@ __global__ void __launch_bounds__(256) net_group(NetParams p) {
       s = 0.f;
       y = lg(0.f);
       netc = (active && real) ? const_net(p, L, t, u) : 0.f;
+      if (active && real) e_next = unit_noise(p, p.trial0 + (uint32_t)t, 0, L.U, u);
       phase = 0;
       ddone = true;
     }
