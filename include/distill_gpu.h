@@ -239,7 +239,8 @@ dg_status dg_grid_search(dg_model* model, const dg_grid_desc* desc, dg_grid_resu
    start[e] = (player xy, predator xy, prey xy). At step t = 0, 1, ...:
      - every allocation c (layout as dg_grid_search) is simulated on n_trials
        perceptions of the current positions, noise stream (trial t n_trials + j,
-       cand c) at Philox blocks 2e and 2e + 1; FP64 mean; best = argmax
+       cand c) at Philox blocks 2e and 2e + 1 (e the global episode index,
+       episode_offset + row); FP64 mean; best = argmax
        (lowest index on exact ties);
      - the player perceives once more with the best allocation (stream
        (trial t, cand 0xFFFFFFFF), same blocks) and moves speed[0] times the
@@ -260,6 +261,9 @@ typedef struct {
   uint64_t seed;
   double speed[3];            /* step lengths of player, predator, prey (>= 0) */
   double capture_radius;      /* >= 0 */
+  int64_t episode_offset;     /* global index of episode 0 (its noise), >= 0; with
+                                 offset + E <= 2^31 - 1 a call reproduces episodes
+                                 offset .. offset + E - 1 of a larger run */
 } dg_episode_desc;
 
 /* Outputs of dg_run_episodes (device pointers, caller-owned). */

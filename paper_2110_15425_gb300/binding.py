@@ -70,7 +70,8 @@ class dg_episode_desc(C.Structure):
     _fields_ = [("n_episodes", C.c_int32), ("max_steps", C.c_int32),
                 ("n_levels", C.c_int32 * 3), ("n_trials", C.c_int32),
                 ("levels", C.c_void_p * 3), ("start", C.c_void_p), ("seed", C.c_uint64),
-                ("speed", C.c_double * 3), ("capture_radius", C.c_double)]
+                ("speed", C.c_double * 3), ("capture_radius", C.c_double),
+                ("episode_offset", C.c_int64)]
 
 
 class dg_episode_out(C.Structure):
@@ -260,8 +261,10 @@ def dg_argmax_f64(ctx, values, result, stream=None):
                               stream_handle(stream)))
 
 
-def episode_desc(levels, start, n_trials, max_steps, seed, speed=(1.0, 0.6, 0.5), radius=1.0):
+def episode_desc(levels, start, n_trials, max_steps, seed, speed=(1.0, 0.6, 0.5), radius=1.0,
+                 episode_offset=0):
     d = dg_episode_desc()
+    d.episode_offset = episode_offset
     d._keep = (tuple(levels), start)
     d.n_episodes = start.shape[0]
     d.max_steps = max_steps

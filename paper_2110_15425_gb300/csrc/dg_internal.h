@@ -194,6 +194,7 @@ struct EpisodeParams {
   double speed[3];               // player, predator, prey
   double radius;
   int E, T;                      // episodes, maximum steps
+  uint32_t e0;                   // global index of episode 0
   int t;                         // the step a launch performs
   const float* start;            // [E][6]
   float* state;                  // [E][6] positions at the start of the step

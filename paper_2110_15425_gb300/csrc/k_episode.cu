@@ -5,8 +5,9 @@
 //
 // Episode e keeps its positions S = (P, D, Y) in device memory. Step t:
 //   - every allocation c is simulated on n_trials perceptions of S (noise
-//     stream (trial t n_trials + j, cand c), Philox blocks 2e and 2e + 1), FP64
-//     mean, best = argmax (lowest index on ties);
+//     stream (trial t n_trials + j, cand c), Philox blocks 2e and 2e + 1, e
+//     the global episode index), FP64 mean, best = argmax (lowest index on
+//     ties);
 //   - the player perceives S once more with the best allocation (stream
 //     (trial t, cand 0xFFFFFFFF)) and moves speed[0] act; the predator steps
 //     speed[1] unit(P - D) toward it, the prey speed[2] unit(Y - P) away, all
@@ -115,7 +116,7 @@ __device__ void finish_episode(const EpisodeParams& p, int e) {
     // perceived position of entity `lane` with the chosen allocation
     const float a = lane == 0 ? p.lv[0][l0] : (lane == 1 ? p.lv[1][l1] : p.lv[2][l2]);
     const uint4 w = noise_block_rk(p.rk, (uint32_t)p.t, 0xFFFFFFFFu,
-                                2u * (uint32_t)e + (lane == 2 ? 1u : 0u));
+                                2u * (p.e0 + (uint32_t)e) + (lane == 2 ? 1u : 0u));
     double z0, z1;
     box_muller_f64(lane == 1 ? w.z : w.x, lane == 1 ? w.w : w.y, z0, z1);
     const double sd = __ddiv_rn(1.0, __dadd_rn(p.offset_d, (double)a));
@@ -225,7 +226,8 @@ __global__ void __launch_bounds__(256) episode_step(EpisodeParams p) {
       float hi = 0.f, lo = 0.f;
       for (int j = lane; j < p.n_trials; j += 32)
         two_sum_add(hi, lo, pp_outcome_at(p.rk, trial0 + (uint32_t)j, (uint32_t)c,
-                                          2u * (uint32_t)e, S, sd0, sd1, sd2, p.weight, cost));
+                                          2u * (p.e0 + (uint32_t)e), S, sd0, sd1, sd2, p.weight,
+                                          cost));
       warp_pair_sum(hi, lo);
       if (lane == (int)((c - c0) / 8)) {
         kh = hi;

@@ -1364,6 +1364,8 @@ dg_status dg_run_episodes(dg_model* m, const dg_episode_desc* d, const dg_episod
   if (!(d->capture_radius >= 0.0) || !std::isfinite(d->capture_radius))
     return fail(DG_E_ARG, "dg_run_episodes: capture_radius must be finite and >= 0");
   if (!d->start) return fail(DG_E_ARG, "dg_run_episodes: null start positions");
+  if (d->episode_offset < 0 || d->episode_offset + d->n_episodes > INT32_MAX)
+    return fail(DG_E_ARG, "dg_run_episodes: episode_offset + n_episodes must lie in [0, 2^31 - 1]");
   const long long n_cand = (long long)d->n_levels[0] * d->n_levels[1] * d->n_levels[2];
   if (n_cand > 0xFFFFFFFFll) return fail(DG_E_ARG, "dg_run_episodes: more than 2^32 - 1 candidates");
   const long long cpe = (n_cand + dg::kEpisodeChunk - 1) / dg::kEpisodeChunk;
@@ -1401,6 +1403,7 @@ dg_status dg_run_episodes(dg_model* m, const dg_episode_desc* d, const dg_episod
   p.radius = d->capture_radius;
   p.E = (int)E;
   p.T = d->max_steps;
+  p.e0 = (uint32_t)d->episode_offset;
   p.start = d->start;
   p.state = reinterpret_cast<float*>(x);
   p.active = reinterpret_cast<int*>(x + b_state);

@@ -135,3 +135,53 @@ def test_episode_independent_of_batch(ctx):
     b = _episodes(ctx, w, start=w["start"][:5])
     for k in ("outcome", "steps", "final", "best", "value", "pos"):
         assert np.array_equal(a[k][:5], b[k][:5]), k
+
+
+def test_episode_offset_reassembles(ctx):
+    """Episodes 0..11 in one call equal episodes 0..4 and 5..11 run as two calls
+    with episode_offset 0 and 5 (the noise is keyed by the global index)."""
+    import torch
+    from paper_2110_15425_gb300 import binding as B
+    from paper_2110_15425_gb300 import workloads as W
+    w = W.predator_prey_episodes(n_episodes=12, levels=5, n_trials=8, max_steps=40)
+    full = _episodes(ctx, w)
+    model = B.compose_predator_prey(ctx, obs_offset=w["obs_offset"], pred_weight=w["pred_weight"])
+    try:
+        for lo, hi in ((0, 5), (5, 12)):
+            E, T = hi - lo, 40
+            oc = torch.zeros(E, dtype=torch.int8, device="cuda")
+            st = torch.zeros(E, dtype=torch.int32, device="cuda")
+            best = torch.zeros(E * T, dtype=torch.int32, device="cuda")
+            pos = torch.zeros(E * T * 6, dtype=torch.float32, device="cuda")
+            d = B.episode_desc([dev(l) for l in w["levels"]], dev(w["start"][lo:hi]), 8, T,
+                               w["seed"], speed=w["speed"], radius=w["radius"], episode_offset=lo)
+            B.dg_run_episodes(model, d, B.episode_out(oc, st, None, best, None, pos))
+            assert np.array_equal(host(oc), full["outcome"][lo:hi])
+            assert np.array_equal(host(st), full["steps"][lo:hi])
+            assert np.array_equal(host(best).reshape(E, T), full["best"][lo:hi])
+            assert np.array_equal(host(pos).reshape(E, T, 6), full["pos"][lo:hi])
+    finally:
+        B.dg_model_free(model)
+
+
+def test_episode_bad_arguments(ctx):
+    import torch
+    from paper_2110_15425_gb300 import binding as B
+    from paper_2110_15425_gb300 import workloads as W
+    w = W.predator_prey_episodes(n_episodes=2, levels=3, n_trials=4, max_steps=5)
+    model = B.compose_predator_prey(ctx)
+    oc = torch.zeros(2, dtype=torch.int8, device="cuda")
+    st = torch.zeros(2, dtype=torch.int32, device="cuda")
+    lv = [dev(l) for l in w["levels"]]
+    start = dev(w["start"])
+    try:
+        for kw in (dict(n_trials=0), dict(n_trials=2000), dict(speed=(-1.0, 0.5, 0.5)),
+                   dict(radius=float("nan")), dict(episode_offset=-1), dict(max_steps=0)):
+            args = dict(n_trials=4, max_steps=5, speed=w["speed"], radius=w["radius"], episode_offset=0)
+            args.update(kw)
+            d = B.episode_desc(lv, start, args["n_trials"], args["max_steps"], 1, speed=args["speed"],
+                               radius=args["radius"], episode_offset=args["episode_offset"])
+            with pytest.raises(B.DGError):
+                B.dg_run_episodes(model, d, B.episode_out(oc, st))
+    finally:
+        B.dg_model_free(model)
