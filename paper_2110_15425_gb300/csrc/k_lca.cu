@@ -206,6 +206,43 @@ __global__ void __launch_bounds__(256) lca_batched(LcaParams p) {
 // Shared memory of lca_compact<N>: x, I and next-step noise per lane, trial and step.
 inline size_t compact_smem(int N) { return (3 * (size_t)N * 256) * sizeof(float) + 256 * (8 + 4); }
 
+// The rest of one trial on a whole warp (N a multiple of 4): the lanes draw
+// the noise of 32 / (N / 4) steps at once (lane l: Philox block l mod N/4 of
+// step k + l div (N/4)), then every lane takes those steps on its own copy of
+// the state, gathering each step's normals by shuffles. The arithmetic is the
+// one-lane step's, so the trial ends exactly as it would have.
+template <int N>
+__device__ void lca_warp_trial(const LcaParams& p, long long t, int k, float (&x)[N],
+                               const float (&I)[N]) {
+  using L = Lca<N, 1>;
+  constexpr int NB = N / 4, R = 32 / NB;
+  const int lane = threadIdx.x & 31;
+  const uint32_t trial = p.trial0 + (uint32_t)t;
+  while (true) {
+    const float4 z = normals4(noise_block_rk(
+        p.rk, trial, 0u, (uint32_t)(k + lane / NB) * (uint32_t)NB + (uint32_t)(lane % NB)));
+#pragma unroll 1
+    for (int s = 0; s < R; ++s) {
+      float e[N];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const int src = s * NB + b;
+        e[4 * b] = __shfl_sync(kFull, z.x, src);
+        e[4 * b + 1] = __shfl_sync(kFull, z.y, src);
+        e[4 * b + 2] = __shfl_sync(kFull, z.z, src);
+        e[4 * b + 3] = __shfl_sync(kFull, z.w, src);
+      }
+      int8_t c = -1;
+      const bool hit = L::step(p, e, 0, kFull, x, I, c);
+      ++k;
+      if (hit || k >= p.max_steps) {
+        if (lane == 0) L::store(p, t, 0, hit ? c : (int8_t)-1, hit ? k : p.max_steps, x);
+        return;
+      }
+    }
+  }
+}
+
 template <int N>
 __global__ void __launch_bounds__(256) lca_compact(LcaParams p) {
   using L = Lca<N, 1>;
@@ -284,12 +321,28 @@ __global__ void __launch_bounds__(256) lca_compact(LcaParams p) {
     }
     // ---- the free lanes take new trials
     f = fetch_trial(p.cursor, !active);
-    if (!active && f >= 0 && f < p.n) {
+    const bool refilled = !active && f >= 0 && f < p.n;
+    if (refilled) {
       active = true;
       t = p.perm ? (long long)__ldg(p.perm + f) : f;
       k = 0;
       L::load(p, t, 0, x, I);
       L::noise(p, p.trial0 + (uint32_t)t, 0, 0, e);
+    }
+    if constexpr (N % 4 == 0) {
+      // no trial left to hand out and at most one per warp still running: a
+      // warp each, so that the last, longest trials run at a warp's pace
+      if (!__syncthreads_or(refilled ? 1 : 0) && total > 0 && total <= 8) {
+        if (warp < total) {
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            x[i] = s_x[i * 256 + warp];
+            I[i] = s_I[i * 256 + warp];
+          }
+          lca_warp_trial<N>(p, s_t[warp], s_k[warp], x, I);
+        }
+        return;
+      }
     }
     if (!__syncthreads_or(active ? 1 : 0)) break;
   }
