@@ -81,6 +81,8 @@ def parse():
                     help="one job of this kind, default launch shape, 1 warm + 1 timed launch "
                          "(the small case for per-kernel ncu captures)")
     ap.add_argument("--n", type=int, default=0, help="trials (or candidates) for --only")
+    ap.add_argument("--hidden", type=int, default=256,
+                    help="hidden units of the wide network for --only wide (64, 128, 192, 256)")
     return ap.parse_args()
 
 
@@ -401,7 +403,8 @@ def run_only(args):
             p = cuda(w["I"])
             d = B.run_desc(w["I"].shape[0], w["seed"], trial_params=p)
         else:
-            w = W.stroop_small() if k == "stroop" else W.stroop_wide(n_trials=args.n or WIDE_TRIALS)
+            w = (W.stroop_small() if k == "stroop" else
+                 W.stroop_wide(n_trials=args.n or WIDE_TRIALS, hidden=args.hidden))
             m = B.compose_network(ctx, w["layers"], w["projections"], rate=w["rate"],
                                   noise_sd=w["noise_sd"], stop_layer=w["stop_layer"],
                                   stop_threshold=w["stop_threshold"], max_steps=w["max_steps"],
@@ -420,7 +423,10 @@ def run_only(args):
     go()
     e1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"only": k, "n": args.n, "ms": e0.elapsed_time(e1)}))
+    out = {"only": k, "n": args.n, "ms": e0.elapsed_time(e1)}
+    if k not in ("grid", "refine", "episodes"):
+        out["trial_steps"] = int(st.to(torch.int64).sum().item())
+    print(json.dumps(out))
     B.dg_model_free(m)
     B.dg_destroy(ctx)
 

@@ -85,7 +85,7 @@ WIDE_RESP = 16
 
 def stroop_wide(weight_seed: int = 4, noise_seed: int = 5, n_trials: int = 65536,
                 hidden_range: float = 6.0, resp_range: float = 2.0, resp_bias: float = -8.0,
-                max_steps: int = 500):
+                max_steps: int = 500, hidden: int = WIDE_HIDDEN):
     """Wide multitask network. Trial t: stimulus t % 16, task (t // 16) % 16,
     i.e. condition t % 256 with condition c = task*16 + stim.
 
@@ -97,13 +97,13 @@ def stroop_wide(weight_seed: int = 4, noise_seed: int = 5, n_trials: int = 65536
     layers = [
         dict(name="stimulus", size=WIDE_STIM, input=True),
         dict(name="task", size=WIDE_TASK, input=True),
-        dict(name="hidden", size=WIDE_HIDDEN, input=False, gain=1.0, bias=-4.0),
+        dict(name="hidden", size=hidden, input=False, gain=1.0, bias=-4.0),
         dict(name="response", size=WIDE_RESP, input=False, gain=1.0, bias=resp_bias),
     ]
     projections = [
-        (0, 2, _u(rng, -hidden_range, hidden_range, (WIDE_HIDDEN, WIDE_STIM))),
-        (1, 2, _u(rng, -hidden_range, hidden_range, (WIDE_HIDDEN, WIDE_TASK))),
-        (2, 3, _u(rng, -resp_range, resp_range, (WIDE_RESP, WIDE_HIDDEN))),
+        (0, 2, _u(rng, -hidden_range, hidden_range, (hidden, WIDE_STIM))),
+        (1, 2, _u(rng, -hidden_range, hidden_range, (hidden, WIDE_TASK))),
+        (2, 3, _u(rng, -resp_range, resp_range, (WIDE_RESP, hidden))),
     ]
     cond = np.zeros((WIDE_STIM * WIDE_TASK, WIDE_STIM + WIDE_TASK), F32)
     for c in range(WIDE_STIM * WIDE_TASK):
