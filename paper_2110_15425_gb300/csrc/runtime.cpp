@@ -688,7 +688,7 @@ struct Server {
     // Job memory comes from the stream-ordered allocator: allocation and
     // release are ordered on the job's stream and never synchronize the
     // device, so admitted jobs keep overlapping. The pool keeps freed memory
-    // for reuse instead of returning it to the driver.
+    // for reuse instead of returning it to the CUDA driver.
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
       uint64_t keep = UINT64_MAX;
