@@ -141,6 +141,19 @@ __global__ void __launch_bounds__(256) net_group(NetParams p) {
   const bool real = u < L.U;
   const bool in_stop = u >= L.stop_off && u < L.stop_off + L.stop_size;
   const Logistic lg = Logistic::of(real ? L.gain[u] : 1.f, real ? L.bias[u] : 0.f);
+  // this lane's layout in registers: constants and up to kEdgeRegs incoming
+  // edges (the rest, if any, are read from shared memory each step)
+  constexpr int kEdgeRegs = 8;
+  const int D = L.D;
+  const float rate = L.rate, keep = 1.0f - L.rate, noise = L.noise, thr = L.stop_threshold;
+  const int max_steps = L.max_steps, stop_off = L.stop_off;
+  int esrc[kEdgeRegs];
+  float ew[kEdgeRegs];
+#pragma unroll
+  for (int d = 0; d < kEdgeRegs; ++d) {
+    esrc[d] = real && d < D ? L.src[u][d] : 0;
+    ew[d] = real && d < D ? L.w[u][d] : 0.f;
+  }
 
   long long f = fetch_trial(p.cursor, u == 0);
   f = __shfl_sync(kFull, f, root);
@@ -166,7 +179,14 @@ __global__ void __launch_bounds__(256) net_group(NetParams p) {
     if (active && (!EXT || phase == 0)) {
       // synchronous: every lane reads the step k outputs before any update
       float net = netc;
-      for (int d = 0; d < L.D; ++d) {
+#pragma unroll
+      for (int d = 0; d < kEdgeRegs; ++d) {
+        if (d < D) {
+          const float yv = __shfl_sync(gmask, y, root + esrc[d]);
+          if (real) net = fmaf(ew[d], yv, net);
+        }
+      }
+      for (int d = kEdgeRegs; d < D; ++d) {
         const int si = real ? L.src[u][d] : 0;
         const float yv = __shfl_sync(gmask, y, root + si);
         if (real) net = fmaf(L.w[u][d], yv, net);
@@ -174,12 +194,12 @@ __global__ void __launch_bounds__(256) net_group(NetParams p) {
       if (real) {
         const float e = e_next;
         e_next = unit_noise(p, p.trial0 + (uint32_t)t, k + 1, L.U, u);
-        s = fmaf(1.0f - L.rate, s, fmaf(L.rate, net, L.noise * e));
+        s = fmaf(keep, s, fmaf(rate, net, noise * e));
         y = lg(s);
       }
       // top-1 (lowest index on ties) and top-2 of the stop layer
       float v1 = in_stop ? y : -FLT_MAX, v2 = -FLT_MAX;
-      int i1 = in_stop ? u - L.stop_off : 1 << 20;
+      int i1 = in_stop ? u - stop_off : 1 << 20;
 #pragma unroll
       for (int o = 1; o < G; o <<= 1) {
         const float ov1 = __shfl_xor_sync(gmask, v1, o);
@@ -194,9 +214,9 @@ __global__ void __launch_bounds__(256) net_group(NetParams p) {
         }
       }
       ++k;
-      const bool hit = v1 - v2 > L.stop_threshold;
-      if (hit || k >= L.max_steps) {
-        if (p.yout && in_stop) p.yout[(size_t)t * p.state_size + (u - L.stop_off)] = y;
+      const bool hit = v1 - v2 > thr;
+      if (hit || k >= max_steps) {
+        if (p.yout && in_stop) p.yout[(size_t)t * p.state_size + (u - stop_off)] = y;
         if (!EXT || L.n_ddm == 0) {
           if (u == 0) {
             p.choice[t] = hit ? (int8_t)i1 : (int8_t)-1;
