@@ -60,6 +60,15 @@ OPS_PER_UNIT = {"ddm": 32, "lca4": 4 * 31, "lca8": 8 * 31, "lca16": 16 * 31, "st
 # parameters in and 5 B out per trial = 13.6 MB.
 DDM_TRAFFIC_BYTES = 12_598_784
 LANES_PER_SM = 128
+# The pass's jobs, longest first. Graph branches are created (and served jobs
+# submitted) in this order: the wide network's CTAs take their SMs before the
+# persistent kernels fill the GPU (2-4 % shorter passes than job order).
+LONGEST_FIRST = ("wide", "ddm", "lca16", "lca8", "lca4", "grid", "stroop")
+
+
+def longest_first(jobs):
+    rank = {n: i for i, n in enumerate(LONGEST_FIRST)}
+    return sorted(jobs, key=lambda j: rank.get(j["name"], len(rank)))
 WIDE_TRIALS = 16384
 
 
@@ -202,12 +211,7 @@ class Step:
         B = self.B
         if self.batch is None:
             self.batch = B.dg_batch_create(ctx)
-            # branches created longest job first: the wide network's CTAs take
-            # their SMs before the persistent kernels fill the GPU (measured
-            # 2-4 % shorter passes than creation in job order)
-            rank_of = {n: i for i, n in enumerate(
-                ("wide", "ddm", "lca16", "lca8", "lca4", "grid", "stroop"))}
-            for j in sorted(self.jobs, key=lambda j: rank_of.get(j["name"], len(rank_of))):
+            for j in longest_first(self.jobs):
                 if j.get("grid"):
                     B.dg_batch_add_grid(self.batch, j["model"], j["desc"], j["out"]["result"])
                 else:
@@ -768,7 +772,7 @@ def e2e_serving(B, torch, ctx, step, all_ts, world, rank):
     copied back, every step."""
     host_jobs = []
     h2d = d2h = 0
-    for j in step.jobs:
+    for j in longest_first(step.jobs):
         job = B.dg_job()
         job.model = j["model"].value
         keep = []
