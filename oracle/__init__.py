@@ -98,6 +98,8 @@ def _bind(L):
     L.or_pp_means.argtypes = [P, C.c_int32, P, C.c_int32, P, C.c_int32, P, C.c_int32, P,
                               C.c_int64, C.c_uint64, C.c_double, C.c_double, P]
     L.or_argmax.argtypes = [P, C.c_int64, P, P, P]
+    L.or_ddm_run_offset.argtypes = [P, P, C.c_int64, C.c_uint32, C.c_uint64, C.c_double,
+                                    C.c_double, C.c_double, C.c_int32, P, P, P, P]
     L.or_argmax_reservoir.argtypes = [P, C.c_int64, C.c_uint64, P, P, P, P]
     L.or_extended_run.argtypes = [C.POINTER(OrNet), P, C.c_int, C.c_int, P, C.c_int64,
                                   C.c_uint64, C.c_int, P, P, P, P, P, P, P, P, P, P, P, P, P,
@@ -193,6 +195,19 @@ def ddm_run(A, z, seed, dt=1e-3, sigma=1.0, x0=0.0, max_steps=10000, trial_ids=N
                      _p(out["choice"][lo:]), _p(out["step"][lo:]), _p(out["x"][lo:]),
                      _p(out["margin"][lo:]))
     _threaded(run, n, threads)
+    return out
+
+
+def ddm_run_offset(A, z, seed, trial0, dt=1e-3, sigma=1.0, x0=0.0, max_steps=10000):
+    """DDM trials of a run starting at global id trial0 (trial k: A[k], z[k],
+    noise of id trial0 + k)."""
+    A = _c(A, np.float32)
+    z = _c(z, np.float32)
+    n = A.shape[0]
+    out = dict(choice=np.zeros(n, np.int8), step=np.zeros(n, np.int32),
+               x=np.zeros(n, np.float64), margin=np.zeros(n, np.float64))
+    lib().or_ddm_run_offset(_p(A), _p(z), n, trial0, seed, dt, sigma, x0, max_steps,
+                            _p(out["choice"]), _p(out["step"]), _p(out["x"]), _p(out["margin"]))
     return out
 
 

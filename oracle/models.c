@@ -86,6 +86,14 @@ void or_ddm_run(const float* A, const float* z, const uint32_t* trial_ids, int64
   }
 }
 
+void or_ddm_run_offset(const float* A, const float* z, int64_t n, uint32_t trial0,
+                       uint64_t seed, double dt, double sigma, double x0, int32_t max_steps,
+                       int8_t* choice, int32_t* step, double* x_final, double* margin) {
+  for (int64_t k = 0; k < n; ++k)
+    ddm_trial((double)A[k], (double)z[k], seed, trial0 + (uint32_t)k, 0u, dt, sigma, x0,
+              max_steps, &choice[k], &step[k], &x_final[k], &margin[k]);
+}
+
 /* ------------------------------------------------------------------ LCA --- */
 
 void or_lca_run(int N, const float* I, const uint32_t* trial_ids, int64_t n_ids,

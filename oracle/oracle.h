@@ -75,6 +75,13 @@ void or_ddm_run(const float* A, const float* z, const uint32_t* trial_ids, int64
                 uint64_t seed, double dt, double sigma, double x0, int32_t max_steps,
                 int8_t* choice, int32_t* step, double* x_final, double* margin);
 
+/* The same DDM trials for a run that starts at global trial id trial0:
+   trial k uses A[k], z[k] and the noise stream of id trial0 + k (32-bit, so
+   ids wrap as the device's counter word does). */
+void or_ddm_run_offset(const float* A, const float* z, int64_t n, uint32_t trial0,
+                       uint64_t seed, double dt, double sigma, double x0, int32_t max_steps,
+                       int8_t* choice, int32_t* step, double* x_final, double* margin);
+
 /* ---------------------------------------------------------------- LCA --- */
 
 /* Leaky competing accumulator (Sec. 4.4; Usher-McClelland form). Trial t uses

@@ -161,3 +161,18 @@ def test_lca_noise_index(orc):
                     dt=0.01, threshold=100.0, max_steps=1, rectify=False)
     eps = orc.normals(8, 0, 0, 0, N)
     np.testing.assert_allclose(o["x"][0], 0.1 * eps, rtol=1e-15)
+
+
+def test_ddm_run_offset_matches_trial_ids(orc):
+    """A run starting at global id trial0 is the same computation as the
+    id-indexed run over ids trial0 .. trial0 + n - 1."""
+    import numpy as np
+    rng = np.random.default_rng(3)
+    A = rng.uniform(0.1, 1.0, 50).astype(np.float32)
+    z = rng.uniform(0.5, 2.0, 50).astype(np.float32)
+    a = orc.ddm_run_offset(A, z, 7, 20)
+    Apad = np.concatenate([np.zeros(20, np.float32), A])
+    zpad = np.concatenate([np.ones(20, np.float32), z])
+    b = orc.ddm_run(Apad, zpad, 7, trial_ids=np.arange(20, 70, dtype=np.uint32))
+    for k in ("choice", "step", "x"):
+        assert np.array_equal(a[k], b[k])
