@@ -12,6 +12,7 @@ struct LaunchCfg {
   int block = 256;   // threads per block
   int grid = 0;      // blocks; 0 = one per SM times occupancy
   int tpt = 1;       // threads per trial (LCA)
+  int order = 0;     // LCA: 1 = hand trials out longest-expected-first
 };
 
 // ------------------------------------------------------------------ DDM ---
@@ -67,6 +68,7 @@ struct LcaParams {
   const unsigned int* perm;    // batched form: hand-out order (or null)
   PhiloxKeys rk;                 // round keys of (k0, k1)
   int chunk;                     // compacting form: steps between compactions
+  int tail_max;                  // compacting form: at most this many trials left -> a warp each
 };
 cudaError_t launch_lca(const LcaParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
 bool lca_tpt_supported(int N, int tpt);

@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(256) lca_compact(LcaParams p) {
     if constexpr (N % 4 == 0) {
       // no trial left to hand out and at most one per warp still running: a
       // warp each, so that the last, longest trials run at a warp's pace
-      if (!__syncthreads_or(refilled ? 1 : 0) && total > 0 && total <= 8) {
+      if (!__syncthreads_or(refilled ? 1 : 0) && total > 0 && total <= p.tail_max) {
         if (warp < total) {
 #pragma unroll
           for (int i = 0; i < N; ++i) {

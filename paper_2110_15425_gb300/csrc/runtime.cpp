@@ -215,13 +215,15 @@ void load_tune_file(dg_ctx* ctx) {
   if (ctx->tune_file.empty()) return;
   FILE* f = fopen(ctx->tune_file.c_str(), "r");
   if (!f) return;
-  char key[256];
-  int b, g, t;
-  while (fscanf(f, "%255s %d %d %d", key, &b, &g, &t) == 4) {
+  char line[512], key[256];
+  while (fgets(line, sizeof line, f)) {
+    int b, g, t, o = 0;
+    if (sscanf(line, "%255s %d %d %d %d", key, &b, &g, &t, &o) < 4) continue;
     dg::LaunchCfg c;
     c.block = b;
     c.grid = g;
     c.tpt = t;
+    c.order = o;
     ctx->tuned[key] = c;
   }
   fclose(f);
@@ -232,7 +234,8 @@ void save_tune_file(dg_ctx* ctx) {
   FILE* f = fopen(ctx->tune_file.c_str(), "w");
   if (!f) return;
   for (auto& kv : ctx->tuned)
-    fprintf(f, "%s %d %d %d\n", kv.first.c_str(), kv.second.block, kv.second.grid, kv.second.tpt);
+    fprintf(f, "%s %d %d %d %d\n", kv.first.c_str(), kv.second.block, kv.second.grid,
+            kv.second.tpt, kv.second.order);
   fclose(f);
 }
 
@@ -339,7 +342,12 @@ int forced_tpt() {
   return e ? atoi(e) : 0;
 }
 
-std::vector<dg::LaunchCfg> lca_candidates(int N) {
+// Hand-out order: longest-expected-first pays when lanes take new trials
+// (the long ones start first); when every trial has a lane from the start it
+// only gathers the longest trials into the same few blocks, which then run
+// them side by side to the end. Each shape is offered in both orders, the one
+// expected to win first (the default when the tuner does not run).
+std::vector<dg::LaunchCfg> lca_candidates(int N, long long n, bool lpt) {
   std::vector<dg::LaunchCfg> v;
   const int only = forced_tpt();
   // tpt 0: one lane per trial with block-level compaction of running trials
@@ -353,7 +361,13 @@ std::vector<dg::LaunchCfg> lca_candidates(int N) {
       c.block = 256;
       c.tpt = tpt;
       c.grid = dg::num_sms() * std::max(1, occ / div);
+      const long long lanes = (long long)c.grid * c.block / std::max(1, tpt);
+      c.order = lpt && n > lanes ? 1 : 0;
       v.push_back(c);
+      if (lpt) {
+        c.order ^= 1;
+        v.push_back(c);
+      }
     }
   }
   return v;
@@ -451,36 +465,40 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
     {
       const char* e = getenv("DG_LCA_CHUNK");   // steps between compactions
       p.chunk = e && atoi(e) > 0 ? atoi(e) : 32;
+      const char* tm = getenv("DG_LCA_TAIL");   // trials left in a block before a warp each
+      p.tail_max = tm ? std::max(0, std::min(8, atoi(tm))) : 8;
     }
     p.choice = choice;
     p.step = step;
     p.xout = fs;
     p.cursor = sc->cursor();
+    const bool lpt = mode == DG_MODE_BATCHED && lpt_enabled(d->n_trials) && !m->two_sided;
+    if (lpt && (st = scratch_perm(m->ctx, sc, (size_t)d->n_trials, s)) != DG_OK) return st;
     auto go = [&](const dg::LaunchCfg& c) -> dg_status {
+      p.perm = nullptr;
+      if (lpt && c.order == 1) {
+        dg::SchedParams sp{};
+        sp.kind = 1;
+        sp.a = p.I;
+        sp.N = m->N;
+        sp.n = p.n;
+        sp.dt = m->dt;
+        sp.leak = m->leak;
+        sp.threshold = m->threshold;
+        sp.max_steps = m->max_steps;
+        sp.hist = sc->hist();
+        sp.cursor = sc->bucket_cursor();
+        sp.perm = sc->perm;
+        sp.bucket = reinterpret_cast<unsigned short*>(sc->perm + sc->perm_cap);
+        DG_CUDA(dg::launch_sched(sp, s));
+        p.perm = sc->perm;
+      }
       if (mode == DG_MODE_BATCHED) DG_CUDA(cudaMemsetAsync(sc->cursor(), 0, 8, s));
       DG_CUDA(dg::launch_lca(p, mode, c, s));
       return DG_OK;
     };
     if (mode == DG_MODE_PLAIN) return go(dg::LaunchCfg{});
-    if (lpt_enabled(d->n_trials) && !m->two_sided) {
-      if ((st = scratch_perm(m->ctx, sc, (size_t)d->n_trials, s)) != DG_OK) return st;
-      dg::SchedParams sp{};
-      sp.kind = 1;
-      sp.a = p.I;
-      sp.N = m->N;
-      sp.n = p.n;
-      sp.dt = m->dt;
-      sp.leak = m->leak;
-      sp.threshold = m->threshold;
-      sp.max_steps = m->max_steps;
-      sp.hist = sc->hist();
-      sp.cursor = sc->bucket_cursor();
-      sp.perm = sc->perm;
-      sp.bucket = reinterpret_cast<unsigned short*>(sc->perm + sc->perm_cap);
-      DG_CUDA(dg::launch_sched(sp, s));
-      p.perm = sc->perm;
-    }
-    auto cands = lca_candidates(m->N);
+    auto cands = lca_candidates(m->N, d->n_trials, lpt);
     if (cands.empty()) return fail(DG_E_UNSUPPORTED, "dg_run: no LCA layout for N=%d", m->N);
     return run_tuned(m->ctx,
                      "lca" + std::to_string(m->N) + "/" + bucket + "/t" +
