@@ -68,6 +68,32 @@ __device__ __forceinline__ float u01(uint32_t w) {
 // u = that - (1 - 2^-24) equals ((w >> 9) + 1/2) 2^-23 exactly.
 __device__ __forceinline__ float one_plus(uint32_t w) { return __uint_as_float((w >> 9) | 0x3F800000u); }
 
+// The hardware approximations (MUFU) in their flush-to-zero forms. Every
+// argument and result below is a normal binary32 number or zero (u >= 2^-24,
+// -2 ln u >= 2^-23, angles of magnitude >= 2 pi 2^-24), where the two forms
+// return the same bits; the flush-to-zero form saves the subnormal
+// range fix-up instructions around each approximation.
+__device__ __forceinline__ float approx_lg2(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float approx_rsqrt(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float approx_sin(float x) {
+  float r;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float approx_cos(float x) {
+  float r;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // -2 ln(u) for u in (0, 1). The hardware log2 approximation has a small
 // absolute error, which is a large relative error when u is close to 1 and
 // ln(u) is tiny; there the Taylor series -2 ln(1 - v) = 2 (v + v^2/2 + v^3/3
@@ -75,7 +101,7 @@ __device__ __forceinline__ float one_plus(uint32_t w) { return __uint_as_float((
 // v < 2^-6 five terms leave a relative truncation error below 2e-10.
 __device__ __forceinline__ float neg2_log_u01(float u) {
   const float v = 1.0f - u;
-  float r = -1.38629436111989062f * __log2f(u);   // -2 ln 2
+  float r = -1.38629436111989062f * approx_lg2(u);   // -2 ln 2
   if (v < 0x1p-6f)  // taken for 1 draw in 64
     r = v * fmaf(v, fmaf(v, fmaf(v, fmaf(v, 0.4f, 0.5f), 2.0f / 3.0f), 1.0f), 2.0f);
   return r;
@@ -87,15 +113,14 @@ __device__ __forceinline__ float neg2_log_u01(float u) {
 // cosine, so the hardware sine/cosine see a reduced argument.
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& z0, float& z1) {
   const float y = neg2_log_u01(one_plus(wa) - 0.99999994039535522f);   // 1 - 2^-24
-  const float r = y * rsqrtf(y);
-  float s, c;
+  const float r = y * approx_rsqrt(y);
   // u_b - 1/2 = (one_plus(w_b) - 3/2) + 2^-24, both steps exact; the fma
   // rounds 2 pi (u_b - 1/2) once, as a plain product of the exact difference
   // would (2 pi 2^-24 is exact)
-  __sincosf(fmaf(6.28318530717958648f, one_plus(wb) - 1.5f, 6.28318530717958648f * 0x1p-24f), &s,
-            &c);
-  z0 = -r * c;
-  z1 = -r * s;
+  const float ang =
+      fmaf(6.28318530717958648f, one_plus(wb) - 1.5f, 6.28318530717958648f * 0x1p-24f);
+  z0 = -r * approx_cos(ang);
+  z1 = -r * approx_sin(ang);
 }
 
 __device__ __forceinline__ float4 normals4(uint4 w) {
@@ -140,7 +165,8 @@ __device__ __forceinline__ long long fetch_trial(unsigned long long* cursor, boo
 
 // y = 1 / (1 + exp(-gain (s + bias))) = 1 / (1 + 2^(c1 s + c0)) with
 // c1 = -gain log2(e), c0 = -gain bias log2(e): one fma, the hardware 2^x and
-// reciprocal approximations.
+// reciprocal approximations (flush-to-zero forms: a subnormal 2^x adds
+// nothing to 1, and a reciprocal of 1 + 2^x above 2^126 is 0 either way).
 struct Logistic {
   float c1, c0;
   __device__ __forceinline__ static Logistic of(float gain, float bias) {
@@ -148,9 +174,10 @@ struct Logistic {
     return Logistic{-gain * l2e, -(gain * bias) * l2e};
   }
   __device__ __forceinline__ float operator()(float s) const {
-    float e;
-    asm("ex2.approx.f32 %0, %1;" : "=f"(e) : "f"(fmaf(s, c1, c0)));
-    return __fdividef(1.0f, 1.0f + e);
+    float e, y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fmaf(s, c1, c0)));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(1.0f + e));
+    return y;
   }
 };
 
