@@ -55,10 +55,10 @@ OPS_PER_UNIT = {"ddm": 32, "lca4": 4 * 31, "lca8": 8 * 31, "lca16": 16 * 31, "st
 # DRAM bytes (read + write) of one ddm_batched launch over the 2^20-trial job,
 # from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
 # -k regex:ddm_batched -s 1 -c 1 python bench.py --only ddm` on the current
-# kernel (profiles/ddm_batched_2p20_trials.md): 12,598,784 read + 0 written
+# kernel (profiles/ddm_batched_2p20_trials.md): 12,653,824 read + 256 written
 # (the 5 MB of outputs stay in L2 within the launch). Algorithmic: 8 B of
 # parameters in and 5 B out per trial = 13.6 MB.
-DDM_TRAFFIC_BYTES = 12_598_784
+DDM_TRAFFIC_BYTES = 12_654_080
 LANES_PER_SM = 128
 # The pass's jobs, longest first. Graph branches are created (and served jobs
 # submitted) in this order: the wide network's CTAs take their SMs before the
@@ -231,12 +231,10 @@ class Step:
         return ts
 
     def kernels_per_step(self):
-        """Kernels of one pass: one per job, plus the three-kernel trial-order
-        sort (histogram, scan, scatter) before each DDM and LCA job of at
-        least 4,096 trials."""
-        sorted_jobs = sum(1 for j in self.jobs
-                          if (j["name"] == "ddm" or j["name"].startswith("lca")) and j["n"] >= 4096)
-        return len(self.jobs) + 3 * sorted_jobs
+        """Kernels of one pass: the kernel nodes of the batch's CUDA graph, as
+        the library counts them (one per job, plus the three-kernel trial-order
+        sort wherever the launch-shape tuner chose the sorted hand-out)."""
+        return self.B.dg_batch_kernels(self.batch)
 
 
 # ---------------------------------------------------------------- clocks ---

@@ -406,6 +406,10 @@ dg_status dg_batch_add_run(dg_batch* b, dg_model* model, const dg_run_desc* desc
 dg_status dg_batch_add_grid(dg_batch* b, dg_model* model, const dg_grid_desc* desc,
                             dg_grid_result* result, double* cand_means);
 dg_status dg_batch_launch(dg_batch* b, void* stream);
+/* Kernel launches one dg_batch_launch makes: the kernel nodes of the batch's
+   CUDA graph (trial-order sorts included; memsets are not kernels). Valid after
+   the first dg_batch_launch; DG_E_STATE before. */
+dg_status dg_batch_kernels(const dg_batch* b, int64_t* n_kernels);
 dg_status dg_batch_free(dg_batch* b);
 
 /* ---------------------------------------------------------------- serving --- */

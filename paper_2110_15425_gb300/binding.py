@@ -112,7 +112,7 @@ EXPORTS = [
     "dg_create", "dg_destroy", "dg_last_error", "dg_version", "dg_compose", "dg_model_free",
     "dg_model_info", "dg_run", "dg_grid_search", "dg_argmax_f64", "dg_philox_words",
     "dg_normals", "dg_batch_create", "dg_batch_add_run", "dg_batch_add_grid",
-    "dg_batch_launch", "dg_batch_free", "dg_submit", "dg_wait", "dg_serve_stats",
+    "dg_batch_launch", "dg_batch_kernels", "dg_batch_free", "dg_submit", "dg_wait", "dg_serve_stats",
     "dg_grid_search_noalloc", "dg_stream_status", "dg_selftest_wait_timeout",
     "dg_argmax_f64_reservoir", "dg_grid_refine", "dg_run_episodes",
 ]
@@ -159,6 +159,7 @@ def _declare(L):
         "dg_batch_add_run": [P, P, C.POINTER(dg_run_desc), P, P, P],
         "dg_batch_add_grid": [P, P, C.POINTER(dg_grid_desc), P, P],
         "dg_batch_launch": [P, P],
+        "dg_batch_kernels": [P, P],
         "dg_batch_free": [P],
         "dg_submit": [P, C.POINTER(dg_job), C.POINTER(u64)],
         "dg_wait": [P, u64, i32, C.POINTER(dg_job_result)],
@@ -350,6 +351,13 @@ def dg_batch_add_grid(batch, model, desc, result, cand_means=None):
 
 def dg_batch_launch(batch, stream=None):
     check(lib().dg_batch_launch(batch, stream_handle(stream)))
+
+
+def dg_batch_kernels(batch):
+    """Kernel launches one dg_batch_launch makes (after the first launch)."""
+    n = C.c_int64(0)
+    check(lib().dg_batch_kernels(batch, C.byref(n)))
+    return n.value
 
 
 def dg_batch_free(batch):

@@ -347,9 +347,16 @@ int forced_tpt() {
 // only gathers the longest trials into the same few blocks, which then run
 // them side by side to the end. Each shape is offered in both orders, the one
 // expected to win first (the default when the tuner does not run).
+// DG_LCA_ORDER=<0|1> restricts the hand-out order likewise (0 as given, 1
+// longest-expected-first).
+int forced_order() {
+  const char* e = getenv("DG_LCA_ORDER");
+  return e ? atoi(e) : -1;
+}
+
 std::vector<dg::LaunchCfg> lca_candidates(int N, long long n, bool lpt) {
   std::vector<dg::LaunchCfg> v;
-  const int only = forced_tpt();
+  const int only = forced_tpt(), order = forced_order();
   // tpt 0: one lane per trial with block-level compaction of running trials
   for (int tpt : {0, 1, 2, 4}) {
     if (!dg::lca_tpt_supported(N, tpt) || (only > 0 && tpt != only) || (only < 0 && tpt != 0))
@@ -363,11 +370,8 @@ std::vector<dg::LaunchCfg> lca_candidates(int N, long long n, bool lpt) {
       c.grid = dg::num_sms() * std::max(1, occ / div);
       const long long lanes = (long long)c.grid * c.block / std::max(1, tpt);
       c.order = lpt && n > lanes ? 1 : 0;
-      v.push_back(c);
-      if (lpt) {
-        c.order ^= 1;
-        v.push_back(c);
-      }
+      for (int k = 0; k < (lpt ? 2 : 1); ++k, c.order ^= 1)
+        if (order < 0 || !lpt || c.order == order) v.push_back(c);
     }
   }
   return v;
@@ -502,7 +506,7 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
     if (cands.empty()) return fail(DG_E_UNSUPPORTED, "dg_run: no LCA layout for N=%d", m->N);
     return run_tuned(m->ctx,
                      "lca" + std::to_string(m->N) + "/" + bucket + "/t" +
-                         std::to_string(forced_tpt()),
+                         std::to_string(forced_tpt()) + "/o" + std::to_string(forced_order()),
                      cands, s, go);
   }
   if (m->kind == K_NET) {
@@ -1608,6 +1612,7 @@ struct dg_batch {
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> join;
   cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;         // kernel nodes of the captured graph
 };
 
 dg_status dg_batch_create(dg_ctx* ctx, dg_batch** out) {
@@ -1701,10 +1706,29 @@ dg_status dg_batch_launch(dg_batch* b, void* stream) {
     return st;
   }
   if (ec != cudaSuccess) return fail(DG_E_CUDA, "batch: end capture: %s", cudaGetErrorString(ec));
+  {
+    size_t nn = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+        for (size_t i = 0; i < nn; ++i) {
+          cudaGraphNodeType t;
+          if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+            ++b->kernels;
+        }
+    }
+  }
   ec = cudaGraphInstantiate(&b->exec, g, 0);
   cudaGraphDestroy(g);
   if (ec != cudaSuccess) return fail(DG_E_CUDA, "batch: instantiate: %s", cudaGetErrorString(ec));
   DG_CUDA(cudaGraphLaunch(b->exec, s));
+  return DG_OK;
+}
+
+dg_status dg_batch_kernels(const dg_batch* b, int64_t* n_kernels) {
+  if (!b || !n_kernels) return fail(DG_E_ARG, "dg_batch_kernels: null argument");
+  if (!b->exec) return fail(DG_E_STATE, "dg_batch_kernels: batch not launched yet");
+  *n_kernels = b->kernels;
   return DG_OK;
 }
 

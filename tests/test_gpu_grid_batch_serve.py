@@ -149,11 +149,15 @@ def test_batch_graph_equals_single_runs(ctx):
             B.dg_batch_add_run(b, ml, rl, o["lc"], o["ls"])
             B.dg_batch_add_run(b, ms, rs, o["sc"], o["ss"])
             B.dg_batch_add_grid(b, mp, gd, o["gr"], o["gm"])
+            with pytest.raises(B.DGError):   # no graph before the first launch
+                B.dg_batch_kernels(b)
             for _ in range(3):   # capture, then replays
                 for t in o.values():
                     t.zero_()
                 B.dg_batch_launch(b)
             torch.cuda.synchronize()
+            # one kernel per op at least, plus at most a three-kernel sort each
+            assert 4 <= B.dg_batch_kernels(b) <= 4 * 4
             B.dg_batch_free(b)
         outs[tag] = {k: host(v) for k, v in o.items()}
     for k in outs["single"]:

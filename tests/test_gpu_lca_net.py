@@ -68,6 +68,24 @@ def test_lca_batched_equals_plain_bitwise(ctx, monkeypatch, tpt):
             assert np.array_equal(u, v), N
 
 
+@pytest.mark.parametrize("order", ["0", "1"])
+def test_lca_hand_out_orders(ctx, orc, threads, monkeypatch, order):
+    """Both hand-out orders (as given; longest expected first) at a size that
+    is sorted (>= 4,096 trials) give the plain form's results bit for bit, and
+    the oracle's on a sample of trials."""
+    from paper_2110_15425_gb300 import workloads as W
+    monkeypatch.setenv("DG_LCA_ORDER", order)
+    for N in (4, 16):
+        w = W.lca(n_trials=20000, N=N)
+        a = _lca(ctx, w["I"], w["seed"], 0)
+        b = _lca(ctx, w["I"], w["seed"], 1)
+        for u, v in zip(a, b):
+            assert np.array_equal(u, v), (N, order)
+        ids = np.arange(0, 20000, 37, dtype=np.uint32)
+        ref = orc.lca_run(w["I"], w["seed"], trial_ids=ids, threads=threads)
+        compare_decisions(a[0][ids], a[1][ids], ref, f"lca N={N} order={order}")
+
+
 def test_lca_ddm_mapping(ctx, orc, threads):
     """Sec. 4.4: LCA(N=1, leak 0, no competition, unit noise, two-sided, no
     rectification) decides like the DDM on the same draws."""
