@@ -267,8 +267,13 @@ __global__ void __launch_bounds__(kThreads, 1) wide_kernel(WideParams p) {
       mma_commit(&sh.bar_mma);
     }
 
-    // ---- 3. response units 4q .. 4q+3 of every trial (all quarters)
+    // ---- 3. response units 4q .. 4q+3 of every trial (all quarters); their
+    // normals do not depend on D, so they are drawn while the MMA runs
     {
+      float4 zr = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (warp_live)
+        zr = normals4(noise_block_rk(
+            p.rk, tg, 0u, (uint32_t)k * (uint32_t)(L::U / 4) + (uint32_t)(H / 4 + q)));
       float net[4];
       if (TC) {
         if (!mbar_wait(&sh.bar_mma, phase)) {
@@ -287,9 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1) wide_kernel(WideParams p) {
         }
       }
       if (warp_live) {
-        const float4 z = normals4(noise_block_rk(
-            p.rk, tg, 0u, (uint32_t)k * (uint32_t)(L::U / 4) + (uint32_t)(H / 4 + q)));
-        const float e4[4] = {z.x, z.y, z.z, z.w};
+        const float e4[4] = {zr.x, zr.y, zr.z, zr.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           sr[j] = fmaf(keep, sr[j], fmaf(p.rate, net[j], p.noise * e4[j]));
