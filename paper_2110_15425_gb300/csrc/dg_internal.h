@@ -256,7 +256,7 @@ struct SchedParams {
   const float* b;                // DDM: z[n]
   int N;
   long long n;
-  float dt, sigma2, leak, threshold;
+  float dt, sigma2, leak, inhibition, threshold;
   int max_steps;
   unsigned int* hist;            // [kSchedBuckets] scratch
   unsigned int* cursor;          // [kSchedBuckets] scratch

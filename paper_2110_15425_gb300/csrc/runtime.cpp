@@ -488,6 +488,7 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
         sp.n = p.n;
         sp.dt = m->dt;
         sp.leak = m->leak;
+        sp.inhibition = m->inhibition;
         sp.threshold = m->threshold;
         sp.max_steps = m->max_steps;
         sp.hist = sc->hist();
