@@ -2,6 +2,11 @@
 // model in Sec. 5), Usher-McClelland form, synchronous update:
 //   x_i <- x_i + ((I_i - k x_i - beta sum_{j != i} x_j) dt + sigma sqrt(dt) eps_i)
 //   x_i <- max(0, x_i)                         (unless DG_LCA_NO_RECTIFY)
+// evaluated as x_i <- x_i + (g x_i + (dt I_i - c S) + sigma sqrt(dt) eps_i) with
+// S = sum_j x_j, g = dt (beta - k), c = dt beta: the same update in five
+// instructions per accumulator (dt I_i is formed once per trial). The
+// increment is formed apart from x_i: folding 1 + g into one coefficient
+// would round it once and compound that error over thousands of steps.
 // stop when max_i x_i >= threshold (winner = lowest index among maxima), or,
 // two-sided with N = 1, when |x| >= threshold (the DDM mapping of Sec. 4.4).
 // eps_i of step j (1-based) is normal (j-1) N + i of the (seed, trial, 0) stream.
@@ -88,16 +93,19 @@ struct Lca {
     }
   }
 
-  // One step of one trial with its normals e. Returns true when the trial has
-  // ended at this step.
+  // One step of one trial with its normals e; I holds dt I_i. Returns true
+  // when the trial has ended at this step.
   static __device__ __forceinline__ bool step(const LcaParams& p, const float (&e)[NU], int g,
                                               unsigned gmask, float (&x)[NU], const float (&I)[NU],
                                               int8_t& choice) {
     const float S = group_sum(chunk_sum(x), gmask);
+    // every multiply-add written as fmaf, so that each layout and form
+    // computes the same bits (no contraction left to the compiler)
+    const float gr = p.dt * (p.inhibition - p.leak);   // g
+    const float c = p.dt * p.inhibition;
 #pragma unroll
     for (int i = 0; i < NU; ++i) {
-      const float drive = (I[i] - p.leak * x[i]) - p.inhibition * (S - x[i]);
-      float v = x[i] + fmaf(drive, p.dt, p.diffusion * e[i]);
+      float v = x[i] + fmaf(gr, x[i], fmaf(p.diffusion, e[i], fmaf(-c, S, I[i])));
       if (p.rectify) v = fmaxf(v, 0.f);
       x[i] = v;
     }
@@ -129,7 +137,7 @@ struct Lca {
     const float* src = p.I + (size_t)t * N + g * NU;
 #pragma unroll
     for (int i = 0; i < NU; ++i) {
-      I[i] = __ldg(src + i);
+      I[i] = p.dt * __ldg(src + i);   // dt I_i
       x[i] = 0.f;
     }
   }
