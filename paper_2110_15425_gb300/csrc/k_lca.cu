@@ -81,16 +81,16 @@ struct Lca {
     return v;
   }
 
-  static __device__ __forceinline__ void group_argmax(float& v, int& i, unsigned gmask) {
+  static __device__ __forceinline__ float group_max(float v, unsigned gmask) {
 #pragma unroll
-    for (int o = TPT / 2; o > 0; o >>= 1) {
-      const float ov = __shfl_xor_sync(gmask, v, o);
-      const int oi = __shfl_xor_sync(gmask, i, o);
-      if (ov > v || (ov == v && oi < i)) {
-        v = ov;
-        i = oi;
-      }
-    }
+    for (int o = TPT / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(gmask, v, o));
+    return v;
+  }
+
+  static __device__ __forceinline__ int group_min(int v, unsigned gmask) {
+#pragma unroll
+    for (int o = TPT / 2; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(gmask, v, o));
+    return v;
   }
 
   // One step of one trial with its normals e; I holds dt I_i. Returns true
@@ -116,17 +116,18 @@ struct Lca {
       }
       return false;
     }
+    // the stop test needs only the largest state; the winner (the lowest
+    // index holding it) is looked up on the step that reaches the threshold
     float m = x[0];
-    int mi = g * NU;
 #pragma unroll
-    for (int i = 1; i < NU; ++i)
-      if (x[i] > m) {
-        m = x[i];
-        mi = g * NU + i;
-      }
-    group_argmax(m, mi, gmask);
+    for (int i = 1; i < NU; ++i) m = fmaxf(m, x[i]);
+    m = group_max(m, gmask);
     if (m >= p.threshold) {
-      choice = (int8_t)mi;
+      int mi = N;
+#pragma unroll
+      for (int i = NU - 1; i >= 0; --i)
+        if (x[i] == m) mi = g * NU + i;
+      choice = (int8_t)group_min(mi, gmask);
       return true;
     }
     return false;
