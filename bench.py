@@ -292,6 +292,90 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+class NvmlClockSampler:
+    """SM clock and clock-event reasons read through NVML every 5 ms, strictly
+    inside the timed region (a thread polls between __enter__ and __exit__).
+    Falls back to the nvidia-smi sampler when NVML cannot be loaded."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, device, period_s=0.005):
+        self.device, self.period = device, period_s
+        self.samples, self.max_mhz = [], None
+        self.fallback = None
+        self._stop = threading.Event()
+        self._thread = None
+        self._nvml = None
+        self._handle = None
+
+    def _open(self):
+        import ctypes as C
+        lib = C.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = C.c_void_p()
+        bus = self._pci_bus_id()
+        # NVML numbers all GPUs of the machine; the CUDA device is found by its PCI address
+        if bus is None or lib.nvmlDeviceGetHandleByPciBusId_v2(bus, C.byref(h)) != 0:
+            if lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(self.device), C.byref(h)) != 0:
+                raise OSError("no NVML handle")
+        self._nvml, self._handle = lib, h
+        mx = C.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(h, C.c_int(1), C.byref(mx)) == 0:   # NVML_CLOCK_SM
+            self.max_mhz = float(mx.value)
+        fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self._reasons_fn = fn or lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def _pci_bus_id(self):
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(self.device)
+            return b"%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        except (AttributeError, RuntimeError, ImportError):
+            return None
+
+    def _poll(self):
+        import ctypes as C
+        clk, rs = C.c_uint(), C.c_ulonglong()
+        while not self._stop.is_set():
+            if self._nvml.nvmlDeviceGetClockInfo(self._handle, C.c_int(1), C.byref(clk)) == 0:
+                r = rs.value if self._reasons_fn(self._handle, C.byref(rs)) == 0 else 0
+                self.samples.append((float(clk.value), int(r)))
+            time.sleep(self.period)
+
+    def __enter__(self):
+        try:
+            self._open()
+        except (OSError, AttributeError):
+            self.fallback = ClockSampler(self.device).__enter__()
+            return self
+        self._thread = threading.Thread(target=self._poll, daemon=True)
+        self._thread.start()
+        return self
+
+    def __exit__(self, *a):
+        if self.fallback is not None:
+            self.fallback.__exit__(*a)
+            return
+        self._stop.set()
+        self._thread.join(timeout=1.0)
+
+    def summary(self):
+        if self.fallback is not None:
+            return self.fallback.summary()
+        if not self.samples:
+            return None
+        reasons = set()
+        for _, r in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(c for c, _ in self.samples),
+                "sm_max_mhz": self.max_mhz, "samples": len(self.samples),
+                "reasons": sorted(reasons), "source": "NVML every 5 ms inside the timed region"}
+
+
 # ----------------------------------------------------------- CPU oracle ---
 
 def cpu_baseline(seconds_hint=True):
@@ -480,7 +564,7 @@ def main():
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     barrier()
-    with ClockSampler(local) as clk:
+    with NvmlClockSampler(local) as clk:
         for i in range(K):
             l2_flush.zero_()
             starts[i].record()
