@@ -160,6 +160,17 @@ struct TopTwo {                  // running argmax with lowest-index ties
 };
 
 constexpr int kMaxGridBlocks = 4096;  // size of the per-block argmax partials scratch
+// Batched grid search: lanes per candidate (its trials spread over them).
+// Grids of at least kGridNarrowMin candidates take eight lanes per candidate
+// (four candidates per warp: the per-candidate work is shared by fewer lanes);
+// smaller grids a whole warp, so that a round of a few hundred candidates
+// still spreads over many warps. The choice depends on the whole grid's size
+// only, so a candidate's mean has the same bits whatever range a call
+// evaluates and whatever the launch shape.
+constexpr long long kGridNarrowMin = 16384;
+inline int grid_lanes(const int (&L)[3]) {
+  return (long long)L[0] * L[1] * L[2] >= kGridNarrowMin ? 8 : 32;
+}
 
 struct GridParams {
   const float* lv[3];
@@ -178,7 +189,7 @@ struct GridParams {
   PhiloxKeys rk;                 // round keys of (k0, k1)
 };
 cudaError_t launch_grid(const GridParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
-int grid_blocks(int mode, long long n_cand, int n_trials);
+int grid_blocks(int mode, long long n_cand, int n_trials, int lanes);
 
 cudaError_t launch_argmax(const double* v, long long n, TopTwo* partials, unsigned int* ticket,
                           void* result, cudaStream_t s);

@@ -8,10 +8,12 @@
 //   outcome = -|P + act - Y| - sum_e a_e^2                      (true P, Y)
 // mean_c = FP64 mean of the outcomes; best = argmax_c mean_c, lowest c on ties.
 //
-// Batched form: one warp per candidate (trials spread over the lanes), a
-// compensated FP32 pair sum across the lanes converted to the FP64 mean,
-// running top-2 per warp, block merge, then the last block to finish merges
-// the per-block partials (no second launch, no atomics on the values). Plain form (the paper's mapping): one thread per candidate
+// Batched form: a group of lanes per candidate (the trials spread over them;
+// eight lanes, four candidates per warp, for grids of 16,384 candidates or
+// more, else a whole warp), a compensated FP32 pair sum across the group
+// converted to the FP64 mean, running top-2 per warp, block merge, then the
+// last block to finish merges the per-block partials (no second launch, no
+// atomics on the values). Plain form (the paper's mapping): one thread per candidate
 // with a sequential FP64 sum, then a separate argmax launch.
 //
 // Random tie-break (Sec. 3.3: one of several equally good choices is picked at
@@ -40,12 +42,21 @@ __device__ __forceinline__ float pp_outcome(const GridParams& p, const float* po
   return pp_outcome_at(p.rk, (uint32_t)j, c, 0u, pos + 6 * j, sd0, sd1, sd2, p.weight, cost);
 }
 
-// c: global candidate index
+// c: global candidate index (32-bit division whenever c fits: the 64-bit
+// forms are long software sequences)
 __device__ __forceinline__ void cand_alloc(const GridParams& p, const float* lv, long long c,
                                            float& a0, float& a1, float& a2) {
-  const int l2 = (int)(c % p.L[2]);
-  const int l1 = (int)((c / p.L[2]) % p.L[1]);
-  const int l0 = (int)(c / ((long long)p.L[2] * p.L[1]));
+  int l0, l1, l2;
+  if ((unsigned long long)c <= 0xFFFFFFFFull) {
+    const uint32_t u = (uint32_t)c, q = u / (uint32_t)p.L[2];
+    l2 = (int)(u - q * (uint32_t)p.L[2]);
+    l1 = (int)(q % (uint32_t)p.L[1]);
+    l0 = (int)(q / (uint32_t)p.L[1]);
+  } else {
+    l2 = (int)(c % p.L[2]);
+    l1 = (int)((c / p.L[2]) % p.L[1]);
+    l0 = (int)(c / ((long long)p.L[2] * p.L[1]));
+  }
   a0 = lv[l0];
   a1 = lv[p.L[0] + l1];
   a2 = lv[p.L[0] + p.L[1] + l2];
@@ -105,17 +116,33 @@ __device__ void finish_argmax(TopTwo mine, TopTwo* partials, unsigned int* ticke
   }
 }
 
+// Pair sum over the LANES lanes of a candidate's group, by an xor
+// butterfly; the group's first lane holds the total in a fixed order.
+template <int LANES>
+__device__ __forceinline__ void group_pair_sum(float& hi, float& lo) {
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(kFull, hi, o);
+    const float ol = __shfl_xor_sync(kFull, lo, o);
+    two_sum_add(hi, lo, oh);
+    lo += ol;
+  }
+}
+
+template <int LANES>
 __global__ void __launch_bounds__(256) grid_batched(GridParams p) {
+  constexpr int kGridLanes = LANES, kGridCandsPerWarp = 32 / LANES;
   extern __shared__ float sm[];
   float* pos = sm;
   float* lv = sm + 6 * p.n_trials;
   stage(p, pos, lv);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / kGridLanes, gl = lane % kGridLanes;
   const int wpb = blockDim.x >> 5;
   TopTwo best = top_init();
   const double inv = 1.0 / (double)p.n_trials;
-  // lane `slot` keeps the pair of the warp's slot-th pending candidate; every
-  // 32 candidates (and at the end) all lanes convert theirs to FP64 at once
+  // lane `slot + g` keeps the pair of group g's candidate; every 32
+  // candidates (and at the end) all lanes convert theirs to FP64 at once
   float kh = 0.f, kl = 0.f;
   long long kc = -1;
   int slot = 0;
@@ -127,24 +154,33 @@ __global__ void __launch_bounds__(256) grid_batched(GridParams p) {
     }
     kc = -1;
   };
-  for (long long c = (long long)blockIdx.x * wpb + warp; c < p.n_cand;
-       c += (long long)gridDim.x * wpb) {
-    const long long cg = p.cand0 + c;
-    float a0, a1, a2;
-    cand_alloc(p, lv, cg, a0, a1, a2);
-    const float sd0 = 1.0f / (p.offset + a0), sd1 = 1.0f / (p.offset + a1),
-                sd2 = 1.0f / (p.offset + a2);
-    const float cost = a0 * a0 + a1 * a1 + a2 * a2;
+  for (long long cb = ((long long)blockIdx.x * wpb + warp) * kGridCandsPerWarp; cb < p.n_cand;
+       cb += (long long)gridDim.x * wpb * kGridCandsPerWarp) {
+    const long long c = cb + grp;
     float hi = 0.f, lo = 0.f;
-    for (int j = lane; j < p.n_trials; j += 32)
-      two_sum_add(hi, lo, pp_outcome(p, pos, j, p.stream0 + (uint32_t)cg, sd0, sd1, sd2, cost));
-    warp_pair_sum(hi, lo);
-    if (lane == slot) {
-      kh = hi;
-      kl = lo;
-      kc = c;
+    if (c < p.n_cand) {
+      const long long cg = p.cand0 + c;
+      float a0, a1, a2;
+      cand_alloc(p, lv, cg, a0, a1, a2);
+      const float sd0 = 1.0f / (p.offset + a0), sd1 = 1.0f / (p.offset + a1),
+                  sd2 = 1.0f / (p.offset + a2);
+      const float cost = a0 * a0 + a1 * a1 + a2 * a2;
+      for (int j = gl; j < p.n_trials; j += kGridLanes)
+        two_sum_add(hi, lo, pp_outcome(p, pos, j, p.stream0 + (uint32_t)cg, sd0, sd1, sd2, cost));
     }
-    if (++slot == 32) {
+    group_pair_sum<LANES>(hi, lo);
+    // lane slot + g takes group g's total from the group's first lane
+    const int g = lane - slot;
+    const bool mine = g >= 0 && g < kGridCandsPerWarp;
+    const int src = mine ? g * kGridLanes : 0;
+    const float th = __shfl_sync(kFull, hi, src), tl = __shfl_sync(kFull, lo, src);
+    if (mine && cb + g < p.n_cand) {
+      kh = th;
+      kl = tl;
+      kc = cb + g;
+    }
+    slot += kGridCandsPerWarp;
+    if (slot == 32) {
       flush();
       slot = 0;
     }
@@ -328,8 +364,8 @@ __global__ void refine_step(RefineParams p, int r) {
 
 // ------------------------------------------- coarse-to-fine, one cluster ---
 // The whole refinement in one launch: a cluster of kRefineCluster CTAs (1,024
-// threads each) evaluates a round's candidates, one warp per candidate as
-// grid_batched does; each CTA publishes its top-2 in shared memory, every CTA
+// threads each) evaluates a round's candidates, a warp per candidate as
+// grid_batched does for grids of this size; each CTA publishes its top-2 in shared memory, every CTA
 // reads all of them through distributed shared memory after a cluster
 // barrier, and each lays out the next round itself (the same arithmetic, so
 // the CTAs agree). A second cluster barrier keeps a round's top-2 readable
@@ -396,23 +432,38 @@ __global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(1024, 1
       if (kc >= 0) best = top_merge(best, TopTwo{((double)kh + (double)kl) * inv, kc, -DBL_MAX});
       kc = -1;
     };
-    for (long long c = gw; c < n_cand; c += W) {
-      const int l2 = (int)(c % G), l1 = (int)((c / G) % G), l0 = (int)(c / ((long long)G * G));
-      const float a0 = lv[0][l0], a1 = lv[1][l1], a2 = lv[2][l2];
-      const float sd0 = 1.0f / (p.offset + a0), sd1 = 1.0f / (p.offset + a1),
-                  sd2 = 1.0f / (p.offset + a2);
-      const float cost = a0 * a0 + a1 * a1 + a2 * a2;
+    // candidates as grid_batched evaluates grids of this size (a round holds at
+    // most 8,192 < kGridNarrowMin candidates: a whole warp per candidate)
+    constexpr int kGridLanes = 32, kGridCandsPerWarp = 1;
+    const int grp = lane / kGridLanes, gl = lane % kGridLanes;
+    for (long long cb = (long long)gw * kGridCandsPerWarp; cb < n_cand;
+         cb += (long long)W * kGridCandsPerWarp) {
+      const long long c = cb + grp;
       float hi = 0.f, lo = 0.f;
-      for (int j = lane; j < p.n_trials; j += 32)
-        two_sum_add(hi, lo, pp_outcome_at(p.rk, (uint32_t)j, stream0 + (uint32_t)c, 0u, sm + 6 * j,
-                                          sd0, sd1, sd2, p.weight, cost));
-      warp_pair_sum(hi, lo);
-      if (lane == slot) {
-        kh = hi;
-        kl = lo;
-        kc = c;
+      if (c < n_cand) {
+        const uint32_t u = (uint32_t)c, q = u / (uint32_t)G;
+        const int l2 = (int)(u - q * (uint32_t)G), l1 = (int)(q % (uint32_t)G),
+                  l0 = (int)(q / (uint32_t)G);
+        const float a0 = lv[0][l0], a1 = lv[1][l1], a2 = lv[2][l2];
+        const float sd0 = 1.0f / (p.offset + a0), sd1 = 1.0f / (p.offset + a1),
+                    sd2 = 1.0f / (p.offset + a2);
+        const float cost = a0 * a0 + a1 * a1 + a2 * a2;
+        for (int j = gl; j < p.n_trials; j += kGridLanes)
+          two_sum_add(hi, lo, pp_outcome_at(p.rk, (uint32_t)j, stream0 + (uint32_t)c, 0u,
+                                            sm + 6 * j, sd0, sd1, sd2, p.weight, cost));
       }
-      if (++slot == 32) {
+      group_pair_sum<kGridLanes>(hi, lo);
+      const int g = lane - slot;
+      const bool mine = g >= 0 && g < kGridCandsPerWarp;
+      const int src = mine ? g * kGridLanes : 0;
+      const float th = __shfl_sync(kFull, hi, src), tl = __shfl_sync(kFull, lo, src);
+      if (mine && cb + g < n_cand) {
+        kh = th;
+        kl = tl;
+        kc = cb + g;
+      }
+      slot += kGridCandsPerWarp;
+      if (slot == 32) {
         flush();
         slot = 0;
       }
@@ -475,14 +526,18 @@ size_t grid_smem(const GridParams& p) {
 
 }  // namespace
 
-int grid_blocks(int mode, long long n_cand, int n_trials) {
+int grid_blocks(int mode, long long n_cand, int n_trials, int lanes) {
   (void)n_trials;
   if (mode == 1) return (int)((n_cand + 255) / 256);
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, grid_batched, 256, 0);
+  if (lanes == 8)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, grid_batched<8>, 256, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, grid_batched<32>, 256, 0);
   if (nb < 1) nb = 1;
   long long g = (long long)num_sms() * nb;
-  const long long need = (n_cand + 7) / 8;
+  const long long per_block = 8LL * (32 / lanes);
+  const long long need = (n_cand + per_block - 1) / per_block;
   return (int)(g < need ? g : need);
 }
 
@@ -490,7 +545,8 @@ cudaError_t launch_grid(const GridParams& p, int mode, const LaunchCfg& cfg, cud
   const size_t smem = grid_smem(p);  // <= 6 * 1024 + 3 * 4096 floats (runtime limits)
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(grid_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(grid_batched<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(grid_batched<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     cudaFuncSetAttribute(grid_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     attr = true;
   }
@@ -508,11 +564,16 @@ cudaError_t launch_grid(const GridParams& p, int mode, const LaunchCfg& cfg, cud
     return cudaGetLastError();
   }
   const int block = (cfg.block == 128 || cfg.block == 256) ? cfg.block : 256;
-  int grid = cfg.grid > 0 ? cfg.grid : grid_blocks(0, p.n_cand, p.n_trials);
+  const int lanes = grid_lanes(p.L);
+  int grid = cfg.grid > 0 ? cfg.grid : grid_blocks(0, p.n_cand, p.n_trials, lanes);
   if (grid > kMaxGridBlocks) grid = kMaxGridBlocks;  // one argmax partial per block
-  const long long need = (p.n_cand + block / 32 - 1) / (block / 32);
+  const long long per_block = (long long)(block / 32) * (32 / lanes);
+  const long long need = (p.n_cand + per_block - 1) / per_block;
   if (grid > need) grid = (int)need;
-  grid_batched<<<grid, block, smem, s>>>(p);
+  if (lanes == 8)
+    grid_batched<8><<<grid, block, smem, s>>>(p);
+  else
+    grid_batched<32><<<grid, block, smem, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -83,7 +83,7 @@ extern "C" dg_status dg_grid_search_noalloc(dg_model* model, const dg_grid_desc*
     return dg::set_error(DG_E_CUDA, "dg_grid_search_noalloc: ticket reset failed");
   dg::LaunchCfg cfg;
   cfg.block = 256;
-  const int want = dg::grid_blocks(0, p.n_cand, p.n_trials);
+  const int want = dg::grid_blocks(0, p.n_cand, p.n_trials, dg::grid_lanes(p.L));
   cfg.grid = want < kBlocks ? want : kBlocks;
   if (cfg.grid < 1) cfg.grid = 1;
   cudaError_t e = dg::launch_grid(p, plain ? 1 : 0, cfg, s);

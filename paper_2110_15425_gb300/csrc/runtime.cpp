@@ -377,16 +377,17 @@ std::vector<dg::LaunchCfg> lca_candidates(int N, long long n, bool lpt) {
   return v;
 }
 
-std::vector<dg::LaunchCfg> grid_candidates(long long n_cand) {
+std::vector<dg::LaunchCfg> grid_candidates(long long n_cand, int lanes) {
   std::vector<dg::LaunchCfg> v;
-  const int full = dg::grid_blocks(0, n_cand, 64);
+  const int full = dg::grid_blocks(0, n_cand, 64, lanes);
   for (int per_warp : {0, 2, 3, 4}) {
     dg::LaunchCfg c;
     c.block = 256;
     if (per_warp == 0) {
       c.grid = full;
     } else {
-      long long g = (n_cand + 8LL * per_warp - 1) / (8LL * per_warp);
+      const long long per_block = 8LL * per_warp * (32 / lanes);
+      long long g = (n_cand + per_block - 1) / per_block;
       if (g > (long long)kMaxPartials) continue;
       c.grid = (int)g;
     }
@@ -675,7 +676,7 @@ dg_status grid_device(dg_model* m, const dg_grid_desc* d, dg_grid_result* result
   if (d->mode == DG_MODE_PLAIN) return go(dg::LaunchCfg{});
   const std::string key = "grid/" + std::to_string(log2_bucket(p.n_cand)) + "/" +
                           std::to_string(log2_bucket(p.n_trials));
-  return run_tuned(m->ctx, key, grid_candidates(p.n_cand), s, go);
+  return run_tuned(m->ctx, key, grid_candidates(p.n_cand, dg::grid_lanes(p.L)), s, go);
 }
 
 // ------------------------------------------------------------ serving ---
