@@ -181,7 +181,25 @@ __device__ void finish_episode(const EpisodeParams& p, int e) {
   p.ticket[e] = 0u;  // ready for the next step
 }
 
+// Pair sum over the LANES lanes of a candidate's group (xor butterfly; the
+// group's first lane holds the total in a fixed order).
+template <int LANES>
+__device__ __forceinline__ void lane_group_pair_sum(float& hi, float& lo) {
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(kFull, hi, o);
+    const float ol = __shfl_xor_sync(kFull, lo, o);
+    two_sum_add(hi, lo, oh);
+    lo += ol;
+  }
+}
+
+// LANES lanes per candidate, as the grid search takes them for a grid of this
+// size (grid_lanes): eight, four candidates per warp, for grids of 16,384
+// candidates or more, else a whole warp.
+template <int LANES>
 __global__ void __launch_bounds__(256) episode_step(EpisodeParams p) {
+  constexpr int kPerWarp = 32 / LANES;   // candidates of a warp at a time
   __shared__ TopTwo warp_best[8];
   __shared__ bool last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -210,29 +228,40 @@ __global__ void __launch_bounds__(256) episode_step(EpisodeParams p) {
     for (int d = 0; d < 6; ++d) S[d] = __ldcg(p.state + 6 * e + d);
     TopTwo best = top_init();
     const long long c_end = min((long long)(chunk + 1) * kEpisodeChunk, p.n_cand);
-    // the warp's candidates c0 + 8 i: lane i keeps candidate i's pair, and the
-    // eight means are formed in FP64 together at the end
-    const long long c0 = (long long)chunk * kEpisodeChunk + warp;
+    // the block's 64 candidates, kPerWarp per warp at a time: group g of warp w
+    // takes candidate c0 + 8 kPerWarp i + kPerWarp w + g; lane kPerWarp i + g
+    // keeps its pair, and the warp's means are formed in FP64 together at the end
+    const int grp = lane / LANES, gl = lane % LANES;
+    const long long c0 = (long long)chunk * kEpisodeChunk;
     float kh = 0.f, kl = 0.f;
     long long kc = -1;
-    for (long long c = c0; c < c_end; c += 8) {
-      const int l2 = (int)(c % p.L[2]);
-      const int l1 = (int)((c / p.L[2]) % p.L[1]);
-      const int l0 = (int)(c / ((long long)p.L[2] * p.L[1]));
-      const float a0 = __ldg(p.lv[0] + l0), a1 = __ldg(p.lv[1] + l1), a2 = __ldg(p.lv[2] + l2);
-      const float sd0 = 1.0f / (p.offset + a0), sd1 = 1.0f / (p.offset + a1),
-                  sd2 = 1.0f / (p.offset + a2);
-      const float cost = a0 * a0 + a1 * a1 + a2 * a2;
+    for (int i = 0; (long long)i * 8 * kPerWarp < kEpisodeChunk; ++i) {
+      const long long cb = c0 + (long long)i * 8 * kPerWarp + (long long)warp * kPerWarp;
+      const long long c = cb + grp;
       float hi = 0.f, lo = 0.f;
-      for (int j = lane; j < p.n_trials; j += 32)
-        two_sum_add(hi, lo, pp_outcome_at(p.rk, trial0 + (uint32_t)j, (uint32_t)c,
-                                          2u * (p.e0 + (uint32_t)e), S, sd0, sd1, sd2, p.weight,
-                                          cost));
-      warp_pair_sum(hi, lo);
-      if (lane == (int)((c - c0) / 8)) {
-        kh = hi;
-        kl = lo;
-        kc = c;
+      if (c < c_end) {
+        const uint32_t u = (uint32_t)c, q = u / (uint32_t)p.L[2];   // c < 2^32 (n_cand checked)
+        const int l2 = (int)(u - q * (uint32_t)p.L[2]);
+        const int l1 = (int)(q % (uint32_t)p.L[1]);
+        const int l0 = (int)(q / (uint32_t)p.L[1]);
+        const float a0 = __ldg(p.lv[0] + l0), a1 = __ldg(p.lv[1] + l1), a2 = __ldg(p.lv[2] + l2);
+        const float sd0 = 1.0f / (p.offset + a0), sd1 = 1.0f / (p.offset + a1),
+                    sd2 = 1.0f / (p.offset + a2);
+        const float cost = a0 * a0 + a1 * a1 + a2 * a2;
+        for (int j = gl; j < p.n_trials; j += LANES)
+          two_sum_add(hi, lo, pp_outcome_at(p.rk, trial0 + (uint32_t)j, (uint32_t)c,
+                                            2u * (p.e0 + (uint32_t)e), S, sd0, sd1, sd2,
+                                            p.weight, cost));
+      }
+      lane_group_pair_sum<LANES>(hi, lo);
+      const int g = lane - i * kPerWarp;
+      const bool mine = g >= 0 && g < kPerWarp;
+      const int src = mine ? g * LANES : 0;
+      const float th = __shfl_sync(kFull, hi, src), tl = __shfl_sync(kFull, lo, src);
+      if (mine && cb + g < c_end) {
+        kh = th;
+        kl = tl;
+        kc = cb + g;
       }
     }
     if (kc >= 0) best = TopTwo{((double)kh + (double)kl) * inv, kc, -DBL_MAX};
@@ -263,15 +292,22 @@ cudaError_t launch_episode_init(const EpisodeParams& p, cudaStream_t s) {
 }
 
 cudaError_t launch_episode_step(const EpisodeParams& p, cudaStream_t s) {
-  static int blocks = 0;
-  if (blocks == 0) {
+  const bool narrow = grid_lanes(p.L) == 8;
+  static int blocks[2] = {0, 0};
+  if (blocks[narrow] == 0) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, episode_step, 256, 0);
-    blocks = num_sms() * (nb > 0 ? nb : 1);
+    if (narrow)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, episode_step<8>, 256, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, episode_step<32>, 256, 0);
+    blocks[narrow] = num_sms() * (nb > 0 ? nb : 1);
   }
   long long g = (long long)p.E * p.cpe;
-  if (g > blocks) g = blocks;
-  episode_step<<<(unsigned)g, 256, 0, s>>>(p);
+  if (g > blocks[narrow]) g = blocks[narrow];
+  if (narrow)
+    episode_step<8><<<(unsigned)g, 256, 0, s>>>(p);
+  else
+    episode_step<32><<<(unsigned)g, 256, 0, s>>>(p);
   return cudaGetLastError();
 }
 
