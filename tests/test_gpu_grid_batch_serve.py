@@ -3,7 +3,7 @@ graph batches and the serving loop against single runs."""
 import numpy as np
 import pytest
 
-from gpu_util import compare_decisions, dev, host
+from gpu_util import dev, host
 
 pytestmark = pytest.mark.gpu
 
