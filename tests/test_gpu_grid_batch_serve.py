@@ -82,6 +82,41 @@ def test_grid_full_size(ctx, orc, threads):
         _check_best(ref, best, val, gap)
 
 
+def test_grid_narrow_groups_ragged(ctx, orc, threads):
+    """Grids of 16,384 candidates or more take eight lanes per candidate: a
+    ragged one (17 x 31 x 37 = 19,499 candidates, 37 trials, so neither count
+    fills the groups), whole and as two candidate ranges, through both entry
+    points, against the oracle; the ranges give the whole call's means bit
+    for bit."""
+    import torch
+    from paper_2110_15425_gb300 import binding as B
+    from paper_2110_15425_gb300 import workloads as W
+    g = W.predator_prey(n_trials=37)
+    rng = np.random.default_rng(19)
+    lv = [np.sort(rng.uniform(0, 1, k)).astype(np.float32) for k in (17, 31, 37)]
+    nc = 17 * 31 * 37
+    ref = orc.pp_means(g["pos"], lv, g["seed"], threads=threads)
+    model = B.compose_predator_prey(ctx)
+    try:
+        for search in (B.dg_grid_search, B.dg_grid_search_noalloc):
+            res = torch.zeros(3, dtype=torch.float64, device="cuda")
+            means = torch.zeros(nc, dtype=torch.float64, device="cuda")
+            search(model, B.grid_desc([dev(x) for x in lv], dev(g["pos"]), g["seed"]), res, means)
+            m = host(means)
+            assert np.max(np.abs(m - ref) / np.maximum(np.abs(ref), 1.0)) < 1e-5
+            r = host(res)
+            _check_best(ref, int(r[:1].view(np.int64)[0]), float(r[1]), float(r[2]))
+            parts = []
+            for b, c in ((0, 8000), (8000, nc - 8000)):
+                pm = torch.zeros(c, dtype=torch.float64, device="cuda")
+                search(model, B.grid_desc([dev(x) for x in lv], dev(g["pos"]), g["seed"],
+                                          cand_begin=b, cand_count=c), res, pm)
+                parts.append(host(pm))
+            assert np.concatenate(parts).tobytes() == m.tobytes()
+    finally:
+        B.dg_model_free(model)
+
+
 def test_argmax_ties_and_sizes(ctx):
     import torch
     from paper_2110_15425_gb300 import binding as B
