@@ -59,6 +59,13 @@ OPS_PER_UNIT = {"ddm": 32, "lca4": 4 * 31, "lca8": 8 * 31, "lca16": 16 * 31, "st
 # (the 5 MB of outputs stay in L2 within the launch). Algorithmic: 8 B of
 # parameters in and 5 B out per trial = 13.6 MB.
 DDM_TRAFFIC_BYTES = 12_654_080
+# DRAM bytes of one wide_kernel launch over the 16,384-trial job, from
+# `ncu --set full --clock-control none -k regex:wide_kernel -s 1 -c 1 python bench.py --only wide`
+# on the current kernel (profiles/wide_kernel_16384_trials.md): 158,720 read + 0 written.
+# Algorithmic: the weights (hidden 256 x 32 FP32, the response layer's 16 x 512 BF16 operand
+# image), the 256 condition rows (80 KB read) and 5 B of outputs per trial (82 KB): 0.16 MB.
+WIDE_TRAFFIC_BYTES = 158_720
+TRAFFIC_BYTES = {"ddm": DDM_TRAFFIC_BYTES, "wide": WIDE_TRAFFIC_BYTES}
 LANES_PER_SM = 128
 # The pass's jobs, longest first. Graph branches are created (and served jobs
 # submitted) in this order: the wide network's CTAs take their SMs before the
@@ -648,7 +655,7 @@ def main():
     roofline = {"bound": "alu", "kernel": kernel_names[dominant],
                 "achieved": by_kernel[dominant]["achieved"], "peak": peak_ops / 1e12,
                 "unit": "Tlane-op/s", "frac": by_kernel[dominant]["frac"],
-                "traffic": DDM_TRAFFIC_BYTES if dominant == "ddm" else None,
+                "traffic": TRAFFIC_BYTES.get(dominant),
                 "peak_source": peak_src, "ops_per_unit": OPS_PER_UNIT[dominant],
                 "by_kernel": by_kernel,
                 "ddm": {"kernel": "ddm_batched", "frac": by_kernel["ddm"]["frac"],
