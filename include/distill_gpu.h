@@ -227,7 +227,11 @@ dg_status dg_run(dg_model* model, const dg_run_desc* desc, int8_t* choice, int32
    dg_argmax_f64_reservoir does over the evaluated candidates (indices
    cand_begin ..) in order.
    result: device pointer to one dg_grid_result.
-   cand_means (may be NULL): device, FP64 [L0 L1 L2] mean outcome per candidate.
+   cand_means (may be NULL): device, FP64 mean outcome per evaluated candidate
+   ([cand_count], [L0 L1 L2] for the whole grid). A candidate's mean has the
+   same bits whatever range of candidates a call evaluates and whatever launch
+   shape the library picks, so a search split across calls or GPUs reassembles
+   exactly.
    Errors: DG_E_ARG, DG_E_UNSUPPORTED (not a PREDATOR_PREY model), DG_E_CUDA. */
 dg_status dg_grid_search(dg_model* model, const dg_grid_desc* desc, dg_grid_result* result,
                          double* cand_means, void* stream);
