@@ -73,10 +73,6 @@ struct WideShared {
   float yr[kR][kRows];   // response outputs of the step, [unit][trial row]
 };
 
-__device__ __forceinline__ uint32_t bf16_bits(float f) {
-  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f));
-}
-
 // y = hi + lo with hi = bf16(y), lo = bf16(y - hi); two values per word, one
 // paired conversion for each half.
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
