@@ -46,22 +46,23 @@ WORKLOAD = ("hot-path pass: Stroop 4x1000 (weights seed 0) + DDM 2^20 + LCA 2621
 #   LCA unit-step: normal + drive, update, rectify, sum and max     31
 #   logistic unit-step: normal + integrate (3) + logistic (4)       26
 #   Stroop trial-step: 6 logistic units, 24 edges, stop test        200
-#   wide trial-step: 272 logistic units + bf16 hi/lo split (3 each),
-#     16-way stop test; the 256 x 16 response GEMM runs on tensor cores  7,900
+#   wide trial-step: 272 logistic units (26 each) + the 16-way stop
+#     test (60); the 256 x 16 response GEMM runs on tensor cores and
+#     the kernel's own precision device (bf16 hi/lo activations) is not
+#     counted                                                      7,132
 #   grid evaluation: 6 normals, 3 normalisations, distance, FP64 add   120
 DDM_OPS_PER_TRIAL_STEP = 32
 OPS_PER_UNIT = {"ddm": 32, "lca4": 4 * 31, "lca8": 8 * 31, "lca16": 16 * 31, "stroop": 200,
-                "wide": 7900, "grid": 120}
+                "wide": 7132, "grid": 120}
 # DRAM bytes (read + write) of one ddm_batched launch over the 2^20-trial job,
 # from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
 # -k regex:ddm_batched -s 1 -c 1 python bench.py --only ddm` on the current
-# kernel (profiles/ddm_batched_2p20_trials.md): 12,653,824 read + 256 written
-# (the 5 MB of outputs stay in L2 within the launch). Algorithmic: 8 B of
-# parameters in and 5 B out per trial = 13.6 MB.
+# kernel: 12,653,824 read + 256 written (the 5 MB of outputs stay in L2 within
+# the launch). Algorithmic: 8 B of parameters in and 5 B out per trial = 13.6 MB.
 DDM_TRAFFIC_BYTES = 12_654_080
 # DRAM bytes of one wide_kernel launch over the 16,384-trial job, from
 # `ncu --set full --clock-control none -k regex:wide_kernel -s 1 -c 1 python bench.py --only wide`
-# on the current kernel (profiles/wide_kernel_16384_trials.md): 158,720 read + 0 written.
+# on the current kernel: 158,720 read + 0 written.
 # Algorithmic: the weights (hidden 256 x 32 FP32, the response layer's 16 x 512 BF16 operand
 # image), the 256 condition rows (80 KB read) and 5 B of outputs per trial (82 KB): 0.16 MB.
 WIDE_TRAFFIC_BYTES = 158_720
@@ -385,28 +386,28 @@ class NvmlClockSampler:
 
 # ----------------------------------------------------------- CPU oracle ---
 
-def cpu_baseline(seconds_hint=True):
+def cpu_baseline(threads=None, every=1):
     """The oracle as it stands, on this host's cores, over a bounded sample of
-    the same pass (a fixed fraction of every job). Returns (value, cores, sample)."""
+    the same pass: every `every`-th trial (or candidate) of each job, and every
+    2*`every`-th trial of the wide job. Returns (value, threads, sample)."""
     import oracle
     from paper_2110_15425_gb300 import workloads as W
-    threads = os.cpu_count() or 1
-    frac = 1
-    wide_every = 2
+    threads = threads or (os.cpu_count() or 1)
+    wide_every = 2 * every
     t0 = time.perf_counter()
     steps = 0
     s = W.stroop_small()
-    ids = np.arange(0, s["n_trials"], 1, dtype=np.uint32)
+    ids = np.arange(0, s["n_trials"], every, dtype=np.uint32)
     o = oracle.transfer_run(s["layers"], s["projections"], s["cond_inputs"], s["cond_block"],
                             s["seed"], trial_ids=ids, threads=threads)
     steps += int(o["step"].sum())
     w = W.ddm()
-    ids = np.arange(0, w["A"].shape[0], frac, dtype=np.uint32)
+    ids = np.arange(0, w["A"].shape[0], every, dtype=np.uint32)
     o = oracle.ddm_run(w["A"], w["z"], w["seed"], trial_ids=ids, threads=threads)
     steps += int(o["step"].sum())
     for N in (4, 8, 16):
         l = W.lca(N=N)
-        ids = np.arange(0, l["I"].shape[0], frac, dtype=np.uint32)
+        ids = np.arange(0, l["I"].shape[0], every, dtype=np.uint32)
         o = oracle.lca_run(l["I"], l["seed"], trial_ids=ids, threads=threads)
         steps += int(o["step"].sum())
     wd = W.stroop_wide(n_trials=WIDE_TRIALS)
@@ -415,28 +416,43 @@ def cpu_baseline(seconds_hint=True):
                             trial_ids=ids, threads=threads)
     steps += int(o["step"].sum())
     g = W.predator_prey()
-    ids = np.arange(0, 27000, frac, dtype=np.uint32)
+    ids = np.arange(0, 27000, every, dtype=np.uint32)
     oracle.pp_means(g["pos"], g["levels"], g["seed"], cand_ids=ids, threads=threads)
     steps += ids.shape[0] * g["pos"].shape[0]
     dt = time.perf_counter() - t0
-    sample = (f"the whole Stroop, DDM, LCA and grid jobs, every {wide_every}nd trial of the wide "
-              f"job: {steps} trial-steps in {dt:.1f} s")
+    sample = (f"every {every} trial(s) or candidate(s) of the Stroop, DDM, LCA and grid jobs and "
+              f"every {wide_every} trials of the wide job on {threads} thread(s): {steps} "
+              f"trial-steps in {dt:.1f} s")
     return steps / dt, threads, sample
 
 
+def cpu_baselines():
+    """All-core and single-thread rates of the oracle (the single-thread one
+    over a 16 times sparser sample, so that both take seconds)."""
+    v, cores, sample = cpu_baseline()
+    v1, _, sample1 = cpu_baseline(threads=1, every=16)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "sample": sample1}}
+
+
 # ------------------------------------------------------------- reference ---
+
+# Each reference step runs the oracle on every REF_EVERY-th trial of every job,
+# so that the default --steps/--warmup run ends within a few minutes.
+REF_EVERY = 4
+
 
 def run_reference(args):
     rank, local, world = dist_env()
     if rank != 0:
         return
-    vals = []
     for _ in range(args.warmup):
-        pass
+        cpu_baseline(every=REF_EVERY)
+    vals = []
     sample = cores = None
     t0 = time.perf_counter()
     for _ in range(max(1, args.steps)):
-        v, cores, sample = cpu_baseline()
+        v, cores, sample = cpu_baseline(every=REF_EVERY)
         vals.append(v)
     wall = time.perf_counter() - t0
     value = statistics.mean(vals)
@@ -676,8 +692,7 @@ def main():
         ext = extensions(B, W, torch, ctx, per_job["grid"]["ms"])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, sample = cpu_baseline()
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = cpu_baselines()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,

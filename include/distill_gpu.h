@@ -362,6 +362,19 @@ dg_status dg_stream_status(dg_ctx* ctx, void* stream);
    the paper has no counterpart. */
 dg_status dg_selftest_wait_timeout(dg_ctx* ctx, int32_t wait_us, void* stream);
 
+/* The per-candidate reduction of dg_grid_search and dg_run_episodes applied to
+   given values, so that it can be checked on its own against exact sums (the
+   FP64 per-candidate means that feed the argmax, Sec. 3.6). Group g of
+   per_group FP32 values values[g per_group .. (g + 1) per_group - 1] is reduced
+   as a candidate's trial outcomes are: `lanes` (8 or 32) lanes each add every
+   lanes-th value into a compensated FP32 pair (TwoSum), the group combines its
+   pairs in a fixed butterfly order, and means[g] = (hi + lo) / per_group in
+   FP64. values, means: device; per_group 1 .. 1024. Test aid; the paper
+   describes the reduction only as per-evaluation results that are combined.
+   Errors: DG_E_ARG, DG_E_CUDA. */
+dg_status dg_selftest_pair_sum(const float* values, int64_t n_groups, int32_t per_group,
+                               int32_t lanes, double* means, void* stream);
+
 /* Allocation-free dg_grid_search. The paper has no counterpart: this entry
    point exists for callers that may not allocate device memory themselves or
    let a library do it behind their back - code that runs while someone else's
@@ -376,8 +389,11 @@ dg_status dg_selftest_wait_timeout(dg_ctx* ctx, int32_t wait_us, void* stream);
    Same arguments, outputs and results as dg_grid_search, with these limits:
      - DG_MODE_PLAIN, or DG_TIE_RESERVOIR, without cand_means evaluates at
        most 32768 candidates per call (DG_E_ARG beyond that);
-     - the first call on a device looks up the array's device address; make
-       that first call before any stream capture on that device;
+     - the first call on a device looks up the array's device address and
+       keeps it for the life of the process; make that first call before any
+       stream capture on that device. A reset of the device's primary context
+       after that first call (cudaDeviceReset, or a framework doing one)
+       reloads the library's device memory elsewhere and is not supported;
      - every call shares the one array and it keeps the last call's contents
        (the call clears what must start at zero), so calls that may overlap
        on the GPU, e.g. on two streams without ordering, race: order them. */

@@ -114,7 +114,7 @@ EXPORTS = [
     "dg_normals", "dg_batch_create", "dg_batch_add_run", "dg_batch_add_grid",
     "dg_batch_launch", "dg_batch_kernels", "dg_batch_free", "dg_submit", "dg_wait", "dg_serve_stats",
     "dg_grid_search_noalloc", "dg_stream_status", "dg_selftest_wait_timeout",
-    "dg_argmax_f64_reservoir", "dg_grid_refine", "dg_run_episodes",
+    "dg_argmax_f64_reservoir", "dg_grid_refine", "dg_run_episodes", "dg_selftest_pair_sum",
 ]
 
 _lib = None
@@ -149,6 +149,7 @@ def _declare(L):
         "dg_grid_search_noalloc": [P, C.POINTER(dg_grid_desc), P, P, P],
         "dg_stream_status": [P, P],
         "dg_selftest_wait_timeout": [P, i32, P],
+        "dg_selftest_pair_sum": [P, i64, i32, i32, P, P],
         "dg_argmax_f64": [P, P, i64, P, P],
         "dg_argmax_f64_reservoir": [P, P, i64, u64, P, P],
         "dg_grid_refine": [P, C.POINTER(dg_refine_desc), P, P],
@@ -251,6 +252,11 @@ def dg_grid_search_noalloc(model, desc, result, cand_means=None, stream=None):
 
 def dg_selftest_wait_timeout(ctx, wait_us, stream=None):
     check(lib().dg_selftest_wait_timeout(ctx, wait_us, stream_handle(stream)))
+
+
+def dg_selftest_pair_sum(values, n_groups, per_group, lanes, means, stream=None):
+    check(lib().dg_selftest_pair_sum(ptr(values), n_groups, per_group, lanes, ptr(means),
+                                     stream_handle(stream)))
 
 
 def dg_stream_status(ctx, stream=None):

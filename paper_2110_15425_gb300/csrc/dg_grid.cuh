@@ -76,6 +76,25 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
   hi = s;
 }
 
+// Pair sum over the LANES lanes of a candidate's group, by an xor
+// butterfly; every lane of the group ends with the total, added in a fixed
+// order.
+template <int LANES>
+__device__ __forceinline__ void group_pair_sum(float& hi, float& lo) {
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(kFull, hi, o);
+    const float ol = __shfl_xor_sync(kFull, lo, o);
+    two_sum_add(hi, lo, oh);
+    lo += ol;
+  }
+}
+
+// FP64 mean of a candidate from its pair and 1 / (number of trials).
+__device__ __forceinline__ double pair_mean(float hi, float lo, double inv) {
+  return ((double)hi + (double)lo) * inv;
+}
+
 // Warp total of the lanes' pairs, returned to every lane (tree toward lane 0,
 // then broadcast, so every lane holds the same pair).
 __device__ __forceinline__ void warp_pair_sum(float& hi, float& lo) {

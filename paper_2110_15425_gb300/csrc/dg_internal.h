@@ -283,7 +283,17 @@ cudaError_t launch_normals(uint64_t seed, uint32_t trial, uint32_t cand, uint64_
                            float* out, cudaStream_t s);
 
 cudaError_t launch_wait_timeout(long long limit_cycles, int* status, cudaStream_t s);
+// The grid search's per-candidate reduction on given values (lanes 8 or 32).
+cudaError_t launch_pair_sum(const float* x, long long n_groups, int per, int lanes,
+                            double* means, cudaStream_t s);
 
+// Multiprocessors of the current device (looked up once per device).
 int num_sms();
+
+// Raise the dynamic shared-memory limit of kernel `fn` to at least `bytes` on
+// the current device. The attribute is per device, so it is set once per
+// (kernel, device) pair and again only when a larger limit is asked for;
+// thread-safe. Returns the CUDA error of the attribute call, if any.
+cudaError_t smem_limit(const void* fn, int bytes);
 
 }  // namespace dg

@@ -181,19 +181,6 @@ __device__ void finish_episode(const EpisodeParams& p, int e) {
   p.ticket[e] = 0u;  // ready for the next step
 }
 
-// Pair sum over the LANES lanes of a candidate's group (xor butterfly; the
-// group's first lane holds the total in a fixed order).
-template <int LANES>
-__device__ __forceinline__ void lane_group_pair_sum(float& hi, float& lo) {
-#pragma unroll
-  for (int o = LANES / 2; o > 0; o >>= 1) {
-    const float oh = __shfl_xor_sync(kFull, hi, o);
-    const float ol = __shfl_xor_sync(kFull, lo, o);
-    two_sum_add(hi, lo, oh);
-    lo += ol;
-  }
-}
-
 // LANES lanes per candidate, as the grid search takes them for a grid of this
 // size (grid_lanes): eight, four candidates per warp, for grids of 16,384
 // candidates or more, else a whole warp.
@@ -253,7 +240,7 @@ __global__ void __launch_bounds__(256) episode_step(EpisodeParams p) {
                                             2u * (p.e0 + (uint32_t)e), S, sd0, sd1, sd2,
                                             p.weight, cost));
       }
-      lane_group_pair_sum<LANES>(hi, lo);
+      group_pair_sum<LANES>(hi, lo);
       const int g = lane - i * kPerWarp;
       const bool mine = g >= 0 && g < kPerWarp;
       const int src = mine ? g * LANES : 0;
@@ -264,7 +251,7 @@ __global__ void __launch_bounds__(256) episode_step(EpisodeParams p) {
         kc = cb + g;
       }
     }
-    if (kc >= 0) best = TopTwo{((double)kh + (double)kl) * inv, kc, -DBL_MAX};
+    if (kc >= 0) best = TopTwo{pair_mean(kh, kl, inv), kc, -DBL_MAX};
     best = top_warp(best);
     if (lane == 0) warp_best[warp] = best;
     __syncthreads();

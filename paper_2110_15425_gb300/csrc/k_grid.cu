@@ -116,19 +116,6 @@ __device__ void finish_argmax(TopTwo mine, TopTwo* partials, unsigned int* ticke
   }
 }
 
-// Pair sum over the LANES lanes of a candidate's group, by an xor
-// butterfly; the group's first lane holds the total in a fixed order.
-template <int LANES>
-__device__ __forceinline__ void group_pair_sum(float& hi, float& lo) {
-#pragma unroll
-  for (int o = LANES / 2; o > 0; o >>= 1) {
-    const float oh = __shfl_xor_sync(kFull, hi, o);
-    const float ol = __shfl_xor_sync(kFull, lo, o);
-    two_sum_add(hi, lo, oh);
-    lo += ol;
-  }
-}
-
 template <int LANES>
 __global__ void __launch_bounds__(256) grid_batched(GridParams p) {
   constexpr int kGridLanes = LANES, kGridCandsPerWarp = 32 / LANES;
@@ -148,7 +135,7 @@ __global__ void __launch_bounds__(256) grid_batched(GridParams p) {
   int slot = 0;
   auto flush = [&]() {
     if (kc >= 0) {
-      const double mean = ((double)kh + (double)kl) * inv;
+      const double mean = pair_mean(kh, kl, inv);
       if (p.means) p.means[kc] = mean;
       best = top_merge(best, TopTwo{mean, p.cand0 + kc, -DBL_MAX});
     }
@@ -429,7 +416,7 @@ __global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(1024, 1
     long long kc = -1;
     int slot = 0;
     auto flush = [&]() {
-      if (kc >= 0) best = top_merge(best, TopTwo{((double)kh + (double)kl) * inv, kc, -DBL_MAX});
+      if (kc >= 0) best = top_merge(best, TopTwo{pair_mean(kh, kl, inv), kc, -DBL_MAX});
       kc = -1;
     };
     // candidates as grid_batched evaluates grids of this size (a round holds at
@@ -543,15 +530,10 @@ int grid_blocks(int mode, long long n_cand, int n_trials, int lanes) {
 
 cudaError_t launch_grid(const GridParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s) {
   const size_t smem = grid_smem(p);  // <= 6 * 1024 + 3 * 4096 floats (runtime limits)
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(grid_batched<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    cudaFuncSetAttribute(grid_batched<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    cudaFuncSetAttribute(grid_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    attr = true;
-  }
   if (p.n_cand <= 0) return cudaSuccess;
   if (mode == 1) {
+    cudaError_t ea = smem_limit((const void*)grid_plain, 96 * 1024);
+    if (ea != cudaSuccess) return ea;
     const long long grid = (p.n_cand + 255) / 256;
     grid_plain<<<(unsigned)grid, 256, smem, s>>>(p);
     cudaError_t e = cudaGetLastError();
@@ -570,6 +552,9 @@ cudaError_t launch_grid(const GridParams& p, int mode, const LaunchCfg& cfg, cud
   const long long per_block = (long long)(block / 32) * (32 / lanes);
   const long long need = (p.n_cand + per_block - 1) / per_block;
   if (grid > need) grid = (int)need;
+  cudaError_t ea = lanes == 8 ? smem_limit((const void*)grid_batched<8>, 96 * 1024)
+                              : smem_limit((const void*)grid_batched<32>, 96 * 1024);
+  if (ea != cudaSuccess) return ea;
   if (lanes == 8)
     grid_batched<8><<<grid, block, smem, s>>>(p);
   else

@@ -401,12 +401,8 @@ cudaError_t launch_n(const LcaParams& p, int mode, const LaunchCfg& cfg, cudaStr
     case 0: {   // block-level compaction, one lane per trial (256 threads)
       if constexpr (N <= 16) {
         const size_t smem = compact_smem(N);
-        static bool attr = false;
-        if (!attr) {
-          cudaFuncSetAttribute(lca_compact<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-          attr = true;
-        }
+        const cudaError_t ea = smem_limit((const void*)lca_compact<N>, (int)smem);
+        if (ea != cudaSuccess) return ea;
         lca_compact<N><<<grid, 256, smem, s>>>(p);
         break;
       }
@@ -469,7 +465,7 @@ int lca_max_blocks_per_sm(int N, int tpt, int block) {
   if (!fn) return 0;
   int nb = 0;
   if (tpt == 0) {
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)compact_smem(N));
+    if (smem_limit(fn, (int)compact_smem(N)) != cudaSuccess) return 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, compact_smem(N));
   } else {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0);

@@ -356,8 +356,7 @@ size_t layout_smem() { return ((sizeof(NetLayout) + 15) / 16) * 16; }
 template <int G, bool EXT>
 cudaError_t launch_group(const NetParams& p, const LaunchCfg& cfg, cudaStream_t s) {
   const size_t smem = layout_smem();
-  cudaError_t e = cudaFuncSetAttribute(net_group<G, EXT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = smem_limit((const void*)net_group<G, EXT>, (int)smem);
   if (e != cudaSuccess) return e;
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, net_group<G, EXT>, 256, smem);
@@ -376,8 +375,7 @@ cudaError_t launch_net(const NetParams& p, int mode, const LaunchCfg& cfg, cudaS
   if (mode == 1 || p.cursor == nullptr) {
     const int B = 128;
     const size_t smem = layout_smem() + (size_t)4 * p.U * B * sizeof(float);
-    cudaError_t e =
-        cudaFuncSetAttribute(net_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = smem_limit((const void*)net_plain, 200 * 1024);
     if (e != cudaSuccess) return e;
     net_plain<<<(unsigned)((p.n + B - 1) / B), B, smem, s>>>(p);
     return cudaGetLastError();

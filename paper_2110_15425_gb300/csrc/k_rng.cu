@@ -49,15 +49,4 @@ cudaError_t launch_normals(uint64_t seed, uint32_t trial, uint32_t cand, uint64_
   return cudaGetLastError();
 }
 
-int num_sms() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
-  return sms;
-}
-
 }  // namespace dg

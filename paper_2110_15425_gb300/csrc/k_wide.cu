@@ -354,8 +354,7 @@ cudaError_t launch_h(const WideParams& p, cudaStream_t s) {
   // more than half of an SM's shared memory, so that two CTAs never share an
   // SM (each takes all 512 TMEM columns)
   if (smem < 120 * 1024) smem = 120 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(wide_kernel<H, TC>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = smem_limit((const void*)wide_kernel<H, TC>, (int)smem);
   if (e != cudaSuccess) return e;
   long long grid = (p.n + kRows - 1) / kRows;
   const long long cap = (long long)num_sms();  // one CTA per SM (all of its TMEM)

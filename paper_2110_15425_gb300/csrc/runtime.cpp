@@ -1577,6 +1577,19 @@ dg_status dg_selftest_wait_timeout(dg_ctx* ctx, int32_t wait_us, void* stream) {
   return DG_OK;
 }
 
+dg_status dg_selftest_pair_sum(const float* values, int64_t n_groups, int32_t per_group,
+                               int32_t lanes, double* means, void* stream) {
+  if (n_groups < 0 || per_group < 1 || per_group > 1024 || (lanes != 8 && lanes != 32) ||
+      (n_groups > 0 && (!values || !means)))
+    return fail(DG_E_ARG,
+                "dg_selftest_pair_sum: need n_groups >= 0, per_group in [1, 1024], lanes 8 or 32, "
+                "non-null pointers");
+  if (n_groups > (int64_t)1 << 40)
+    return fail(DG_E_ARG, "dg_selftest_pair_sum: n_groups too large");
+  DG_CUDA(dg::launch_pair_sum(values, n_groups, per_group, lanes, means, (cudaStream_t)stream));
+  return DG_OK;
+}
+
 dg_status dg_philox_words(uint64_t seed, uint32_t trial, uint32_t cand, uint32_t purpose,
                           uint32_t block0, int64_t nblocks, uint32_t* out, void* stream) {
   if (nblocks < 0 || (nblocks > 0 && !out)) return fail(DG_E_ARG, "dg_philox_words: bad arguments");

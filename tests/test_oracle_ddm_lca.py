@@ -5,7 +5,8 @@ the continuous process has P(upper) = 1 / (1 + exp(-2 A z / s^2)) and mean
 decision time (z / A) tanh(A z / s^2). Checking the barrier only every dt
 shifts it outward by beta s sqrt(dt), beta = -zeta(1/2)/sqrt(2 pi) ~ 0.5826
 (Broadie, Glasserman & Kou 1997); the closed forms are evaluated at the
-shifted barrier, and at dt = 1e-4 too, where the shift is small.
+shifted barrier, and at dt = 1e-4 and 1e-5 on nine fixed points too, where
+the shift is small.
 
 LCA: the equivalence mapping of Sec. 4.4 (Fig. clones: LCA with zero rate and
 offset, unit-normal noise is the DDM integrator), the noise-free fixed point,
@@ -61,6 +62,39 @@ def test_ddm_closed_forms(orc, threads, dt, points, n):
         t = o["step"] * dt
         zt_raw = (t.mean() - _mean_dt(A, z)) / (t.std() / math.sqrt(n))
         assert zt_raw > 4.0
+
+
+# Nine fixed (A, z) points spanning the workload's drift and bound ranges.
+SMALL_DT_POINTS = [(A, z) for A in (0.4, 0.7, 1.0) for z in (0.5, 1.0, 1.5)]
+
+
+@pytest.mark.parametrize("dt,n", [(1e-4, 2000), (1e-5, 1000)])
+def test_ddm_closed_forms_small_dt(orc, threads, dt, n):
+    """At small dt the barrier shift beta s sqrt(dt) shrinks (0.0058 at 1e-4,
+    0.0018 at 1e-5) and the discrete walk approaches the continuous closed
+    forms: P(upper) and mean DT on nine fixed points, each |z-score| < 4, and
+    the pooled z-scores over the nine points < 4 as well."""
+    sum_dev_p = sum_var_p = 0.0
+    zts = []
+    for pi, (A, z) in enumerate(SMALL_DT_POINTS):
+        lam1 = A * A / 2 + math.pi**2 / (8 * z * z)
+        o = orc.ddm_run(np.full(n, A, np.float32), np.full(n, z, np.float32), seed=5000 + pi,
+                        dt=dt, max_steps=int(25.0 / lam1 / dt), threads=threads)
+        assert np.all(o["choice"] >= 0), "survival mass must be negligible"
+        Af, zf = float(np.float32(A)), float(np.float32(z))
+        zeff = zf + BETA * math.sqrt(dt)
+        p = _p_upper(Af, zeff)
+        k = int((o["choice"] == 1).sum())
+        zp = (k - n * p) / math.sqrt(n * p * (1 - p))
+        assert abs(zp) < 4.0, (A, z, k / n, p)
+        sum_dev_p += k - n * p
+        sum_var_p += n * p * (1 - p)
+        t = o["step"] * dt
+        zt = (t.mean() - _mean_dt(Af, zeff)) / (t.std() / math.sqrt(n))
+        assert abs(zt) < 4.0, (A, z, t.mean(), _mean_dt(Af, zeff))
+        zts.append(zt)
+    assert abs(sum_dev_p / math.sqrt(sum_var_p)) < 4.0
+    assert abs(sum(zts) / math.sqrt(len(zts))) < 4.0
 
 
 def test_ddm_noise_free_crossing(orc):
