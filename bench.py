@@ -60,12 +60,9 @@ OPS_PER_UNIT = {"ddm": 32, "lca4": 4 * 31, "lca8": 8 * 31, "lca16": 16 * 31, "st
 # kernel: 12,653,824 read + 256 written (the 5 MB of outputs stay in L2 within
 # the launch). Algorithmic: 8 B of parameters in and 5 B out per trial = 13.6 MB.
 DDM_TRAFFIC_BYTES = 12_654_080
-# DRAM bytes of one wide_kernel launch over the 16,384-trial job, from
-# `ncu --set full --clock-control none -k regex:wide_kernel -s 1 -c 1 python bench.py --only wide`
-# on the current kernel: 158,720 read + 0 written.
-# Algorithmic: the weights (hidden 256 x 32 FP32, the response layer's 16 x 512 BF16 operand
-# image), the 256 condition rows (80 KB read) and 5 B of outputs per trial (82 KB): 0.16 MB.
-WIDE_TRAFFIC_BYTES = 158_720
+# DRAM bytes of one wide_block_kernel launch over the 16,384-trial job: not yet
+# captured on the current kernel (None until an ncu capture of it is taken).
+WIDE_TRAFFIC_BYTES = None
 TRAFFIC_BYTES = {"ddm": DDM_TRAFFIC_BYTES, "wide": WIDE_TRAFFIC_BYTES}
 LANES_PER_SM = 128
 # The pass's jobs, longest first. Graph branches are created (and served jobs
@@ -662,7 +659,7 @@ def main():
         ach = ts[name] * OPS_PER_UNIT[name] / (job["ms"] / 1000.0)
         by_kernel[name] = {"achieved": ach / 1e12, "frac": ach / peak_ops,
                            "ops_per_unit": OPS_PER_UNIT[name]}
-    kernel_names = {"ddm": "ddm_batched", "wide": "wide_kernel<256, tensor cores>",
+    kernel_names = {"ddm": "ddm_batched", "wide": "wide_block_kernel<256> (tensor cores)",
                     "lca4": "lca_batched<4,*>", "lca8": "lca_batched<8,*>",
                     "lca16": "lca_batched<16,*>", "stroop": "net_group<8>",
                     "grid": "grid_batched"}

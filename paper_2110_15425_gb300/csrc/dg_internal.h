@@ -147,6 +147,7 @@ struct WideParams {
   unsigned long long* cursor;
   int* status;                   // device status word (bounded mbarrier waits)
   PhiloxKeys rk;                 // round keys of (k0, k1)
+  float* net_table;              // scratch [n_cond][H]: hidden net input per condition
 };
 cudaError_t launch_wide(const WideParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
 size_t wide_smem_bytes(int H, int nin, bool tc);

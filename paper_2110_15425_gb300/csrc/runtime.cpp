@@ -73,6 +73,8 @@ struct Scratch {
   size_t perm_cap = 0;
   unsigned char* ext = nullptr;  // episodes: state, lists, tickets, partials
   size_t ext_cap = 0;
+  float* net = nullptr;          // wide network: hidden net input per condition
+  size_t net_cap = 0;
   unsigned long long* cursor() { return reinterpret_cast<unsigned long long*>(base); }
   unsigned int* ticket() { return reinterpret_cast<unsigned int*>(base + 8); }
   int* status() { return reinterpret_cast<int*>(base + 16); }
@@ -173,6 +175,20 @@ dg_status scratch_ext(dg_ctx* ctx, Scratch* sc, size_t n, cudaStream_t s) {
   sc->ext = nullptr;
   DG_CUDA(cudaMalloc(&sc->ext, n));
   sc->ext_cap = n;
+  return DG_OK;
+}
+
+dg_status scratch_net(dg_ctx* ctx, Scratch* sc, size_t n, cudaStream_t s) {
+  if (sc->net_cap >= n) return DG_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    return fail(DG_E_STATE, "wide network: per-condition table must grow; run once before capture");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  DG_CUDA(cudaStreamSynchronize(s));
+  if (sc->net) cudaFree(sc->net);
+  sc->net = nullptr;
+  DG_CUDA(cudaMalloc(&sc->net, n * sizeof(float)));
+  sc->net_cap = n;
   return DG_OK;
 }
 
@@ -566,6 +582,11 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
     p.yout = fs;
     p.cursor = sc->cursor();
     p.status = sc->status();
+    if (mode == DG_MODE_BATCHED) {
+      // hidden net input of each condition (H floats per condition)
+      if ((st = scratch_net(m->ctx, sc, (size_t)d->n_cond * m->H, s)) != DG_OK) return st;
+      p.net_table = sc->net;
+    }
     DG_CUDA(cudaMemsetAsync(sc->cursor(), 0, 8, s));
     cudaError_t e = dg::launch_wide(p, mode, dg::LaunchCfg{}, s);
     if (e == cudaErrorNotSupported)
@@ -1030,7 +1051,8 @@ dg_status compose_transfer(dg_model* m, const dg_mechanism* mechs, int n_mech,
     const int H = hid >= 0 ? mechs[hid].size : 0;
     const int nin = (in0 >= 0 ? mechs[in0].size : 0) + (in1 >= 0 ? mechs[in1].size : 0);
     if (ps && pt && pr && pr->dtype == DG_BF16 && H >= 64 && H <= 256 && H % 64 == 0 &&
-        mechs[resp].size == 16 && dg::wide_smem_bytes(H, nin, true) <= 227 * 1024) {
+        mechs[resp].size == 16 && dg::wide_smem_bytes(H, nin, true) <= 227 * 1024 &&
+        dg::wide_smem_bytes(H, nin, false) <= 227 * 1024) {
       m->kind = K_WIDE;
       m->S = mechs[in0].size;
       m->T = mechs[in1].size;
@@ -1209,6 +1231,7 @@ dg_status dg_destroy(dg_ctx* ctx) {
     if (kv.second.means) cudaFree(kv.second.means);
     if (kv.second.ext) cudaFree(kv.second.ext);
     if (kv.second.perm) cudaFree(kv.second.perm);
+    if (kv.second.net) cudaFree(kv.second.net);
   }
   delete ctx;
   return DG_OK;
