@@ -936,105 +936,193 @@ def e2e_serving(B, torch, ctx, step, all_ts, world, rank):
             "api": "dg_submit/dg_wait (serving loop, pinned host buffers)"}
 
 
-def served_mix(B, W, torch, ctx, step, n_jobs=48, seed=7):
-    """Served mix: Poisson arrivals of jobs drawn uniformly from the five
-    workloads, trial counts log-uniform in [1e3, 1e6], admitted under the
-    150 GB budget; arrival rate 0.7x the measured capacity."""
+SERVE_JOBS = 256
+
+
+def _mix(B, W, torch, step, n_jobs, seed):
+    """The served mix: jobs drawn uniformly from the five workloads, trial
+    counts log-uniform in [1e3, 1e6] (grid jobs: levels per signal
+    clamp(round((n / 64)^(1/3)), 2, 30) at 64 trials per candidate). Each job
+    carries its pinned host buffers, a dg_job for the serving API and the device
+    buffers of the plain form."""
     rng = np.random.default_rng(seed)
     kinds = ["stroop", "ddm", "lca", "grid", "wide"]
     models = {j["name"]: j["model"] for j in step.jobs}
     have_wide = "wide" in models
     jobs = []
-    for i in range(n_jobs):
+    for _ in range(n_jobs):
         k = kinds[rng.integers(0, 5 if have_wide else 4)]
         n = int(round(10 ** rng.uniform(3, 6)))
         jobs.append((k, n, int(rng.integers(0, 1 << 31))))
+    cuda = lambda t: torch.empty_like(t, device="cuda")  # noqa: E731
     prepared = []
     for k, n, sd in jobs:
         job = B.dg_job()
-        keep = []
+        rec = {"kind": k, "n": n, "seed": sd, "job": job}
         if k == "grid":
             L = int(min(30, max(2, round((n / 64) ** (1 / 3)))))
             g = W.predator_prey(levels=L, noise_seed=sd)
+            rec["model"] = models["grid"]
             job.model = models["grid"].value
             job.is_grid = 1
             pt, pos = _pinned(torch, g["pos"])
-            keep.append(pt)
             job.grid.positions = pos.ctypes.data
             job.grid.n_trials = 64
             job.grid.seed = sd
+            lts = []
             for i in range(3):
                 lt, lv = _pinned(torch, g["levels"][i])
-                keep.append(lt)
+                lts.append(lt)
                 job.grid.levels[i] = lv.ctypes.data
                 job.grid.n_levels[i] = L
             rt, res = _pinned(torch, np.zeros(3, np.float64))
-            keep += [rt, res]
             job.grid_result = res.ctypes.data
+            rec.update(host_in=[pt] + lts, host_out=[rt], dev_in=[cuda(pt)] + [cuda(t) for t in lts],
+                       dev_out=[cuda(rt)], steps=L ** 3 * 64)
         else:
             if k == "stroop":
-                s = W.stroop_small()
-                job.model = models["stroop"].value
-                ht, h = _pinned(torch, s["cond_inputs"])
+                s_ = W.stroop_small()
+                rec["model"] = models["stroop"]
+                ht, h = _pinned(torch, s_["cond_inputs"])
                 job.run.cond_inputs = h.ctypes.data
                 job.run.n_cond, job.run.cond_block = 4, max(1, n // 4)
             elif k == "wide":
                 wd = W.stroop_wide(n_trials=n)
-                job.model = models["wide"].value
+                rec["model"] = models["wide"]
                 ht, h = _pinned(torch, wd["cond_inputs"])
                 job.run.cond_inputs = h.ctypes.data
                 job.run.n_cond, job.run.cond_block = 256, 1
             elif k == "ddm":
                 w = W.ddm(n_trials=n, param_seed=sd)
-                job.model = models["ddm"].value
+                rec["model"] = models["ddm"]
                 ht, h = _pinned(torch, np.concatenate([w["A"], w["z"]]))
                 job.run.trial_params = h.ctypes.data
             else:
-                l = W.lca(n_trials=n, N=8, input_seed=sd)
-                job.model = models["lca8"].value
-                ht, h = _pinned(torch, l["I"])
+                l_ = W.lca(n_trials=n, N=8, input_seed=sd)
+                rec["model"] = models["lca8"]
+                ht, h = _pinned(torch, l_["I"])
                 job.run.trial_params = h.ctypes.data
-            keep.append(ht)
+            job.model = rec["model"].value
             job.run.n_trials = n
             job.run.seed = sd
             ct, ch = _pinned(torch, np.zeros(n, np.int8))
             st, sp = _pinned(torch, np.zeros(n, np.int32))
-            keep += [ct, st, sp]
             job.choice = ch.ctypes.data
             job.step = sp.ctypes.data
-        prepared.append((k, n, job, keep))
-    # capacity: run all jobs back to back once (also warms the allocator)
+            rec.update(host_in=[ht], host_out=[ct, st], dev_in=[cuda(ht)],
+                       dev_out=[cuda(ct), cuda(st)], cond=bool(job.run.cond_inputs),
+                       n_cond=job.run.n_cond, cond_block=job.run.cond_block)
+        prepared.append(rec)
+    return prepared
+
+
+def _plain_job(B, rec, stream):
+    """One job in the plain form: inputs copied in, one plain launch, outputs
+    copied back, on one stream; returns when the outputs are on the host."""
+    for d, h in zip(rec["dev_in"], rec["host_in"]):
+        d.copy_(h, non_blocking=True)
+    if rec["kind"] == "grid":
+        pos, l0, l1, l2 = rec["dev_in"]
+        d = B.grid_desc([l0, l1, l2], pos, rec["seed"], mode=B.DG_MODE_PLAIN)
+        B.dg_grid_search(rec["model"], d, rec["dev_out"][0], stream=stream)
+    else:
+        x = rec["dev_in"][0]
+        d = (B.run_desc(rec["n"], rec["seed"], cond_inputs=x, n_cond=rec["n_cond"],
+                        cond_block=rec["cond_block"], mode=B.DG_MODE_PLAIN) if rec["cond"] else
+             B.run_desc(rec["n"], rec["seed"], trial_params=x, mode=B.DG_MODE_PLAIN))
+        B.dg_run(rec["model"], d, rec["dev_out"][0], rec["dev_out"][1], stream=stream)
+    for h, d in zip(rec["host_out"], rec["dev_out"]):
+        h.copy_(d, non_blocking=True)
+    stream.synchronize()
+
+
+def _trial_steps(prepared):
+    return sum(r["steps"] if r["kind"] == "grid" else int(r["host_out"][1].numpy().sum())
+               for r in prepared)
+
+
+def _lat_stats(lat, wall, n_jobs, steps):
+    lat = sorted(lat)
+    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+    return {"p50_ms": 1000 * lat[len(lat) // 2], "p99_ms": 1000 * p99,
+            "max_ms": 1000 * lat[-1], "wall_s": wall, "jobs_per_s": n_jobs / wall,
+            "trial_steps_per_s": steps / wall}
+
+
+def _serve(B, ctx, prepared, arrivals):
+    """Submit each job at its arrival time (seconds from the start) through
+    dg_submit; latency = completion - submission (the library's clock)."""
     t0 = time.perf_counter()
-    for k, n, job, keep in prepared:
-        B.dg_wait(ctx, B.dg_submit(ctx, job), 600000)
-    serial = time.perf_counter() - t0
-    rate = 0.7 * n_jobs / serial
-    gaps = rng.exponential(1.0 / rate, n_jobs)
     tickets = []
-    t_start = time.perf_counter()
-    next_t = t_start
-    for (k, n, job, keep), g in zip(prepared, gaps):
-        next_t += g
-        while time.perf_counter() < next_t:
-            time.sleep(min(0.0005, max(0.0, next_t - time.perf_counter())))
-        tickets.append(B.dg_submit(ctx, job))
+    for rec, a in zip(prepared, arrivals):
+        while time.perf_counter() - t0 < a:
+            time.sleep(min(0.0005, max(0.0, a - (time.perf_counter() - t0))))
+        tickets.append(B.dg_submit(ctx, rec["job"]))
     lat = []
-    total_steps = 0
-    for (k, n, job, keep), t in zip(prepared, tickets):
+    for t in tickets:
         r = B.dg_wait(ctx, t, 600000)
         lat.append(r.t_done - r.t_submit)
-        # keep[-1] is the job's host step array
-        js = job.grid.n_levels[0] ** 3 * 64 if k == "grid" else int(keep[-1].sum())
-        if os.environ.get("DG_BENCH_DEBUG"):
-            print("served job", k, n, js, r.status, file=sys.stderr)
-        total_steps += js
-    wall = time.perf_counter() - t_start
-    lat.sort()
-    return {"jobs": n_jobs, "arrival_rate_per_s": rate, "wall_s": wall,
-            "p50_ms": 1000 * lat[len(lat) // 2], "p99_ms": 1000 * lat[min(len(lat) - 1,
-                                                                      int(math.ceil(0.99 * len(lat))) - 1)],
-            "jobs_per_s": n_jobs / wall, "trial_steps_per_s": total_steps / wall,
-            "serial_s": serial, "mix": "stroop/ddm/lca8/grid" + ("/wide" if have_wide else "")}
+    return lat, time.perf_counter() - t0
+
+
+def _plain(B, prepared, arrivals, stream):
+    """The same jobs one after another on one stream in arrival order, each
+    started at its arrival time or when the previous one ends, whichever is
+    later; latency = completion - arrival."""
+    t0 = time.perf_counter()
+    lat = []
+    for rec, a in zip(prepared, arrivals):
+        while time.perf_counter() - t0 < a:
+            time.sleep(min(0.0005, max(0.0, a - (time.perf_counter() - t0))))
+        _plain_job(B, rec, stream)
+        lat.append(time.perf_counter() - t0 - a)
+    return lat, time.perf_counter() - t0
+
+
+def served_mix(B, W, torch, ctx, step, n_jobs=SERVE_JOBS, seed=7):
+    """The served mix against the plain one-launch-per-job form on the same
+    jobs. Capacity: all jobs arriving at once (jobs/s until the last result is
+    on the host). Then Poisson arrivals at 0.7x each form's capacity, the same
+    arrival sequence (scaled) replayed through both forms: p50/p99 latency
+    (arrival to results on the host), jobs/s and trial-steps/s."""
+    prepared = _mix(B, W, torch, step, n_jobs, seed)
+    stream = torch.cuda.Stream()
+    zero = [0.0] * n_jobs
+    # warm-up: the serving pool and the plain form's per-stream scratch
+    _serve(B, ctx, prepared, zero)
+    with torch.cuda.stream(stream):
+        _plain(B, prepared, zero, stream)
+    steps = _trial_steps(prepared)
+    lat_s, wall_s = _serve(B, ctx, prepared, zero)
+    with torch.cuda.stream(stream):
+        lat_p, wall_p = _plain(B, prepared, zero, stream)
+    cap_s, cap_p = n_jobs / wall_s, n_jobs / wall_p
+    gaps = np.random.default_rng(seed + 1).exponential(1.0, n_jobs)
+    unit = np.cumsum(gaps) - gaps[0]          # unit-rate Poisson arrival times
+
+    def at(rate):
+        arr = list(unit / rate)
+        ls, ws = _serve(B, ctx, prepared, arr)
+        with torch.cuda.stream(stream):
+            lp, wp = _plain(B, prepared, arr, stream)
+        return {"arrival_rate_per_s": rate, "served": _lat_stats(ls, ws, n_jobs, steps),
+                "plain": _lat_stats(lp, wp, n_jobs, steps)}
+    at_served = at(0.7 * cap_s)
+    at_plain = at(0.7 * cap_p)
+    out = dict(at_served["served"])
+    out.update({
+        "jobs": n_jobs, "mix": "stroop/ddm/lca8/grid/wide, trials log-uniform 1e3-1e6",
+        "arrival_rate_per_s": at_served["arrival_rate_per_s"],
+        "capacity_jobs_per_s": cap_s, "capacity_trial_steps_per_s": steps / wall_s,
+        "saturated": _lat_stats(lat_s, wall_s, n_jobs, steps),
+        "plain": dict(at_served["plain"], capacity_jobs_per_s=cap_p,
+                      capacity_trial_steps_per_s=steps / wall_p,
+                      saturated=_lat_stats(lat_p, wall_p, n_jobs, steps),
+                      form="dg_run / dg_grid_search DG_MODE_PLAIN, one job after another on "
+                           "one stream, host copies included"),
+        "at_plain_capacity_rate": at_plain,
+        "trial_steps": steps})
+    return out
 
 
 if __name__ == "__main__":
