@@ -65,6 +65,7 @@ DDM_TRAFFIC_BYTES = 12_654_080
 WIDE_TRAFFIC_BYTES = None
 TRAFFIC_BYTES = {"ddm": DDM_TRAFFIC_BYTES, "wide": WIDE_TRAFFIC_BYTES}
 LANES_PER_SM = 128
+PEAK_OPS = [40.27e12]   # SMs x lanes x max SM clock, set from the device in main()
 # The pass's jobs, longest first. Graph branches are created (and served jobs
 # submitted) in this order: the wide network's CTAs take their SMs before the
 # persistent kernels fill the GPU (2-4 % shorter passes than job order).
@@ -652,6 +653,7 @@ def main():
     dominant = max(per_job, key=lambda k: per_job[k]["ms"])
     sm_max = pk.get("sm_max_mhz", 2070.0)
     peak_ops = sms * LANES_PER_SM * sm_max * 1e6
+    PEAK_OPS[0] = peak_ops
     peak_src = (f"{sms} SMs x {LANES_PER_SM} FP32/INT32 lanes x {sm_max:.0f} MHz "
                 f"({pk_kind} max SM clock)")
     by_kernel = {}
@@ -850,6 +852,24 @@ def extensions(B, W, torch, ctx, grid_ms):
                 "trial_steps_per_s": (net_steps + node_steps) / (xms / 1e3)}
         finally:
             B.dg_model_free(xm)
+        # a batch of 16 searches (the 30^3 x 64 grid, each its own positions and
+        # seed) in one launch, against the same searches one call each
+        nb = 16
+        bw = [W.predator_prey(pos_seed=3 + i, noise_seed=13 + i) for i in range(nb)]
+        bkeep = [([cuda(l) for l in w_["levels"]], cuda(w_["pos"])) for w_ in bw]
+        bdesc = [B.grid_desc(lv_, pos_, w_["seed"]) for (lv_, pos_), w_ in zip(bkeep, bw)]
+        bres = torch.zeros(nb * 3, dtype=torch.float64, device="cuda")
+        B.dg_grid_search_batch(pp, bdesc, bres)
+        ms_batch = _time_ms(torch, lambda: B.dg_grid_search_batch(pp, bdesc, bres))
+        ms_single = _time_ms(torch, lambda: [B.dg_grid_search(pp, d_, bres[3 * i:3 * i + 3])
+                                             for i, d_ in enumerate(bdesc)])
+        evals = nb * nc * 64
+        out["grid_search_batch"] = {
+            "searches": nb, "candidates_per_search": nc, "trials": 64, "ms": ms_batch,
+            "candidates_per_s": nb * nc / (ms_batch / 1e3),
+            "frac_alu": evals * OPS_PER_UNIT["grid"] / (ms_batch / 1e3) / PEAK_OPS[0],
+            "ms_one_call_each": ms_single,
+            "candidates_per_s_one_call_each": nb * nc / (ms_single / 1e3)}
         # reservoir tie-break: the 30^3 search with either rule
         res0 = torch.zeros(3, dtype=torch.float64, device="cuda")
         d0 = B.grid_desc(lv, pos, g["seed"])

@@ -236,6 +236,24 @@ dg_status dg_run(dg_model* model, const dg_run_desc* desc, int8_t* choice, int32
 dg_status dg_grid_search(dg_model* model, const dg_grid_desc* desc, dg_grid_result* result,
                          double* cand_means, void* stream);
 
+/* A batch of independent grid searches of one PREDATOR_PREY model in one
+   launch: the Control node's search (Sec. 2.1) for n_searches situations at
+   once, every evaluation of every search in parallel (Sec. 3.6). Search i is
+   exactly dg_grid_search(model, &descs[i], &results[i], cand_means[i]): the
+   same candidates, noise streams, FP64 means (bit for bit) and lowest-index
+   argmax. All searches share the grid shape (n_levels) and n_trials; each has
+   its own level values, positions and seed; whole grids only (cand_begin =
+   cand_count = 0), DG_TIE_LOWEST, DG_MODE_BATCHED.
+   descs: host array [n_searches] (device pointers inside, as for
+   dg_grid_search); results: device array [n_searches]; cand_means: NULL, or a
+   host array [n_searches] of device pointers ([L0 L1 L2] each, or NULL).
+   n_searches 1 .. 256. The first call on a stream with a given size
+   allocates scratch (not inside stream capture).
+   Errors: DG_E_ARG, DG_E_UNSUPPORTED (not a PREDATOR_PREY model), DG_E_STATE
+   (scratch must grow inside capture), DG_E_CUDA. */
+dg_status dg_grid_search_batch(dg_model* model, int32_t n_searches, const dg_grid_desc* descs,
+                               dg_grid_result* results, double* const* cand_means, void* stream);
+
 /* Time-stepped predator-prey episodes (Sec. 2.1: the whole search over
    allocations is repeated at every time step until the prey or the player is
    caught; the positions carried between steps are the sequential state of

@@ -115,6 +115,7 @@ EXPORTS = [
     "dg_batch_launch", "dg_batch_kernels", "dg_batch_free", "dg_submit", "dg_wait", "dg_serve_stats",
     "dg_grid_search_noalloc", "dg_stream_status", "dg_selftest_wait_timeout",
     "dg_argmax_f64_reservoir", "dg_grid_refine", "dg_run_episodes", "dg_selftest_pair_sum",
+    "dg_grid_search_batch",
 ]
 
 _lib = None
@@ -147,6 +148,7 @@ def _declare(L):
         "dg_run": [P, C.POINTER(dg_run_desc), P, P, P, P],
         "dg_grid_search": [P, C.POINTER(dg_grid_desc), P, P, P],
         "dg_grid_search_noalloc": [P, C.POINTER(dg_grid_desc), P, P, P],
+        "dg_grid_search_batch": [P, i32, C.POINTER(dg_grid_desc), P, P, P],
         "dg_stream_status": [P, P],
         "dg_selftest_wait_timeout": [P, i32, P],
         "dg_selftest_pair_sum": [P, i64, i32, i32, P, P],
@@ -243,6 +245,17 @@ def dg_run(model, desc, choice, step, final_state=None, stream=None):
 def dg_grid_search(model, desc, result, cand_means=None, stream=None):
     check(lib().dg_grid_search(model, C.byref(desc), ptr(result), ptr(cand_means),
                                stream_handle(stream)))
+
+
+def dg_grid_search_batch(model, descs, results, cand_means=None, stream=None):
+    """descs: list of dg_grid_desc; results: device tensor of len(descs) x 3
+    doubles; cand_means: list of device tensors (or None entries) or None."""
+    n = len(descs)
+    arr = (dg_grid_desc * n)(*descs)
+    means = None
+    if cand_means is not None:
+        means = (C.c_void_p * n)(*[None if t is None else t.data_ptr() for t in cand_means])
+    check(lib().dg_grid_search_batch(model, n, arr, ptr(results), means, stream_handle(stream)))
 
 
 def dg_grid_search_noalloc(model, desc, result, cand_means=None, stream=None):

@@ -22,7 +22,12 @@ struct LaunchCfg {
 struct PhiloxKeys {
   uint32_t k[20];
 };
-inline PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
+#ifdef __CUDACC__
+#define DG_HD __host__ __device__
+#else
+#define DG_HD
+#endif
+DG_HD inline PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
   PhiloxKeys r;
   for (int i = 0; i < 10; ++i) {
     r.k[2 * i] = k0 + (uint32_t)i * 0x9E3779B9u;
@@ -194,6 +199,32 @@ int grid_blocks(int mode, long long n_cand, int n_trials, int lanes);
 
 cudaError_t launch_argmax(const double* v, long long n, TopTwo* partials, unsigned int* ticket,
                           void* result, cudaStream_t s);
+
+// A batch of whole-grid searches of one predator-prey model in one launch: the
+// searches share the grid shape (levels per signal, trials per candidate) and
+// each has its own level values, positions, seed and outputs.
+constexpr int kMaxGridBatch = 256;
+constexpr int kGridChunk = 128;    // candidates per work item
+struct GridBatchItem {
+  const float* lv[3];
+  const float* pos;                // [n_trials][6]
+  void* result;                    // dg_grid_result*
+  double* means;                   // [n_cand] or null
+  uint32_t k0, k1;                 // Philox key of the search's seed
+};
+struct GridBatchParams {
+  int L[3];
+  int n_trials;
+  float offset, weight;
+  long long n_cand;
+  int cpc;                         // chunks per search
+  int n_search;
+  unsigned long long* cursor;      // scratch, zeroed per launch
+  unsigned int* ticket;            // scratch [n_search], zeroed per launch
+  TopTwo* partials;                // scratch [n_search][cpc]
+  GridBatchItem items[kMaxGridBatch];
+};
+cudaError_t launch_grid_batch(const GridBatchParams& p, cudaStream_t s);
 // --------------------------------------------- predator-prey episodes ---
 constexpr int kEpisodeChunk = 64;   // candidates per work item (8 warps x 8)
 struct EpisodeParams {

@@ -205,6 +205,112 @@ __global__ void __launch_bounds__(256) argmax_kernel(const double* v, long long 
   finish_argmax(best, partials, ticket, result);
 }
 
+// A batch of whole-grid searches (GridBatchParams): persistent blocks take
+// (search, chunk of kGridChunk candidates) items in order from a cursor;
+// each candidate is evaluated exactly as grid_batched does (the same lanes per
+// candidate, trial split, pair sums and FP64 mean, so its mean has the same
+// bits), the chunk's top-2 goes to the search's partials, and the block that
+// completes a search's last chunk merges them into its result. Many searches
+// per launch amortise the ramp and drain that a one-wave search pays.
+template <int LANES>
+__global__ void __launch_bounds__(256) grid_batch(GridBatchParams p) {
+  constexpr int kPerWarp = 32 / LANES;
+  __shared__ TopTwo warp_best[8];
+  __shared__ bool last;
+  __shared__ long long item;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / LANES, gl = lane % LANES;
+  const long long items = (long long)p.n_search * p.cpc;
+  const double inv = 1.0 / (double)p.n_trials;
+  for (;;) {
+    if (threadIdx.x == 0) item = (long long)atomicAdd(p.cursor, 1ull);
+    __syncthreads();
+    const long long w = item;
+    if (w >= items) break;
+    const int si = (int)(w / p.cpc);
+    const int chunk = (int)(w % p.cpc);
+    const GridBatchItem& S = p.items[si];
+    const PhiloxKeys rk = philox_keys(S.k0, S.k1);
+    const long long c0 = (long long)chunk * kGridChunk;
+    const long long c_end = min(c0 + kGridChunk, p.n_cand);
+    float kh = 0.f, kl = 0.f;
+    long long kc = -1;
+    for (int i = 0; i * 8 * kPerWarp < kGridChunk; ++i) {
+      const long long cb = c0 + (long long)i * 8 * kPerWarp + (long long)warp * kPerWarp;
+      const long long c = cb + grp;
+      float hi = 0.f, lo = 0.f;
+      if (c < c_end) {
+        const uint32_t u = (uint32_t)c, q = u / (uint32_t)p.L[2];   // c < 2^32 (checked)
+        const int l2 = (int)(u - q * (uint32_t)p.L[2]);
+        const int l1 = (int)(q % (uint32_t)p.L[1]);
+        const int l0 = (int)(q / (uint32_t)p.L[1]);
+        const float a0 = __ldg(S.lv[0] + l0), a1 = __ldg(S.lv[1] + l1), a2 = __ldg(S.lv[2] + l2);
+        const float sd0 = 1.0f / (p.offset + a0), sd1 = 1.0f / (p.offset + a1),
+                    sd2 = 1.0f / (p.offset + a2);
+        const float cost = a0 * a0 + a1 * a1 + a2 * a2;
+        for (int j = gl; j < p.n_trials; j += LANES) {
+          float X[6];
+#pragma unroll
+          for (int d = 0; d < 6; ++d) X[d] = __ldg(S.pos + 6 * j + d);
+          two_sum_add(hi, lo, pp_outcome_at(rk, (uint32_t)j, (uint32_t)c, 0u, X, sd0, sd1, sd2,
+                                            p.weight, cost));
+        }
+      }
+      group_pair_sum<LANES>(hi, lo);
+      const int g = lane - i * kPerWarp;
+      const bool mine = g >= 0 && g < kPerWarp;
+      const int src = mine ? g * LANES : 0;
+      const float th = __shfl_sync(kFull, hi, src), tl = __shfl_sync(kFull, lo, src);
+      if (mine && cb + g < c_end) {
+        kh = th;
+        kl = tl;
+        kc = cb + g;
+      }
+    }
+    TopTwo best = top_init();
+    if (kc >= 0) {
+      const double mean = pair_mean(kh, kl, inv);
+      if (S.means) S.means[kc] = mean;
+      best = TopTwo{mean, kc, -DBL_MAX};
+    }
+    best = top_warp(best);
+    if (lane == 0) warp_best[warp] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      TopTwo r = warp_best[0];
+      for (int i = 1; i < 8; ++i) r = top_merge(r, warp_best[i]);
+      p.partials[(size_t)si * p.cpc + chunk] = r;
+      __threadfence();
+      last = atomicAdd(p.ticket + si, 1u) == (unsigned)(p.cpc - 1);
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      TopTwo t = top_init();
+      for (int b = threadIdx.x; b < p.cpc; b += blockDim.x) {
+        const TopTwo* q = p.partials + (size_t)si * p.cpc + b;
+        TopTwo v;
+        v.v1 = __ldcg(&q->v1);
+        v.i1 = __ldcg(&q->i1);
+        v.v2 = __ldcg(&q->v2);
+        t = top_merge(t, v);
+      }
+      t = top_warp(t);
+      if (lane == 0) warp_best[warp] = t;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        TopTwo r = warp_best[0];
+        for (int i = 1; i < 8; ++i) r = top_merge(r, warp_best[i]);
+        GridResultDev* out = reinterpret_cast<GridResultDev*>(S.result);
+        out->best_index = r.i1;
+        out->best_value = r.v1;
+        out->gap = (r.v2 == -DBL_MAX) ? 0.0 : r.v1 - r.v2;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __device__ __forceinline__ bool reservoir_accepts(uint32_t k0, uint32_t k1, long long i,
                                                   long long k) {
   if (k == 1) return true;
@@ -559,6 +665,24 @@ cudaError_t launch_grid(const GridParams& p, int mode, const LaunchCfg& cfg, cud
     grid_batched<8><<<grid, block, smem, s>>>(p);
   else
     grid_batched<32><<<grid, block, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grid_batch(const GridBatchParams& p, cudaStream_t s) {
+  const bool narrow = grid_lanes(p.L) == 8;
+  int nb = 0;
+  cudaError_t e = narrow
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, grid_batch<8>, 256, 0)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, grid_batch<32>, 256, 0);
+  if (e != cudaSuccess) return e;
+  long long g = (long long)num_sms() * (nb > 0 ? nb : 1);
+  const long long items = (long long)p.n_search * p.cpc;
+  if (g > items) g = items;
+  if (g < 1) return cudaSuccess;
+  if (narrow)
+    grid_batch<8><<<(unsigned)g, 256, 0, s>>>(p);
+  else
+    grid_batch<32><<<(unsigned)g, 256, 0, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -73,6 +73,8 @@ struct Scratch {
   size_t perm_cap = 0;
   unsigned char* ext = nullptr;  // episodes: state, lists, tickets, partials
   size_t ext_cap = 0;
+  unsigned char* gb = nullptr;   // batched grid searches: cursor, tickets, partials
+  size_t gb_cap = 0;
   float* net = nullptr;          // wide network: hidden net input per condition
   size_t net_cap = 0;
   unsigned long long* cursor() { return reinterpret_cast<unsigned long long*>(base); }
@@ -175,6 +177,20 @@ dg_status scratch_ext(dg_ctx* ctx, Scratch* sc, size_t n, cudaStream_t s) {
   sc->ext = nullptr;
   DG_CUDA(cudaMalloc(&sc->ext, n));
   sc->ext_cap = n;
+  return DG_OK;
+}
+
+dg_status scratch_gb(dg_ctx* ctx, Scratch* sc, size_t bytes, cudaStream_t s) {
+  if (sc->gb_cap >= bytes) return DG_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    return fail(DG_E_STATE, "grid search batch: scratch must grow; run this size once before capture");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  DG_CUDA(cudaStreamSynchronize(s));
+  if (sc->gb) cudaFree(sc->gb);
+  sc->gb = nullptr;
+  DG_CUDA(cudaMalloc(&sc->gb, bytes));
+  sc->gb_cap = bytes;
   return DG_OK;
 }
 
@@ -1101,6 +1117,7 @@ dg_status compose_transfer(dg_model* m, const dg_mechanism* mechs, int n_mech,
   L.noise = (float)noise;
   L.stop_off = noff[stop->mech];
   L.stop_size = mechs[stop->mech].size;
+
   L.stop_threshold = (float)stop->threshold;
   L.max_steps = stop->max_steps;
   for (int i = 0; i < n_mech; ++i)
@@ -1232,6 +1249,7 @@ dg_status dg_destroy(dg_ctx* ctx) {
     if (kv.second.ext) cudaFree(kv.second.ext);
     if (kv.second.perm) cudaFree(kv.second.perm);
     if (kv.second.net) cudaFree(kv.second.net);
+    if (kv.second.gb) cudaFree(kv.second.gb);
   }
   delete ctx;
   return DG_OK;
@@ -1377,6 +1395,58 @@ dg_status dg_grid_search(dg_model* m, const dg_grid_desc* d, dg_grid_result* res
   if (st != DG_OK) return st;
   DG_CUDA(cudaSetDevice(m->ctx->device));
   return grid_device(m, d, result, cand_means, (cudaStream_t)stream);
+}
+
+dg_status dg_grid_search_batch(dg_model* m, int32_t n_searches, const dg_grid_desc* descs,
+                               dg_grid_result* results, double* const* cand_means, void* stream) {
+  if (!m || !descs || !results || n_searches < 1 || n_searches > dg::kMaxGridBatch)
+    return fail(DG_E_ARG, "dg_grid_search_batch: null model, descs or results, or n_searches "
+                          "outside [1, %d]", dg::kMaxGridBatch);
+  for (int i = 0; i < n_searches; ++i) {
+    const dg_grid_desc& d = descs[i];
+    dg_status st = check_grid_args(m, &d, results + i);
+    if (st != DG_OK) return st;
+    for (int e = 0; e < 3; ++e)
+      if (d.n_levels[e] != descs[0].n_levels[e])
+        return fail(DG_E_ARG, "dg_grid_search_batch: search %d has another grid shape", i);
+    if (d.n_trials != descs[0].n_trials)
+      return fail(DG_E_ARG, "dg_grid_search_batch: search %d has another trial count", i);
+    if (d.cand_begin != 0 || d.cand_count != 0 || d.tie_break != DG_TIE_LOWEST ||
+        d.mode != DG_MODE_BATCHED)
+      return fail(DG_E_ARG, "dg_grid_search_batch: search %d: whole grids, lowest-index ties "
+                            "and the batched mode only", i);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_CUDA(cudaSetDevice(m->ctx->device));
+  Scratch* sc = nullptr;
+  dg_status st = get_scratch(m->ctx, s, &sc);
+  if (st != DG_OK) return st;
+  dg::GridBatchParams p{};
+  for (int e = 0; e < 3; ++e) p.L[e] = descs[0].n_levels[e];
+  p.n_trials = descs[0].n_trials;
+  p.offset = m->offset;
+  p.weight = m->weight;
+  p.n_cand = (long long)p.L[0] * p.L[1] * p.L[2];
+  p.cpc = (int)((p.n_cand + dg::kGridChunk - 1) / dg::kGridChunk);
+  p.n_search = n_searches;
+  const size_t head = 256 + ((size_t)n_searches * sizeof(unsigned int) + 255) / 256 * 256;
+  const size_t bytes = head + (size_t)n_searches * p.cpc * sizeof(dg::TopTwo);
+  if ((st = scratch_gb(m->ctx, sc, bytes, s)) != DG_OK) return st;
+  p.cursor = reinterpret_cast<unsigned long long*>(sc->gb);
+  p.ticket = reinterpret_cast<unsigned int*>(sc->gb + 256);
+  p.partials = reinterpret_cast<dg::TopTwo*>(sc->gb + head);
+  for (int i = 0; i < n_searches; ++i) {
+    dg::GridBatchItem& it = p.items[i];
+    for (int e = 0; e < 3; ++e) it.lv[e] = descs[i].levels[e];
+    it.pos = descs[i].positions;
+    it.result = results + i;
+    it.means = cand_means ? cand_means[i] : nullptr;
+    it.k0 = (uint32_t)descs[i].seed;
+    it.k1 = (uint32_t)(descs[i].seed >> 32);
+  }
+  DG_CUDA(cudaMemsetAsync(sc->gb, 0, head, s));
+  DG_CUDA(dg::launch_grid_batch(p, s));
+  return DG_OK;
 }
 
 dg_status dg_argmax_f64(dg_ctx* ctx, const double* values, int64_t n, dg_grid_result* result,
