@@ -101,9 +101,13 @@ typedef struct {
 typedef struct {
   int32_t sender;        /* index into the mechanism array */
   int32_t receiver;
-  const float* weights;  /* host, FP32 [receiver size][sender size] row-major; copied at compose */
+  const float* weights;  /* host, FP32 [receiver size][sender size] row-major; copied at compose.
+                            NULL with lo < hi: drawn from the compose call's weight_seed, see
+                            dg_compose; NULL with lo = hi = 0: the graph's structural edge
+                            (identity, predator-prey chain) */
   int32_t dtype;         /* DG_F32 or DG_BF16 */
   int32_t reserved;
+  double lo, hi;         /* range of seeded weights (weights NULL) */
 } dg_projection;
 
 typedef struct {
@@ -189,13 +193,26 @@ const char* dg_version(void);
                  DG_BF16 hidden->response projection) runs on the tensor-core kernel.
      - PREDATOR_PREY: DG_INPUT(6) -> DG_PP_OBSERVE(6) -> DG_PP_ACTION(2) ->
                  DG_PP_OBJECTIVE(1), chained by projections with NULL weights.
+   Static read-only parameters (Sec. 3.3): a projection with NULL weights and
+   lo < hi gets weights drawn from weight_seed: weight w (row-major index)
+   of projection p (its index in projs) is lo + (hi - lo) u, formed in FP64
+   and rounded to FP32, u = ((x >> 9) + 1/2) 2^-23 with x word (w & 3) of
+   Philox4x32-10(key = (weight_seed lo, weight_seed hi), counter = (p, 0,
+   w >> 2, 2)) (purpose 2 keeps these draws apart from all noise).
    Weights are copied to the device (synchronously) before return.
    Errors: DG_E_ARG (null/invalid values), DG_E_SHAPE (graph not valid),
    DG_E_UNSUPPORTED (valid but outside the kernels' limits), DG_E_CUDA. */
 dg_status dg_compose(dg_ctx* ctx, const dg_mechanism* mechs, int32_t n_mech,
                      const dg_projection* projs, int32_t n_proj, const dg_stop* stop,
-                     dg_model** out);
+                     uint64_t weight_seed, dg_model** out);
 dg_status dg_model_free(dg_model* model);
+
+/* The FP32 weights a model was composed with for projection `proj` (its index
+   in the compose call's projs): the given ones, or those drawn from the seed
+   (before any BF16 rounding of the device copy). out: host, n floats, n =
+   receiver size x sender size (0 for a structural edge).
+   Errors: DG_E_ARG (proj out of range, n not the projection's size). */
+dg_status dg_model_weights(const dg_model* model, int32_t proj, float* out, int64_t n);
 
 /* Model kind (0 DDM, 1 LCA, 2 TRANSFER small, 3 TRANSFER wide, 4 PREDATOR_PREY)
    and the number of floats dg_run writes per trial into final_state. */

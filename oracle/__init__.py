@@ -83,6 +83,7 @@ def _bind(L):
                                   C.c_int64, P]
     L.or_uniform.argtypes = [C.c_uint32]
     L.or_uniform.restype = C.c_double
+    L.or_weights.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_double, C.c_double, P]
     L.or_box_muller.argtypes = [P, P]
     L.or_normals.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_int64, P]
     L.or_ddm_run.argtypes = [P, P, P, C.c_int64, C.c_uint64, C.c_double, C.c_double, C.c_double,
@@ -160,6 +161,13 @@ def philox_words(seed, trial, cand, purpose, block0, nblocks):
 
 def uniform(w):
     return lib().or_uniform(int(w))
+
+
+def weights(seed, proj, n, lo, hi):
+    """Seeded weights of projection `proj`: n float32 values in [lo, hi]."""
+    out = np.zeros(n, np.float32)
+    lib().or_weights(seed, proj, n, lo, hi, _p(out))
+    return out
 
 
 def box_muller(words):

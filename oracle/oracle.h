@@ -54,6 +54,7 @@ void or_philox_words(uint64_t seed, uint32_t trial, uint32_t cand, uint32_t purp
 
 /* u = ((w >> 9) + 1/2) * 2^-23, in (0, 1); exact in binary32. */
 double or_uniform(uint32_t w);
+void or_weights(uint64_t seed, uint32_t proj, int64_t n, double lo, double hi, float* out);
 
 /* Box-Muller on (w0,w1) and (w2,w3): z[0..3]. */
 void or_box_muller(const uint32_t w[4], double z[4]);

@@ -88,3 +88,16 @@ void or_normals(uint64_t seed, uint32_t trial, uint32_t cand, uint64_t d0, int64
     out[k] = z[d & 3];
   }
 }
+
+/* Static weights drawn from a seed (Sec. 3.3's read-only parameters): weight w
+   of projection `proj` is lo + (hi - lo) u in FP64, rounded to binary32, where
+   u is the uniform of word (w mod 4) of the Philox block with counter
+   (proj, 0, w div 4, purpose 2). */
+void or_weights(uint64_t seed, uint32_t proj, int64_t n, double lo, double hi, float* out) {
+  uint32_t w[4];
+  for (int64_t i = 0; i < n; ++i) {
+    if ((i & 3) == 0) or_philox_words(seed, proj, 0u, 2u, (uint32_t)(i >> 2), 1, w);
+    const double u = or_uniform(w[i & 3]);
+    out[i] = (float)(lo + (hi - lo) * u);
+  }
+}

@@ -45,7 +45,8 @@ class dg_mechanism(C.Structure):
 
 class dg_projection(C.Structure):
     _fields_ = [("sender", C.c_int32), ("receiver", C.c_int32), ("weights", C.c_void_p),
-                ("dtype", C.c_int32), ("reserved", C.c_int32)]
+                ("dtype", C.c_int32), ("reserved", C.c_int32), ("lo", C.c_double),
+                ("hi", C.c_double)]
 
 
 class dg_stop(C.Structure):
@@ -115,7 +116,7 @@ EXPORTS = [
     "dg_batch_launch", "dg_batch_kernels", "dg_batch_free", "dg_submit", "dg_wait", "dg_serve_stats",
     "dg_grid_search_noalloc", "dg_stream_status", "dg_selftest_wait_timeout",
     "dg_argmax_f64_reservoir", "dg_grid_refine", "dg_run_episodes", "dg_selftest_pair_sum",
-    "dg_grid_search_batch",
+    "dg_grid_search_batch", "dg_model_weights",
 ]
 
 _lib = None
@@ -142,7 +143,8 @@ def _declare(L):
         "dg_create": [C.POINTER(P), S, C.c_size_t],
         "dg_destroy": [P],
         "dg_compose": [P, C.POINTER(dg_mechanism), i32, C.POINTER(dg_projection), i32,
-                       C.POINTER(dg_stop), C.POINTER(P)],
+                       C.POINTER(dg_stop), u64, C.POINTER(P)],
+        "dg_model_weights": [P, i32, P, i64],
         "dg_model_free": [P],
         "dg_model_info": [P, C.POINTER(i32), C.POINTER(i32)],
         "dg_run": [P, C.POINTER(dg_run_desc), P, P, P, P],
@@ -219,12 +221,21 @@ def dg_last_error():
     return lib().dg_last_error().decode()
 
 
-def dg_compose(ctx, mechs, projs, stop):
+def dg_compose(ctx, mechs, projs, stop, weight_seed=0):
     m = (dg_mechanism * len(mechs))(*mechs)
     p = (dg_projection * max(1, len(projs)))(*projs) if projs else None
     out = C.c_void_p()
-    check(lib().dg_compose(ctx, m, len(mechs), p, len(projs), C.byref(stop), C.byref(out)))
+    check(lib().dg_compose(ctx, m, len(mechs), p, len(projs), C.byref(stop), weight_seed,
+                           C.byref(out)))
     return out
+
+
+def dg_model_weights(model, proj_index, n):
+    """The FP32 weights the model holds for projection proj_index (n floats)."""
+    import numpy as np
+    out = np.zeros(max(n, 1), np.float32)
+    check(lib().dg_model_weights(model, proj_index, out.ctypes.data_as(C.c_void_p), n))
+    return out[:n]
 
 
 def dg_model_free(model):
@@ -413,13 +424,16 @@ def mech(kind, size, **kw):
     return m
 
 
-def proj(sender, receiver, weights=None, dtype=DG_F32):
-    """weights: numpy float32 [recv][send] (kept alive by the caller until compose returns)."""
+def proj(sender, receiver, weights=None, dtype=DG_F32, lo=0.0, hi=0.0):
+    """weights: numpy float32 [recv][send] (kept alive by the caller until compose
+    returns), or None with lo < hi for weights drawn from the compose seed."""
     p = dg_projection()
     p.sender = sender
     p.receiver = receiver
     p.weights = None if weights is None else weights.ctypes.data
     p.dtype = dtype
+    p.lo = lo
+    p.hi = hi
     return p
 
 
@@ -444,8 +458,9 @@ def compose_lca(ctx, N, leak=0.2, inhibition=0.3, sigma=0.1, dt=0.01, threshold=
 
 
 def compose_network(ctx, layers, projections, rate=0.1, noise_sd=0.01, stop_layer=None,
-                    stop_threshold=0.7, max_steps=500, bf16_edges=()):
-    """layers: dicts (size, input, gain, bias); projections: (sender, receiver, W[recv][send])."""
+                    stop_threshold=0.7, max_steps=500, bf16_edges=(), weight_seed=0):
+    """layers: dicts (size, input, gain, bias); projections: (sender, receiver, W), W a
+    [recv][send] array, or a (lo, hi) pair for weights drawn from weight_seed."""
     import numpy as np
     ms = []
     for l in layers:
@@ -454,12 +469,17 @@ def compose_network(ctx, layers, projections, rate=0.1, noise_sd=0.01, stop_laye
         else:
             ms.append(mech(DG_TRANSFER_LOGISTIC, int(l["size"]), gain=float(l.get("gain", 1.0)),
                            bias=float(l.get("bias", 0.0)), rate=rate, noise=noise_sd))
-    keep = [np.ascontiguousarray(W, dtype=np.float32) for (_, _, W) in projections]
-    ps = [proj(s, r, keep[i], DG_BF16 if i in bf16_edges else DG_F32)
-          for i, (s, r, _) in enumerate(projections)]
+    ps, keep = [], []
+    for i, (s, r, W) in enumerate(projections):
+        dt = DG_BF16 if i in bf16_edges else DG_F32
+        if isinstance(W, tuple):
+            ps.append(proj(s, r, None, dt, lo=float(W[0]), hi=float(W[1])))
+        else:
+            keep.append(np.ascontiguousarray(W, dtype=np.float32))
+            ps.append(proj(s, r, keep[-1], dt))
     if stop_layer is None:
         stop_layer = len(layers) - 1
-    model = dg_compose(ctx, ms, ps, stop(stop_layer, max_steps, stop_threshold))
+    model = dg_compose(ctx, ms, ps, stop(stop_layer, max_steps, stop_threshold), weight_seed)
     del keep
     return model
 

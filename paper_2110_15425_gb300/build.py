@@ -19,6 +19,7 @@ LIB = os.path.join(OUT_DIR, "libdistill_gpu.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
+              "-Xcompiler", "-ffp-contract=off",
               "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
 
 

@@ -20,7 +20,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // One Philox4x32-10 block. Each round multiplies words 0 and 2 by the two
 // round multipliers, then mixes the high halves with words 1 and 3 and the
 // key; the key advances by the two Weyl increments between rounds.
-__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+__host__ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     // one 32x32 -> 64-bit multiply gives both halves of each product

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "distill_gpu.h"
+#include "dg_device.cuh"
 #include "dg_internal.h"
 
 // ----------------------------------------------------------------- errors ---
@@ -127,6 +128,7 @@ struct dg_model {
   double offset_d = 0.0, weight_d = 0.0;  // as given, for the FP64 episode moves
   int state_size = 0;
   int n_inputs = 0;  // TRANSFER: input units per condition row
+  std::vector<std::vector<float>> proj_w;  // FP32 weights of each projection (empty: structural)
 };
 
 namespace {
@@ -1260,10 +1262,41 @@ dg_status dg_destroy(dg_ctx* ctx) {
 }
 
 dg_status dg_compose(dg_ctx* ctx, const dg_mechanism* mechs, int32_t n_mech,
-                     const dg_projection* projs, int32_t n_proj, const dg_stop* stop,
-                     dg_model** out) {
-  if (!ctx || !mechs || !stop || !out || n_mech < 1 || n_proj < 0 || (n_proj > 0 && !projs))
+                     const dg_projection* projs_in, int32_t n_proj, const dg_stop* stop,
+                     uint64_t weight_seed, dg_model** out) {
+  if (!ctx || !mechs || !stop || !out || n_mech < 1 || n_proj < 0 || (n_proj > 0 && !projs_in))
     return fail(DG_E_ARG, "dg_compose: null or empty arguments");
+  // seeded weights: projection p, weight w: lo + (hi - lo) u in FP64, rounded
+  // to FP32, u from word w & 3 of Philox(counter (p, 0, w >> 2, 2)) (Sec. 3.3
+  // static parameters, drawn apart from all noise)
+  std::vector<dg_projection> pj(projs_in, projs_in + n_proj);
+  std::vector<std::vector<float>> pw(n_proj);
+  for (int p = 0; p < n_proj; ++p) {
+    dg_projection& q = pj[p];
+    if (q.sender < 0 || q.sender >= n_mech || q.receiver < 0 || q.receiver >= n_mech)
+      return fail(DG_E_SHAPE, "dg_compose: projection %d names a mechanism out of range", p);
+    const size_t n = (size_t)mechs[q.receiver].size * (size_t)mechs[q.sender].size;
+    if (!q.weights && (q.lo != 0.0 || q.hi != 0.0)) {
+      if (!(q.lo < q.hi) || !std::isfinite(q.lo) || !std::isfinite(q.hi))
+        return fail(DG_E_ARG, "dg_compose: projection %d: seeded weights need finite lo < hi", p);
+      const uint32_t k0 = (uint32_t)weight_seed, k1 = (uint32_t)(weight_seed >> 32);
+      pw[p].resize(n);
+      for (size_t w = 0; w < n; w += 4) {
+        const uint4 x = dg::philox(make_uint4((uint32_t)p, 0u, (uint32_t)(w >> 2), 2u), k0, k1);
+        const uint32_t word[4] = {x.x, x.y, x.z, x.w};
+        for (size_t i = 0; i < 4 && w + i < n; ++i) {
+          const double u = ((double)(word[i] >> 9) + 0.5) * 0x1p-23;
+          const double span = q.hi - q.lo;
+          const double scaled = span * u;    // host code is built without contraction
+          pw[p][w + i] = (float)(q.lo + scaled);
+        }
+      }
+      q.weights = pw[p].data();
+    } else if (q.weights) {
+      pw[p].assign(q.weights, q.weights + n);
+    }
+  }
+  const dg_projection* projs = n_proj ? pj.data() : nullptr;
   if (stop->max_steps < 1) return fail(DG_E_ARG, "dg_compose: stop.max_steps must be >= 1");
   for (int i = 0; i < n_mech; ++i) {
     if (mechs[i].kind < DG_INPUT || mechs[i].kind > DG_PP_OBJECTIVE)
@@ -1273,6 +1306,7 @@ dg_status dg_compose(dg_ctx* ctx, const dg_mechanism* mechs, int32_t n_mech,
   DG_CUDA(cudaSetDevice(ctx->device));
   std::unique_ptr<dg_model> m(new dg_model);
   m->ctx = ctx;
+  m->proj_w = std::move(pw);
   int counts[7] = {0};
   for (int i = 0; i < n_mech; ++i) counts[mechs[i].kind]++;
   const int integrators = counts[DG_DDM] + counts[DG_LCA];
@@ -1375,6 +1409,18 @@ dg_status dg_model_free(dg_model* m) {
   cudaFree(m->d_w_resp_bf16);
   cudaFree(m->d_w_resp_f32);
   delete m;
+  return DG_OK;
+}
+
+dg_status dg_model_weights(const dg_model* m, int32_t proj, float* out, int64_t n) {
+  if (!m || proj < 0 || proj >= (int32_t)m->proj_w.size())
+    return fail(DG_E_ARG, "dg_model_weights: projection out of range");
+  const auto& w = m->proj_w[proj];
+  if (n != (int64_t)w.size())
+    return fail(DG_E_ARG, "dg_model_weights: projection %d holds %lld weights, not %lld", proj,
+                (long long)w.size(), (long long)n);
+  if (n > 0 && !out) return fail(DG_E_ARG, "dg_model_weights: null output");
+  if (n > 0) memcpy(out, w.data(), (size_t)n * sizeof(float));
   return DG_OK;
 }
 

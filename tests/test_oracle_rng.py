@@ -141,3 +141,27 @@ def test_normals_stream_indexing(orc):
         assert np.array_equal(z[4 * b:4 * b + 4], ref)
     z2 = orc.normals(9, 4, 0, 5, 4)
     assert np.array_equal(z2, z[5:9])
+
+
+def test_seeded_weights(orc):
+    """Seeded static weights (Sec. 3.3): in [lo, hi]; uniform in distribution
+    (mean, variance and a chi-square over 16 bins on 65,536 draws); distinct
+    per projection and per seed; and drawn from a counter purpose of their own,
+    apart from the noise streams of the same (trial, cand) counter."""
+    n = 65536
+    lo, hi = -2.5, 2.5
+    w = orc.weights(7, 3, n, lo, hi).astype(np.float64)
+    assert w.min() >= lo and w.max() <= hi
+    assert abs(w.mean() - (lo + hi) / 2) < 4 * (hi - lo) / np.sqrt(12 * n)
+    assert abs(w.var() / ((hi - lo) ** 2 / 12) - 1.0) < 0.02
+    counts = np.histogram(w, bins=16, range=(lo, hi))[0]
+    chi2 = ((counts - n / 16) ** 2 / (n / 16)).sum()
+    assert chi2 < 40.0   # 15 degrees of freedom: p < 1e-3
+    assert not np.array_equal(orc.weights(7, 4, 64, lo, hi), orc.weights(7, 3, 64, lo, hi))
+    assert not np.array_equal(orc.weights(8, 3, 64, lo, hi), orc.weights(7, 3, 64, lo, hi))
+    # a unit range gives the generator's uniforms; purpose 2 differs from the
+    # noise purpose 0 on the same counter words
+    u = orc.weights(7, 3, 8, 0.0, 1.0)
+    noise_words = orc.philox_words(7, 3, 0, 0, 0, 2)
+    assert not np.array_equal(u, np.float32([orc.uniform(x) for x in noise_words]))
+    assert np.all((u > 0) & (u < 1))
