@@ -60,9 +60,12 @@ OPS_PER_UNIT = {"ddm": 32, "lca4": 4 * 31, "lca8": 8 * 31, "lca16": 16 * 31, "st
 # kernel: 12,653,824 read + 256 written (the 5 MB of outputs stay in L2 within
 # the launch). Algorithmic: 8 B of parameters in and 5 B out per trial = 13.6 MB.
 DDM_TRAFFIC_BYTES = 12_654_080
-# DRAM bytes of one wide_block_kernel launch over the 16,384-trial job: not yet
-# captured on the current kernel (None until an ncu capture of it is taken).
-WIDE_TRAFFIC_BYTES = None
+# DRAM bytes of one wide_block_kernel launch over the 16,384-trial job, from
+# `ncu --set full --clock-control none -k regex:wide_block -s 1 -c 1 python bench.py --only wide`
+# on the current kernel: 320 read + 0 written (the weights, the per-condition table and the
+# outputs stay in L2). Algorithmic: the weights (16 KB BF16 operand image, 32 KB hidden
+# weights), the 256 condition rows and 5 B of outputs per trial: 0.16 MB.
+WIDE_TRAFFIC_BYTES = 320
 TRAFFIC_BYTES = {"ddm": DDM_TRAFFIC_BYTES, "wide": WIDE_TRAFFIC_BYTES}
 LANES_PER_SM = 128
 PEAK_OPS = [40.27e12]   # SMs x lanes x max SM clock, set from the device in main()
@@ -92,7 +95,7 @@ def parse():
                     help="run warmup + 1 step only (for ncu launch lists)")
     ap.add_argument("--only", default=None,
                     choices=["ddm", "lca4", "lca8", "lca16", "grid", "stroop", "wide", "refine",
-                             "episodes"],
+                             "episodes", "grid_batch"],
                     help="one job of this kind, default launch shape, 1 warm + 1 timed launch "
                          "(the small case for per-kernel ncu captures)")
     ap.add_argument("--n", type=int, default=0, help="trials (or candidates) for --only")
@@ -485,6 +488,14 @@ def run_only(args):
         pos = cuda(g["pos"])
         res = torch.zeros(3, dtype=torch.float64, device="cuda")
         go = lambda: B.dg_grid_search(m, B.grid_desc(lv, pos, g["seed"]), res)  # noqa: E731
+    elif k == "grid_batch":
+        nb = args.n or 16   # searches of the 30^3 x 64 grid, each its own positions and seed
+        bw = [W.predator_prey(pos_seed=3 + i, noise_seed=13 + i) for i in range(nb)]
+        m = B.compose_predator_prey(ctx)
+        bkeep = [([cuda(l) for l in w_["levels"]], cuda(w_["pos"])) for w_ in bw]
+        bdesc = [B.grid_desc(lv_, pos_, w_["seed"]) for (lv_, pos_), w_ in zip(bkeep, bw)]
+        res = torch.zeros(nb * 3, dtype=torch.float64, device="cuda")
+        go = lambda: B.dg_grid_search_batch(m, bdesc, res)  # noqa: E731
     elif k == "episodes":
         w = W.predator_prey_episodes(n_episodes=args.n or 64)
         m = B.compose_predator_prey(ctx)
@@ -536,7 +547,7 @@ def run_only(args):
     e1.record()
     torch.cuda.synchronize()
     out = {"only": k, "n": args.n, "ms": e0.elapsed_time(e1)}
-    if k not in ("grid", "refine", "episodes"):
+    if k not in ("grid", "refine", "episodes", "grid_batch"):
         out["trial_steps"] = int(st.to(torch.int64).sum().item())
     print(json.dumps(out))
     B.dg_model_free(m)
