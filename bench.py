@@ -95,7 +95,7 @@ def parse():
                     help="run warmup + 1 step only (for ncu launch lists)")
     ap.add_argument("--only", default=None,
                     choices=["ddm", "lca4", "lca8", "lca16", "grid", "stroop", "wide", "refine",
-                             "episodes", "grid_batch"],
+                             "episodes", "grid_batch", "small_jobs"],
                     help="one job of this kind, default launch shape, 1 warm + 1 timed launch "
                          "(the small case for per-kernel ncu captures)")
     ap.add_argument("--n", type=int, default=0, help="trials (or candidates) for --only")
@@ -480,6 +480,21 @@ def run_only(args):
     ctx = B.dg_create(0)
     cuda = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
     k = args.only
+    if k == "small_jobs":   # the many-small-jobs serving measurement alone
+        w, l8 = W.ddm(n_trials=1), W.lca(n_trials=1, N=8)
+        models = [dict(name="ddm", model=B.compose_ddm(ctx, dt=w["dt"], sigma=w["sigma"],
+                                                       max_steps=w["max_steps"])),
+                  dict(name="lca8", model=B.compose_lca(
+                      ctx, 8, leak=l8["leak"], inhibition=l8["inhibition"], sigma=l8["sigma"],
+                      dt=l8["dt"], threshold=l8["threshold"], max_steps=l8["max_steps"]))]
+
+        class _Models:
+            jobs = models
+        print(json.dumps(served_small_jobs(B, W, torch, ctx, _Models, n_jobs=args.n or SERVE_JOBS)))
+        for j in models:
+            B.dg_model_free(j["model"])
+        B.dg_destroy(ctx)
+        return
     if k == "grid":
         L = max(2, round(args.n ** (1 / 3))) if args.n else 30
         g = W.predator_prey(levels=L)
@@ -694,6 +709,7 @@ def main():
         e2e = e2e_serving(B, torch, ctx, step, all_ts, world, rank)
         if world == 1:
             serving = served_mix(B, W, torch, ctx, step)
+            serving["small_jobs"] = served_small_jobs(B, W, torch, ctx, step)
 
     gpu_launches = step.kernels_per_step() * K
     clocks = clk.summary()
@@ -970,20 +986,20 @@ def e2e_serving(B, torch, ctx, step, all_ts, world, rank):
 SERVE_JOBS = 256
 
 
-def _mix(B, W, torch, step, n_jobs, seed):
+def _mix(B, W, torch, step, n_jobs, seed, kinds=("stroop", "ddm", "lca", "grid", "wide"),
+         log_trials=(3, 6)):
     """The served mix: jobs drawn uniformly from the five workloads, trial
     counts log-uniform in [1e3, 1e6] (grid jobs: levels per signal
     clamp(round((n / 64)^(1/3)), 2, 30) at 64 trials per candidate). Each job
     carries its pinned host buffers, a dg_job for the serving API and the device
     buffers of the plain form."""
     rng = np.random.default_rng(seed)
-    kinds = ["stroop", "ddm", "lca", "grid", "wide"]
     models = {j["name"]: j["model"] for j in step.jobs}
-    have_wide = "wide" in models
+    kinds = [k for k in kinds if k != "wide" or "wide" in models]
     jobs = []
     for _ in range(n_jobs):
-        k = kinds[rng.integers(0, 5 if have_wide else 4)]
-        n = int(round(10 ** rng.uniform(3, 6)))
+        k = kinds[rng.integers(0, len(kinds))]
+        n = int(round(10 ** rng.uniform(*log_trials)))
         jobs.append((k, n, int(rng.integers(0, 1 << 31))))
     cuda = lambda t: torch.empty_like(t, device="cuda")  # noqa: E731
     prepared = []
@@ -1108,6 +1124,43 @@ def _plain(B, prepared, arrivals, stream):
         _plain_job(B, rec, stream)
         lat.append(time.perf_counter() - t0 - a)
     return lat, time.perf_counter() - t0
+
+
+def served_small_jobs(B, W, torch, ctx, step, n_jobs=SERVE_JOBS, seed=17):
+    """Many small jobs: DDM and LCA (N = 8) jobs of 1e3-1e4 trials, all arriving at
+    once, through the serving API and through the plain form: jobs/s,
+    trial-steps/s and latency."""
+    prepared = _mix(B, W, torch, step, n_jobs, seed, kinds=("ddm", "lca"), log_trials=(3, 4))
+    stream = torch.cuda.Stream()
+    zero = [0.0] * n_jobs
+    # a second context whose serving loop gives every job its own launch
+    os.environ["DG_SERVE_GROUP_TRIALS"] = "0"
+    try:
+        ctx_each = B.dg_create(0)
+        _serve(B, ctx_each, prepared, zero)
+    finally:
+        del os.environ["DG_SERVE_GROUP_TRIALS"]
+    _serve(B, ctx, prepared, zero)
+    with torch.cuda.stream(stream):
+        _plain(B, prepared, zero, stream)
+    steps = _trial_steps(prepared)
+    res = {}
+    for r in range(3):   # best of three per form, the forms interleaved
+        for name, fn in (("served", lambda: _serve(B, ctx, prepared, zero)),
+                         ("served_per_job", lambda: _serve(B, ctx_each, prepared, zero))):
+            lat, wall = fn()
+            if name not in res or wall < res[name][1]:
+                res[name] = (lat, wall)
+    with torch.cuda.stream(stream):
+        lat_p, wall_p = _plain(B, prepared, zero, stream)
+    B.dg_destroy(ctx_each)
+    return {"jobs": n_jobs, "mix": "ddm/lca8, trials log-uniform 1e3-1e4, all at once",
+            "trial_steps": steps,
+            "served": dict(_lat_stats(*res["served"], n_jobs, steps),
+                           form="serving loop, small jobs of one model share a launch"),
+            "served_per_job": dict(_lat_stats(*res["served_per_job"], n_jobs, steps),
+                                   form="serving loop, a launch and a stream per job"),
+            "plain": _lat_stats(lat_p, wall_p, n_jobs, steps)}
 
 
 def served_mix(B, W, torch, ctx, step, n_jobs=SERVE_JOBS, seed=7):

@@ -237,6 +237,21 @@ dg_status dg_model_info(const dg_model* model, int32_t* kind, int32_t* state_siz
 dg_status dg_run(dg_model* model, const dg_run_desc* desc, int8_t* choice, int32_t* step,
                  float* final_state, void* stream);
 
+/* Several jobs of one DDM or LCA model in one persistent launch: Sec. 3.6's
+   parallel evaluations taken across jobs as well as within one, so that jobs
+   too small to fill the GPU share its lanes and the launch's ramp and drain.
+   Job i is exactly dg_run(model, &descs[i], choice[i], step[i],
+   final_state ? final_state[i] : NULL): the same trials, random streams and
+   results, bit for bit. Each desc is checked as dg_run checks it and must use
+   DG_MODE_BATCHED; jobs may differ in n_trials (0 allowed), trial_offset, seed
+   and trial_params. choice, step (and final_state when not NULL) are host
+   arrays of n_jobs device pointers; an entry of final_state may be NULL.
+   n_jobs: 1 .. 64; at most 2^31 - 1 trials in all.
+   Errors: DG_E_ARG, DG_E_UNSUPPORTED (not a DDM or LCA model), DG_E_CUDA. */
+dg_status dg_run_jobs(dg_model* model, int32_t n_jobs, const dg_run_desc* descs,
+                      int8_t* const* choice, int32_t* const* step, float* const* final_state,
+                      void* stream);
+
 /* Predator-prey grid search (Sec. 2.1, 3.6): simulate every candidate
    allocation over desc->n_trials noisy trials, average the outcomes in FP64,
    and take the argmax. Exact ties of the best mean go to the lowest index, or
@@ -494,8 +509,12 @@ typedef struct {
 
 /* Queue a job; returns at once with a ticket. The serving loop admits queued
    jobs in arrival order while the HBM budget has room, runs admitted jobs
-   concurrently (each on its own stream, continuous batching), and frees a
-   job's memory when its results are on the host.
+   concurrently (each launch on its own stream, continuous batching), and frees
+   a job's memory when its results are on the host. A batched DDM or LCA job of
+   at most 65,536 trials (environment DG_SERVE_GROUP_TRIALS; 0 turns this off)
+   takes later queued batched DDM or LCA jobs of the same model, up to that size
+   each, 64 jobs and 2^22 trials in all, into one dg_run_jobs launch; results
+   are those of the jobs run alone.
    Errors: DG_E_ARG; DG_E_BUDGET if the job alone exceeds the budget. */
 dg_status dg_submit(dg_ctx* ctx, const dg_job* job, uint64_t* ticket);
 

@@ -116,7 +116,7 @@ EXPORTS = [
     "dg_batch_launch", "dg_batch_kernels", "dg_batch_free", "dg_submit", "dg_wait", "dg_serve_stats",
     "dg_grid_search_noalloc", "dg_stream_status", "dg_selftest_wait_timeout",
     "dg_argmax_f64_reservoir", "dg_grid_refine", "dg_run_episodes", "dg_selftest_pair_sum",
-    "dg_grid_search_batch", "dg_model_weights",
+    "dg_grid_search_batch", "dg_model_weights", "dg_run_jobs",
 ]
 
 _lib = None
@@ -151,6 +151,7 @@ def _declare(L):
         "dg_grid_search": [P, C.POINTER(dg_grid_desc), P, P, P],
         "dg_grid_search_noalloc": [P, C.POINTER(dg_grid_desc), P, P, P],
         "dg_grid_search_batch": [P, i32, C.POINTER(dg_grid_desc), P, P, P],
+        "dg_run_jobs": [P, i32, C.POINTER(dg_run_desc), P, P, P, P],
         "dg_stream_status": [P, P],
         "dg_selftest_wait_timeout": [P, i32, P],
         "dg_selftest_pair_sum": [P, i64, i32, i32, P, P],
@@ -251,6 +252,20 @@ def dg_model_info(model):
 def dg_run(model, desc, choice, step, final_state=None, stream=None):
     check(lib().dg_run(model, C.byref(desc), ptr(choice), ptr(step), ptr(final_state),
                        stream_handle(stream)))
+
+
+def dg_run_jobs(model, descs, choices, steps, final_states=None, stream=None):
+    """descs: list of dg_run_desc (device trial_params); choices, steps: lists
+    of device tensors; final_states: list of device tensors (or None entries)
+    or None."""
+    n = len(descs)
+    arr = (dg_run_desc * n)(*descs)
+    ch = (C.c_void_p * n)(*[t.data_ptr() for t in choices])
+    st = (C.c_void_p * n)(*[t.data_ptr() for t in steps])
+    fs = None
+    if final_states is not None:
+        fs = (C.c_void_p * n)(*[None if t is None else t.data_ptr() for t in final_states])
+    check(lib().dg_run_jobs(model, n, arr, ch, st, fs, stream_handle(stream)))
 
 
 def dg_grid_search(model, desc, result, cand_means=None, stream=None):

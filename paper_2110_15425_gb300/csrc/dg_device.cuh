@@ -13,6 +13,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "dg_internal.h"
+
 namespace dg {
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -46,6 +48,18 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const Keys& rk) {
   }
   return c;
 }
+
+// Round keys formed where they are used from the key pair (one add each),
+// for code that holds a different key in each lane and has no registers to
+// spare for the twenty round keys; same keys, same blocks as dg::PhiloxKeys.
+struct KeyPair {
+  struct Rounds {
+    uint32_t k0, k1;
+    __device__ __forceinline__ uint32_t operator[](int i) const {
+      return (i & 1) ? k1 + (uint32_t)(i >> 1) * 0xBB67AE85u : k0 + (uint32_t)(i >> 1) * 0x9E3779B9u;
+    }
+  } k;
+};
 
 template <typename Keys>
 __device__ __forceinline__ uint4 noise_block_rk(const Keys& rk, uint32_t trial, uint32_t cand,
@@ -161,6 +175,29 @@ __device__ __forceinline__ long long fetch_trial(unsigned long long* cursor, boo
   base = __shfl_sync(kFull, base, leader);
   if (!need) return -1;
   return (long long)(base + (unsigned long long)__popc(mask & ((1u << lane) - 1u)));
+}
+
+// Multi-job launches: copy the job table from the kernel parameter into
+// shared memory (one barrier), and find the job holding entry f of the
+// concatenated trial list (the last job whose start is at most f; starts
+// ascend from 0).
+__device__ __forceinline__ void copy_jobs(const MultiJobTable& tab, MultiJob* s_job) {
+  static_assert(sizeof(MultiJob) % 8 == 0, "job records copy as 8-byte words");
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(tab.jobs);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(s_job);
+  const int words = tab.n_jobs * (int)(sizeof(MultiJob) / 8);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
+__device__ __forceinline__ int multi_job_of(const MultiJob* s_job, int n_jobs, long long f) {
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (s_job[mid].start <= f) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
 }
 
 // y = 1 / (1 + exp(-gain (s + bias))) = 1 / (1 + 2^(c1 s + c0)) with

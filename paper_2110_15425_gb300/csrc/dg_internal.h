@@ -36,6 +36,28 @@ DG_HD inline PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
   return r;
 }
 
+// One job of a multi-job launch (DDM or LCA): the launch's trial list is the
+// concatenation of its jobs' trials, job j holding list entries
+// start .. start + n - 1; each job has its own inputs, outputs, seed and
+// trial offset (the model's parameters are the launch's).
+constexpr int kMaxMultiJobs = 64;
+struct MultiJob {
+  long long start;
+  long long n;
+  const float* in;               // DDM: [2][n] (A row, z row); LCA: [n][N]
+  int8_t* choice;
+  int32_t* step;
+  float* xout;                   // may be null
+  uint32_t trial0;
+  uint32_t k0, k1;
+  uint32_t pad;
+};
+// The jobs of one multi-job launch, passed by value as a kernel parameter.
+struct MultiJobTable {
+  int n_jobs;
+  MultiJob jobs[kMaxMultiJobs];
+};
+
 struct DdmParams {
   const float* A;      // [n] drift
   const float* z;      // [n] threshold
@@ -54,6 +76,9 @@ struct DdmParams {
   PhiloxKeys rk;               // round keys of (k0, k1)
 };
 cudaError_t launch_ddm(const DdmParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
+// Trials of several jobs of one DDM model in one persistent launch: p holds the
+// model's parameters, p.n the total of the jobs' trials and p.cursor.
+cudaError_t launch_ddm_multi(const DdmParams& p, const MultiJobTable& tab, cudaStream_t s);
 int ddm_max_blocks_per_sm(int block);
 
 // ------------------------------------------------------------------ LCA ---
@@ -76,6 +101,9 @@ struct LcaParams {
   int tail_max;                  // compacting form: at most this many trials left -> a warp each
 };
 cudaError_t launch_lca(const LcaParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
+// Trials of several jobs of one LCA model in one persistent launch (a lane per
+// trial; p holds the model's parameters, p.n the total and p.cursor).
+cudaError_t launch_lca_multi(const LcaParams& p, const MultiJobTable& tab, cudaStream_t s);
 bool lca_tpt_supported(int N, int tpt);
 int lca_max_blocks_per_sm(int N, int tpt, int block);
 

@@ -152,6 +152,38 @@ __global__ void __launch_bounds__(256, 8) ddm_batched(DdmParams p) {
   }
 }
 
+// Several jobs of one model in one launch (the serving loop's groups): each
+// warp takes the next entry of the concatenated trial list and runs it as
+// ddm_batched does, with its job's inputs, outputs and seed.
+__global__ void __launch_bounds__(256, 4) ddm_multi(DdmParams p,
+                                                    const __grid_constant__ MultiJobTable tab) {
+  __shared__ MultiJob s_job[kMaxMultiJobs];
+  copy_jobs(tab, s_job);
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    unsigned long long f = 0;
+    if (lane == 0) f = atomicAdd(p.cursor, 1ull);
+    f = __shfl_sync(kFull, f, 0);
+    if (f >= (unsigned long long)p.n) return;
+    const MultiJob& J = s_job[multi_job_of(s_job, tab.n_jobs, (long long)f)];
+    DdmParams q = p;
+    q.n = J.n;
+    q.A = J.in;
+    q.z = J.in + J.n;
+    q.choice = J.choice;
+    q.step = J.step;
+    q.xout = J.xout;
+    q.trial0 = J.trial0;
+    q.rk = philox_keys(J.k0, J.k1);
+    const long long t = (long long)f - J.start;
+    const DdmTrial d = ddm_begin(q, t);
+    if (d.narrow)
+      ddm_trial_warp<Fix32>(q, t, d);
+    else
+      ddm_trial_warp<Fix64>(q, t, d);
+  }
+}
+
 // One thread per trial, one block after another (the plain form).
 template <typename F>
 __device__ __forceinline__ void ddm_trial_plain(const DdmParams& p, long long t,
@@ -193,6 +225,18 @@ int ddm_max_blocks_per_sm(int block) {
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ddm_batched, block, 0);
   return nb;
+}
+
+cudaError_t launch_ddm_multi(const DdmParams& p, const MultiJobTable& tab, cudaStream_t s) {
+  if (p.n <= 0 || tab.n_jobs < 1 || tab.n_jobs > kMaxMultiJobs) return cudaErrorInvalidValue;
+  int nb = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ddm_multi, 256, 0);
+  if (e != cudaSuccess) return e;
+  long long grid = (long long)num_sms() * (nb > 0 ? nb : 1);
+  const long long need = (p.n * 32 + 255) / 256;   // one warp per trial
+  if (grid > need) grid = need;
+  ddm_multi<<<(unsigned)grid, 256, 0, s>>>(p, tab);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ddm(const DdmParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s) {

@@ -29,11 +29,17 @@ struct Lca {
   // Normals of this lane's units for step index k (0-based).
   static __device__ __forceinline__ void noise(const LcaParams& p, uint32_t trial, int k, int g,
                                                float (&e)[NU]) {
+    noise_k(p.rk, trial, k, g, e);
+  }
+
+  template <typename Keys>
+  static __device__ __forceinline__ void noise_k(const Keys& rk, uint32_t trial, int k, int g,
+                                                 float (&e)[NU]) {
     if constexpr (NU % 4 == 0) {
       const uint32_t b0 = (uint32_t)k * (uint32_t)(N / 4) + (uint32_t)(g * (NU / 4));
 #pragma unroll
       for (int b = 0; b < NU / 4; ++b) {
-        const float4 z = normals4(noise_block_rk(p.rk, trial, 0u, b0 + (uint32_t)b));
+        const float4 z = normals4(noise_block_rk(rk, trial, 0u, b0 + (uint32_t)b));
         e[4 * b + 0] = z.x;
         e[4 * b + 1] = z.y;
         e[4 * b + 2] = z.z;
@@ -46,7 +52,7 @@ struct Lca {
 #pragma unroll
       for (int i = 0; i < NU; ++i) {
         const uint32_t d = d0 + (uint32_t)i;
-        if (i == 0 || (d & 3u) == 0u) z = normals4(noise_block_rk(p.rk, trial, 0u, d >> 2));
+        if (i == 0 || (d & 3u) == 0u) z = normals4(noise_block_rk(rk, trial, 0u, d >> 2));
         e[i] = pick4(z, d & 3u);
       }
     }
@@ -357,6 +363,64 @@ __global__ void __launch_bounds__(256) lca_compact(LcaParams p) {
   }
 }
 
+// Several jobs of one model in one launch (the serving loop's groups), one
+// lane per trial: a lane that finishes its trial takes the next entry of the
+// concatenated trial list and runs it with that job's inputs, outputs and
+// seed; the steps are lca_batched's, so each trial ends as in a launch of its
+// job alone.
+template <int N>
+__global__ void __launch_bounds__(256) lca_multi(LcaParams p,
+                                                 const __grid_constant__ MultiJobTable tab) {
+  using L = Lca<N, 1>;
+  __shared__ MultiJob s_job[kMaxMultiJobs];
+  copy_jobs(tab, s_job);
+  const int lane = threadIdx.x & 31;
+  const unsigned self = 1u << lane;
+  float x[N], I[N], e[N];
+  LcaParams q = p;
+  KeyPair kp{};
+  long long t = 0;
+  int k = 0;
+  auto begin = [&](long long f) {
+    const MultiJob& J = s_job[multi_job_of(s_job, tab.n_jobs, f)];
+    q.I = J.in;
+    q.choice = J.choice;
+    q.step = J.step;
+    q.xout = J.xout;
+    q.trial0 = J.trial0;
+    kp.k.k0 = J.k0;
+    kp.k.k1 = J.k1;
+    t = f - J.start;
+    k = 0;
+    L::load(q, t, 0, x, I);
+    L::noise_k(kp, q.trial0 + (uint32_t)t, 0, 0, e);
+  };
+  long long f = fetch_trial(p.cursor, true);
+  bool active = f >= 0 && f < p.n;
+  if (active) begin(f);
+  while (__any_sync(kFull, active)) {
+    bool finished = false;
+    if (active) {
+      float en[N];
+      L::noise_k(kp, q.trial0 + (uint32_t)t, k + 1, 0, en);
+      int8_t c = -1;
+      const bool hit = L::step(q, e, 0, self, x, I, c);
+      ++k;
+      if (hit || k >= p.max_steps) {
+        L::store(q, t, 0, hit ? c : (int8_t)-1, hit ? k : p.max_steps, x);
+        finished = true;
+      }
+#pragma unroll
+      for (int i = 0; i < N; ++i) e[i] = en[i];
+    }
+    f = fetch_trial(p.cursor, finished);
+    if (finished) {
+      active = f < p.n;
+      if (active) begin(f);
+    }
+  }
+}
+
 template <int N>
 __global__ void __launch_bounds__(256) lca_plain(LcaParams p) {
   using L = Lca<N, 1>;
@@ -421,6 +485,18 @@ cudaError_t launch_n(const LcaParams& p, int mode, const LaunchCfg& cfg, cudaStr
 }
 
 template <int N>
+cudaError_t launch_multi_n(const LcaParams& p, const MultiJobTable& tab, cudaStream_t s) {
+  int nb = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, lca_multi<N>, 256, 0);
+  if (e != cudaSuccess) return e;
+  long long grid = (long long)num_sms() * (nb > 0 ? nb : 1);
+  const long long need = (p.n + 255) / 256;   // one lane per trial
+  if (grid > need) grid = need;
+  lca_multi<N><<<(unsigned)grid, 256, 0, s>>>(p, tab);
+  return cudaGetLastError();
+}
+
+template <int N>
 void* compact_fn() {
   return (void*)lca_compact<N>;
 }
@@ -457,6 +533,18 @@ void* kernel_for(int N, int tpt) {
 }
 
 }  // namespace
+
+cudaError_t launch_lca_multi(const LcaParams& p, const MultiJobTable& tab, cudaStream_t s) {
+  if (p.n <= 0 || tab.n_jobs < 1 || tab.n_jobs > kMaxMultiJobs) return cudaErrorInvalidValue;
+  switch (p.N) {
+#define DG_CASE(n) case n: return launch_multi_n<n>(p, tab, s);
+    DG_CASE(1) DG_CASE(2) DG_CASE(3) DG_CASE(4) DG_CASE(5) DG_CASE(6) DG_CASE(7) DG_CASE(8)
+    DG_CASE(9) DG_CASE(10) DG_CASE(11) DG_CASE(12) DG_CASE(13) DG_CASE(14) DG_CASE(15)
+    DG_CASE(16)
+#undef DG_CASE
+  }
+  return cudaErrorInvalidValue;
+}
 
 bool lca_tpt_supported(int N, int tpt) { return kernel_for(N, tpt) != nullptr; }
 

@@ -436,6 +436,30 @@ std::vector<dg::LaunchCfg> grid_candidates(long long n_cand, int lanes) {
 
 // ---------------------------------------------------------- run paths ---
 
+// The model's part of a DDM or LCA launch (the per-call part is set by the caller).
+dg::DdmParams ddm_model_params(const dg_model* m) {
+  dg::DdmParams p{};
+  p.dt = m->dt;
+  p.diffusion = m->diffusion;
+  p.x0 = m->x0;
+  p.max_steps = m->max_steps;
+  return p;
+}
+
+dg::LcaParams lca_model_params(const dg_model* m) {
+  dg::LcaParams p{};
+  p.N = m->N;
+  p.dt = m->dt;
+  p.diffusion = m->diffusion;
+  p.leak = m->leak;
+  p.inhibition = m->inhibition;
+  p.threshold = m->threshold;
+  p.max_steps = m->max_steps;
+  p.rectify = m->rectify;
+  p.two_sided = m->two_sided;
+  return p;
+}
+
 dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t* step,
                      float* fs, cudaStream_t s) {
   if (d->n_trials == 0) return DG_OK;
@@ -447,7 +471,7 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
   const std::string bucket = std::to_string(log2_bucket(d->n_trials));
 
   if (m->kind == K_DDM) {
-    dg::DdmParams p{};
+    dg::DdmParams p = ddm_model_params(m);
     p.A = d->trial_params;
     p.z = d->trial_params + d->n_trials;
     p.n = d->n_trials;
@@ -455,10 +479,6 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
     p.k0 = k0;
     p.k1 = k1;
     p.rk = dg::philox_keys(k0, k1);
-    p.dt = m->dt;
-    p.diffusion = m->diffusion;
-    p.x0 = m->x0;
-    p.max_steps = m->max_steps;
     p.choice = choice;
     p.step = step;
     p.xout = fs;
@@ -489,22 +509,13 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
     return run_tuned(m->ctx, "ddm/" + bucket, ddm_candidates(), s, go);
   }
   if (m->kind == K_LCA) {
-    dg::LcaParams p{};
+    dg::LcaParams p = lca_model_params(m);
     p.I = d->trial_params;
     p.n = d->n_trials;
     p.trial0 = (uint32_t)d->trial_offset;
-    p.N = m->N;
     p.k0 = k0;
     p.k1 = k1;
     p.rk = dg::philox_keys(k0, k1);
-    p.dt = m->dt;
-    p.diffusion = m->diffusion;
-    p.leak = m->leak;
-    p.inhibition = m->inhibition;
-    p.threshold = m->threshold;
-    p.max_steps = m->max_steps;
-    p.rectify = m->rectify;
-    p.two_sided = m->two_sided;
     {
       const char* e = getenv("DG_LCA_CHUNK");   // steps between compactions
       p.chunk = e && atoi(e) > 0 ? atoi(e) : 32;
@@ -652,6 +663,68 @@ size_t run_cond_floats(const dg_model* m, const dg_run_desc* d) {
   return 0;
 }
 
+// Several jobs of one DDM or LCA model in one persistent launch: the jobs'
+// trials form one list (job i's trials after those of jobs 0 .. i-1, empty
+// jobs left out) that the kernel hands out from one cursor; each trial runs
+// with its job's inputs, outputs, seed and trial offset, exactly as in a
+// batched dg_run of that job alone. Arguments are checked by the caller.
+dg_status run_jobs_device(dg_model* m, int n_jobs, const dg_run_desc* d, int8_t* const* choice,
+                          int32_t* const* step, float* const* fs, cudaStream_t s) {
+  dg::MultiJobTable tab{};
+  long long total = 0;
+  for (int i = 0; i < n_jobs; ++i) {
+    if (d[i].n_trials == 0) continue;
+    dg::MultiJob& J = tab.jobs[tab.n_jobs++];
+    J.start = total;
+    J.n = d[i].n_trials;
+    J.in = d[i].trial_params;
+    J.choice = choice[i];
+    J.step = step[i];
+    J.xout = fs ? fs[i] : nullptr;
+    J.trial0 = (uint32_t)d[i].trial_offset;
+    J.k0 = (uint32_t)d[i].seed;
+    J.k1 = (uint32_t)(d[i].seed >> 32);
+    total += d[i].n_trials;
+  }
+  if (total == 0) return DG_OK;
+  Scratch* sc = nullptr;
+  dg_status st = get_scratch(m->ctx, s, &sc);
+  if (st != DG_OK) return st;
+  DG_CUDA(cudaMemsetAsync(sc->cursor(), 0, 8, s));
+  if (m->kind == K_DDM) {
+    dg::DdmParams p = ddm_model_params(m);
+    p.n = total;
+    p.cursor = sc->cursor();
+    DG_CUDA(dg::launch_ddm_multi(p, tab, s));
+    return DG_OK;
+  }
+  dg::LcaParams p = lca_model_params(m);
+  p.n = total;
+  p.cursor = sc->cursor();
+  DG_CUDA(dg::launch_lca_multi(p, tab, s));
+  return DG_OK;
+}
+
+dg_status check_jobs_args(dg_model* m, int n_jobs, const dg_run_desc* d, int8_t* const* choice,
+                          int32_t* const* step) {
+  if (!m || !d || !choice || !step || n_jobs < 1 || n_jobs > dg::kMaxMultiJobs)
+    return fail(DG_E_ARG, "dg_run_jobs: null model, descs or outputs, or n_jobs outside [1, %d]",
+                dg::kMaxMultiJobs);
+  if (m->kind != K_DDM && m->kind != K_LCA)
+    return fail(DG_E_UNSUPPORTED, "dg_run_jobs: DDM and LCA models only");
+  long long total = 0;
+  for (int i = 0; i < n_jobs; ++i) {
+    dg_status st = check_run_args(m, d + i, choice[i], step[i]);
+    if (st != DG_OK) return st;
+    if (d[i].mode != DG_MODE_BATCHED)
+      return fail(DG_E_ARG, "dg_run_jobs: job %d: the batched mode only", i);
+    total += d[i].n_trials;
+  }
+  if (total > INT32_MAX)
+    return fail(DG_E_ARG, "dg_run_jobs: %lld trials in all, at most 2^31-1", total);
+  return DG_OK;
+}
+
 // ------------------------------------------------------------- grid ---
 
 dg_status check_grid_args(dg_model* m, const dg_grid_desc* d, dg_grid_result* result) {
@@ -743,8 +816,14 @@ struct Server {
   std::unordered_map<uint64_t, std::shared_ptr<JobRec>> jobs;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
-  std::vector<uint64_t> slot_job;  // 0 = free
+  std::vector<std::vector<uint64_t>> slot_jobs;  // the jobs of the slot's launch; empty = free
   size_t in_use = 0;
+  // Small DDM and LCA jobs of one model share one launch (dg_run_jobs): a
+  // job of at most group_job_trials trials gathers later queued jobs of the
+  // same model, up to kMaxMultiJobs jobs and kGroupTrials trials in all.
+  long long group_job_trials = 1 << 16;
+  static constexpr long long kGroupTrials = 1 << 22;
+  static constexpr size_t kGroupScan = 4096;   // queued jobs looked at per group
   uint64_t next_id = 1;
   int64_t n_running = 0, n_done = 0;
   bool stop = false;
@@ -768,8 +847,9 @@ struct Server {
       cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
       streams.push_back(s);
       events.push_back(e);
-      slot_job.push_back(0);
+      slot_jobs.emplace_back();
     }
+    if (const char* e = getenv("DG_SERVE_GROUP_TRIALS")) group_job_trials = atoll(e);
     th = std::thread([this] { loop(); });
   }
 
@@ -806,8 +886,22 @@ struct Server {
     return b + 16 * 256;
   }
 
-  // Enqueue a job's copies and kernels on its slot's stream.
-  dg_status launch(JobRec& r, cudaStream_t s) {
+  bool groupable(const JobRec& r) const {
+    const dg_job& j = r.job;
+    return !j.is_grid && (j.model->kind == K_DDM || j.model->kind == K_LCA) &&
+           j.run.mode == DG_MODE_BATCHED && j.run.n_trials > 0 &&
+           j.run.n_trials <= group_job_trials;
+  }
+
+  // Device copies of a run job: inputs copied in, outputs allocated.
+  struct Staged {
+    dg_run_desc d;
+    int8_t* choice;
+    int32_t* step;
+    float* fs;
+  };
+
+  dg_status stage_run(JobRec& r, cudaStream_t s, Staged* out) {
     DG_CUDA(cudaMallocAsync(&r.dmem, r.bytes, s));
     unsigned char* p = reinterpret_cast<unsigned char*>(r.dmem);
     auto take = [&](size_t bytes) {
@@ -816,31 +910,6 @@ struct Server {
       return q;
     };
     const dg_job& j = r.job;
-    if (j.is_grid) {
-      dg_grid_desc d = j.grid;
-      const size_t nc = d.cand_count ? (size_t)d.cand_count
-                                     : (size_t)d.n_levels[0] * d.n_levels[1] * d.n_levels[2];
-      float* pos = (float*)take(6 * sizeof(float) * d.n_trials);
-      DG_CUDA(cudaMemcpyAsync(pos, j.grid.positions, 6 * sizeof(float) * d.n_trials,
-                              cudaMemcpyHostToDevice, s));
-      d.positions = pos;
-      for (int i = 0; i < 3; ++i) {
-        float* lv = (float*)take(sizeof(float) * d.n_levels[i]);
-        DG_CUDA(cudaMemcpyAsync(lv, j.grid.levels[i], sizeof(float) * d.n_levels[i],
-                                cudaMemcpyHostToDevice, s));
-        d.levels[i] = lv;
-      }
-      dg_grid_result* res = (dg_grid_result*)take(sizeof(dg_grid_result));
-      double* means = (double*)take(sizeof(double) * nc);
-      dg_status st = grid_device(j.model, &d, res, means, s);
-      if (st != DG_OK) return st;
-      DG_CUDA(cudaMemcpyAsync(j.grid_result, res, sizeof(dg_grid_result),
-                              cudaMemcpyDeviceToHost, s));
-      if (j.cand_means)
-        DG_CUDA(cudaMemcpyAsync(j.cand_means, means, sizeof(double) * nc,
-                                cudaMemcpyDeviceToHost, s));
-      return DG_OK;
-    }
     dg_run_desc d = j.run;
     const size_t n = (size_t)d.n_trials;
     const size_t pf = run_param_floats(j.model, &d), cf = run_cond_floats(j.model, &d);
@@ -854,15 +923,86 @@ struct Server {
       DG_CUDA(cudaMemcpyAsync(ci, j.run.cond_inputs, cf * sizeof(float), cudaMemcpyHostToDevice, s));
       d.cond_inputs = ci;
     }
-    int8_t* ch = (int8_t*)take(n);
-    int32_t* stp = (int32_t*)take(n * sizeof(int32_t));
-    float* fs = j.final_state ? (float*)take(n * sizeof(float) * j.model->state_size) : nullptr;
-    dg_status st = run_device(j.model, &d, ch, stp, fs, s);
+    out->d = d;
+    out->choice = (int8_t*)take(n);
+    out->step = (int32_t*)take(n * sizeof(int32_t));
+    out->fs = j.final_state ? (float*)take(n * sizeof(float) * j.model->state_size) : nullptr;
+    return DG_OK;
+  }
+
+  dg_status unstage_run(JobRec& r, cudaStream_t s, const Staged& g) {
+    const dg_job& j = r.job;
+    const size_t n = (size_t)j.run.n_trials;
+    DG_CUDA(cudaMemcpyAsync(j.choice, g.choice, n, cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaMemcpyAsync(j.step, g.step, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (g.fs)
+      DG_CUDA(cudaMemcpyAsync(j.final_state, g.fs, n * sizeof(float) * j.model->state_size,
+                              cudaMemcpyDeviceToHost, s));
+    return DG_OK;
+  }
+
+  // Enqueue a group's copies and one multi-job launch on its slot's stream.
+  dg_status launch_group(const std::vector<std::shared_ptr<JobRec>>& grp, cudaStream_t s) {
+    const int n = (int)grp.size();
+    std::vector<Staged> g(n);
+    std::vector<dg_run_desc> d(n);
+    std::vector<int8_t*> ch(n);
+    std::vector<int32_t*> stp(n);
+    std::vector<float*> fs(n);
+    for (int i = 0; i < n; ++i) {
+      dg_status st = stage_run(*grp[i], s, &g[i]);
+      if (st != DG_OK) return st;
+      d[i] = g[i].d;
+      ch[i] = g[i].choice;
+      stp[i] = g[i].step;
+      fs[i] = g[i].fs;
+    }
+    dg_status st = run_jobs_device(grp[0]->job.model, n, d.data(), ch.data(), stp.data(),
+                                   fs.data(), s);
     if (st != DG_OK) return st;
-    DG_CUDA(cudaMemcpyAsync(j.choice, ch, n, cudaMemcpyDeviceToHost, s));
-    DG_CUDA(cudaMemcpyAsync(j.step, stp, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    if (fs)
-      DG_CUDA(cudaMemcpyAsync(j.final_state, fs, n * sizeof(float) * j.model->state_size,
+    for (int i = 0; i < n; ++i)
+      if ((st = unstage_run(*grp[i], s, g[i])) != DG_OK) return st;
+    return DG_OK;
+  }
+
+  // Enqueue a job's copies and kernels on its slot's stream.
+  dg_status launch(JobRec& r, cudaStream_t s) {
+    const dg_job& j = r.job;
+    if (!j.is_grid) {
+      Staged g;
+      dg_status st = stage_run(r, s, &g);
+      if (st != DG_OK) return st;
+      if ((st = run_device(j.model, &g.d, g.choice, g.step, g.fs, s)) != DG_OK) return st;
+      return unstage_run(r, s, g);
+    }
+    DG_CUDA(cudaMallocAsync(&r.dmem, r.bytes, s));
+    unsigned char* p = reinterpret_cast<unsigned char*>(r.dmem);
+    auto take = [&](size_t bytes) {
+      unsigned char* q = p;
+      p += (bytes + 255) / 256 * 256;
+      return q;
+    };
+    dg_grid_desc d = j.grid;
+    const size_t nc = d.cand_count ? (size_t)d.cand_count
+                                   : (size_t)d.n_levels[0] * d.n_levels[1] * d.n_levels[2];
+    float* pos = (float*)take(6 * sizeof(float) * d.n_trials);
+    DG_CUDA(cudaMemcpyAsync(pos, j.grid.positions, 6 * sizeof(float) * d.n_trials,
+                            cudaMemcpyHostToDevice, s));
+    d.positions = pos;
+    for (int i = 0; i < 3; ++i) {
+      float* lv = (float*)take(sizeof(float) * d.n_levels[i]);
+      DG_CUDA(cudaMemcpyAsync(lv, j.grid.levels[i], sizeof(float) * d.n_levels[i],
+                              cudaMemcpyHostToDevice, s));
+      d.levels[i] = lv;
+    }
+    dg_grid_result* res = (dg_grid_result*)take(sizeof(dg_grid_result));
+    double* means = (double*)take(sizeof(double) * nc);
+    dg_status st = grid_device(j.model, &d, res, means, s);
+    if (st != DG_OK) return st;
+    DG_CUDA(cudaMemcpyAsync(j.grid_result, res, sizeof(dg_grid_result),
+                            cudaMemcpyDeviceToHost, s));
+    if (j.cand_means)
+      DG_CUDA(cudaMemcpyAsync(j.cand_means, means, sizeof(double) * nc,
                               cudaMemcpyDeviceToHost, s));
     return DG_OK;
   }
@@ -878,7 +1018,6 @@ struct Server {
     r.status = st;
     r.state = 2;
     r.t_done = now_s();
-    if (r.slot >= 0) slot_job[r.slot] = 0;
     r.slot = -1;
     --n_running;
     ++n_done;
@@ -892,51 +1031,80 @@ struct Server {
       bool progress = false;
       // retire finished jobs
       for (size_t i = 0; i < streams.size(); ++i) {
-        if (!slot_job[i]) continue;
+        if (slot_jobs[i].empty()) continue;
         cudaError_t q = cudaEventQuery(events[i]);
         if (q == cudaErrorNotReady) continue;
-        auto& r = *jobs[slot_job[i]];
-        finish(r, q == cudaSuccess ? DG_OK : DG_E_CUDA);
+        for (uint64_t id : slot_jobs[i]) finish(*jobs[id], q == cudaSuccess ? DG_OK : DG_E_CUDA);
+        slot_jobs[i].clear();
         progress = true;
       }
       if (progress) cv_done.notify_all();
       // admit queued jobs in arrival order while memory and slots allow;
       // the launches themselves happen without the lock
-      std::vector<std::shared_ptr<JobRec>> admitted;
+      std::vector<std::vector<std::shared_ptr<JobRec>>> admitted;
       while (!queue.empty()) {
         auto rp = jobs[queue.front()];
         if (in_use + rp->bytes > ctx->budget) break;
         int slot = -1;
         for (size_t i = 0; i < streams.size(); ++i)
-          if (!slot_job[i]) {
+          if (slot_jobs[i].empty()) {
             slot = (int)i;
             break;
           }
         if (slot < 0) break;
         queue.pop_front();
-        rp->slot = slot;
-        rp->state = 1;
-        rp->t_admit = now_s();
-        in_use += rp->bytes;
-        ++n_running;
-        slot_job[slot] = rp->id;
-        admitted.push_back(rp);
+        std::vector<std::shared_ptr<JobRec>> grp{rp};
+        size_t bytes = rp->bytes;
+        if (groupable(*rp)) {
+          long long total = rp->job.run.n_trials;
+          size_t scanned = 0;
+          for (auto it = queue.begin(); it != queue.end() && scanned < kGroupScan &&
+                                        (int)grp.size() < dg::kMaxMultiJobs;
+               ++scanned) {
+            auto& q = jobs[*it];
+            if (groupable(*q) && q->job.model == rp->job.model &&
+                total + q->job.run.n_trials <= kGroupTrials &&
+                in_use + bytes + q->bytes <= ctx->budget) {
+              grp.push_back(q);
+              total += q->job.run.n_trials;
+              bytes += q->bytes;
+              it = queue.erase(it);
+            } else {
+              ++it;
+            }
+          }
+        }
+        const double t = now_s();
+        for (auto& g : grp) {
+          g->slot = slot;
+          g->state = 1;
+          g->t_admit = t;
+          in_use += g->bytes;
+          ++n_running;
+          slot_jobs[slot].push_back(g->id);
+        }
+        admitted.push_back(std::move(grp));
       }
       if (!admitted.empty()) {
         progress = true;
         lk.unlock();
         std::vector<std::pair<std::shared_ptr<JobRec>, dg_status>> failed;
-        for (auto& rp : admitted) {
-          cudaStream_t s = streams[rp->slot];
-          dg_status st = launch(*rp, s);
-          if (st == DG_OK && cudaEventRecord(events[rp->slot], s) != cudaSuccess) st = DG_E_CUDA;
+        for (auto& grp : admitted) {
+          const int slot = grp[0]->slot;
+          cudaStream_t s = streams[slot];
+          dg_status st = grp.size() == 1 ? launch(*grp[0], s) : launch_group(grp, s);
+          if (st == DG_OK && cudaEventRecord(events[slot], s) != cudaSuccess) st = DG_E_CUDA;
           if (st != DG_OK) {
             cudaStreamSynchronize(s);
-            failed.emplace_back(rp, st);
+            for (auto& g : grp) failed.emplace_back(g, st);
           }
         }
         lk.lock();
-        for (auto& f : failed) finish(*f.first, f.second);
+        for (auto& f : failed) {
+          const int slot = f.first->slot;
+          finish(*f.first, f.second);
+          if (slot >= 0) slot_jobs[slot].clear();
+        }
         if (!failed.empty()) cv_done.notify_all();
       }
       if (stop) break;
@@ -1437,6 +1605,15 @@ dg_status dg_run(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t* ste
   if (st != DG_OK) return st;
   DG_CUDA(cudaSetDevice(m->ctx->device));
   return run_device(m, d, choice, step, final_state, (cudaStream_t)stream);
+}
+
+dg_status dg_run_jobs(dg_model* m, int32_t n_jobs, const dg_run_desc* descs,
+                      int8_t* const* choice, int32_t* const* step, float* const* final_state,
+                      void* stream) {
+  dg_status st = check_jobs_args(m, n_jobs, descs, choice, step);
+  if (st != DG_OK) return st;
+  DG_CUDA(cudaSetDevice(m->ctx->device));
+  return run_jobs_device(m, n_jobs, descs, choice, step, final_state, (cudaStream_t)stream);
 }
 
 dg_status dg_grid_search(dg_model* m, const dg_grid_desc* d, dg_grid_result* result,

@@ -1,0 +1,190 @@
+"""GPU: several DDM or LCA jobs in one persistent launch (dg_run_jobs, and the
+serving loop's groups of small jobs) return exactly what each job returns
+when run alone, and what the oracle returns."""
+import numpy as np
+import pytest
+
+from gpu_util import compare_decisions, dev, host
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [0, 1, 37, 1000, 4097, 20000, 3, 65536]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2110_15425_gb300 import binding as B
+    torch.cuda.init()
+    c = B.dg_create(0)
+    yield c
+    B.dg_destroy(c)
+
+
+def _inputs(kind, n, i, N=None):
+    from paper_2110_15425_gb300 import workloads as W
+    if kind == "ddm":
+        w = W.ddm(n_trials=max(n, 1), param_seed=70 + i)
+        return np.ascontiguousarray(np.concatenate([w["A"][:n], w["z"][:n]]).astype(np.float32))
+    w = W.lca(n_trials=max(n, 1), N=N, input_seed=90 + i)
+    return np.ascontiguousarray(w["I"][:n].astype(np.float32))
+
+
+def _alone(B, model, h, n, seed, offset, state):
+    import torch
+    d = B.run_desc(n, seed, trial_params=dev(h) if n else None, trial_offset=offset)
+    c = torch.full((max(n, 1),), 9, dtype=torch.int8, device="cuda")
+    s = torch.full((max(n, 1),), -9, dtype=torch.int32, device="cuda")
+    f = torch.zeros(max(n, 1) * state, dtype=torch.float32, device="cuda")
+    if n:
+        B.dg_run(model, d, c, s, f)
+    return host(c)[:n], host(s)[:n], host(f)[:n * state]
+
+
+def _jobs(B, model, hs, ns, seeds, offsets, state, with_state):
+    import torch
+    descs, cs, ss, fs = [], [], [], []
+    for h, n, seed, off, ws in zip(hs, ns, seeds, offsets, with_state):
+        descs.append(B.run_desc(n, seed, trial_params=dev(h) if n else None, trial_offset=off))
+        cs.append(torch.full((max(n, 1),), 9, dtype=torch.int8, device="cuda"))
+        ss.append(torch.full((max(n, 1),), -9, dtype=torch.int32, device="cuda"))
+        fs.append(torch.zeros(max(n, 1) * state, dtype=torch.float32, device="cuda") if ws
+                  else None)
+    B.dg_run_jobs(model, descs, cs, ss, fs)
+    return descs, cs, ss, fs
+
+
+@pytest.mark.parametrize("kind,N", [("ddm", 1), ("lca", 4), ("lca", 8), ("lca", 16), ("lca", 5),
+                                    ("lca", 1)])
+def test_run_jobs_equal_single_runs(ctx, kind, N):
+    from paper_2110_15425_gb300 import binding as B
+    if kind == "ddm":
+        model = B.compose_ddm(ctx)
+    elif N == 1:
+        model = B.compose_lca(ctx, 1, leak=0.0, inhibition=0.0, sigma=1.0, dt=1e-3,
+                              threshold=1.25, max_steps=10000, rectify=False, two_sided=True)
+    else:
+        model = B.compose_lca(ctx, N)
+    try:
+        state = B.dg_model_info(model)[1]
+        hs = [_inputs(kind, n, i, N) for i, n in enumerate(SIZES)]
+        seeds = [11 + 1000003 * i for i in range(len(SIZES))]
+        offsets = [0, 5, 0, 123456, 0, 7, 2 ** 31, 0]
+        with_state = [i % 2 == 0 for i in range(len(SIZES))]
+        descs, cs, ss, fs = _jobs(B, model, hs, SIZES, seeds, offsets, state, with_state)
+        for i, n in enumerate(SIZES):
+            c, s, f = _alone(B, model, hs[i], n, seeds[i], offsets[i], state)
+            assert np.array_equal(host(cs[i])[:n], c), (kind, N, i)
+            assert np.array_equal(host(ss[i])[:n], s), (kind, N, i)
+            if with_state[i]:
+                assert np.array_equal(host(fs[i])[:n * state].view(np.uint32), f.view(np.uint32))
+            if n == 0:
+                assert host(cs[i])[0] == 9 and host(ss[i])[0] == -9   # untouched
+    finally:
+        B.dg_model_free(model)
+
+
+def test_run_jobs_against_oracle(ctx, orc, threads):
+    """Job i of a multi-job launch against the oracle on a sample of its
+    trials, with the job's own seed and trial offset."""
+    from paper_2110_15425_gb300 import binding as B
+    from paper_2110_15425_gb300 import workloads as W
+    md = B.compose_ddm(ctx)
+    ml = B.compose_lca(ctx, 8)
+    try:
+        for kind, model in (("ddm", md), ("lca", ml)):
+            ws = [W.ddm(n_trials=6000, param_seed=5 + i) if kind == "ddm"
+                  else W.lca(n_trials=6000, N=8, input_seed=5 + i) for i in range(3)]
+            offsets = [0, 6000, 40000]
+            seeds = [w["seed"] + i for i, w in enumerate(ws)]
+            hs = [np.ascontiguousarray(np.concatenate([w["A"], w["z"]])) if kind == "ddm"
+                  else np.ascontiguousarray(w["I"]) for w in ws]
+            state = B.dg_model_info(model)[1]
+            descs, cs, ss, fs = _jobs(B, model, hs, [6000] * 3, seeds, offsets, state,
+                                      [False] * 3)
+            for i, w in enumerate(ws):
+                ids = np.arange(0, 6000, 13, dtype=np.uint32)
+                # the oracle reads trial g's inputs at row g: pad to the offset
+                off = offsets[i]
+                if kind == "ddm":
+                    A = np.concatenate([np.zeros(off, np.float32), w["A"]])
+                    z = np.concatenate([np.ones(off, np.float32), w["z"]])
+                    ref = orc.ddm_run(A, z, seeds[i], trial_ids=ids + off, threads=threads)
+                else:
+                    I = np.concatenate([np.zeros((off, 8), np.float32), w["I"]])
+                    ref = orc.lca_run(I, seeds[i], trial_ids=ids + off, threads=threads)
+                compare_decisions(host(cs[i])[ids], host(ss[i])[ids], ref, f"{kind} job {i}")
+    finally:
+        B.dg_model_free(md)
+        B.dg_model_free(ml)
+
+
+def test_run_jobs_arguments(ctx):
+    import torch
+    from paper_2110_15425_gb300 import binding as B
+    md = B.compose_ddm(ctx)
+    mp = B.compose_predator_prey(ctx)
+    h = _inputs("ddm", 10, 0)
+    c = torch.zeros(10, dtype=torch.int8, device="cuda")
+    s = torch.zeros(10, dtype=torch.int32, device="cuda")
+    try:
+        d = B.run_desc(10, 1, trial_params=dev(h))
+        with pytest.raises(RuntimeError):
+            B.dg_run_jobs(md, [], [], [])
+        with pytest.raises(RuntimeError):
+            B.dg_run_jobs(md, [d] * 65, [c] * 65, [s] * 65)
+        with pytest.raises(RuntimeError):
+            B.dg_run_jobs(mp, [d], [c], [s])
+        dp = B.run_desc(10, 1, trial_params=dev(h), mode=B.DG_MODE_PLAIN)
+        with pytest.raises(RuntimeError):
+            B.dg_run_jobs(md, [d, dp], [c, c], [s, s])
+        dn = B.run_desc(10, 1)   # no trial_params
+        with pytest.raises(RuntimeError):
+            B.dg_run_jobs(md, [dn], [c], [s])
+        B.dg_run_jobs(md, [d] * 64, [c] * 64, [s] * 64)   # 64 jobs is the limit
+    finally:
+        B.dg_model_free(md)
+        B.dg_model_free(mp)
+
+
+def test_served_small_jobs_grouped_equal_direct_runs(ctx):
+    """Many small DDM and LCA jobs of several models submitted at once: the
+    serving loop groups them into multi-job launches; every job's outputs
+    (final states included) equal a direct dg_run of the job."""
+    from paper_2110_15425_gb300 import binding as B
+    rng = np.random.default_rng(12)
+    models = dict(ddm=B.compose_ddm(ctx), ddm2=B.compose_ddm(ctx, dt=2e-3, sigma=0.8),
+                  lca4=B.compose_lca(ctx, 4), lca8=B.compose_lca(ctx, 8))
+    try:
+        jobs = []
+        for i in range(160):
+            k = ["ddm", "ddm2", "lca4", "lca8"][int(rng.integers(4))]
+            n = int(rng.integers(1, 12000))
+            N = 1 if k.startswith("ddm") else int(k[3:])
+            h = _inputs("ddm" if N == 1 else "lca", n, 200 + i, N)
+            j = B.dg_job()
+            j.model = models[k].value
+            j.run.n_trials = n
+            j.run.seed = int(rng.integers(1, 2 ** 40))
+            j.run.trial_offset = int(rng.integers(0, 10 ** 6))
+            j.run.trial_params = h.ctypes.data
+            ch = np.zeros(n, np.int8)
+            st = np.zeros(n, np.int32)
+            fs = np.zeros(n * N, np.float32) if i % 3 == 0 else None
+            j.choice = ch.ctypes.data
+            j.step = st.ctypes.data
+            if fs is not None:
+                j.final_state = fs.ctypes.data
+            jobs.append((k, n, N, h, j, ch, st, fs))
+        tickets = [B.dg_submit(ctx, x[4]) for x in jobs]
+        for t in tickets:
+            r = B.dg_wait(ctx, t, 120000)
+            assert r.status == 0
+        for k, n, N, h, j, ch, st, fs in jobs:
+            c, s, f = _alone(B, models[k], h, n, j.run.seed, j.run.trial_offset, N)
+            assert np.array_equal(ch, c) and np.array_equal(st, s), (k, n)
+            if fs is not None:
+                assert np.array_equal(fs.view(np.uint32), f.view(np.uint32)), (k, n)
+    finally:
+        for m in models.values():
+            B.dg_model_free(m)
