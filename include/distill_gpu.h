@@ -246,7 +246,7 @@ dg_status dg_run(dg_model* model, const dg_run_desc* desc, int8_t* choice, int32
    DG_MODE_BATCHED; jobs may differ in n_trials (0 allowed), trial_offset, seed
    and trial_params. choice, step (and final_state when not NULL) are host
    arrays of n_jobs device pointers; an entry of final_state may be NULL.
-   n_jobs: 1 .. 64; at most 2^31 - 1 trials in all.
+   n_jobs: 1 .. 256; at most 2^31 - 1 trials in all.
    Errors: DG_E_ARG, DG_E_UNSUPPORTED (not a DDM or LCA model), DG_E_CUDA. */
 dg_status dg_run_jobs(dg_model* model, int32_t n_jobs, const dg_run_desc* descs,
                       int8_t* const* choice, int32_t* const* step, float* const* final_state,
@@ -513,8 +513,12 @@ typedef struct {
    a job's memory when its results are on the host. A batched DDM or LCA job of
    at most 65,536 trials (environment DG_SERVE_GROUP_TRIALS; 0 turns this off)
    takes later queued batched DDM or LCA jobs of the same model, up to that size
-   each, 64 jobs and 2^22 trials in all, into one dg_run_jobs launch; results
-   are those of the jobs run alone.
+   each, 256 jobs and 2^23 trials in all, into one dg_run_jobs launch; results
+   are those of the jobs run alone. A grouped job whose trial_params, choice,
+   step (and final_state) are all pinned host memory (cudaHostAlloc, or
+   cudaHostRegister'd) is read and written by the kernel in place through the
+   memory's device mapping, without staging copies (DG_SERVE_ZERO_COPY=0 turns
+   this off).
    Errors: DG_E_ARG; DG_E_BUDGET if the job alone exceeds the budget. */
 dg_status dg_submit(dg_ctx* ctx, const dg_job* job, uint64_t* ticket);
 

@@ -40,7 +40,7 @@ DG_HD inline PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
 // concatenation of its jobs' trials, job j holding list entries
 // start .. start + n - 1; each job has its own inputs, outputs, seed and
 // trial offset (the model's parameters are the launch's).
-constexpr int kMaxMultiJobs = 64;
+constexpr int kMaxMultiJobs = 256;   // table: 16 KB of kernel parameter space
 struct MultiJob {
   long long start;
   long long n;

@@ -226,16 +226,16 @@ inline size_t compact_smem(int N) { return (3 * (size_t)N * 256) * sizeof(float)
 // step k + l div (N/4)), then every lane takes those steps on its own copy of
 // the state, gathering each step's normals by shuffles. The arithmetic is the
 // one-lane step's, so the trial ends exactly as it would have.
-template <int N>
-__device__ void lca_warp_trial(const LcaParams& p, long long t, int k, float (&x)[N],
-                               const float (&I)[N]) {
+template <int N, typename Keys>
+__device__ void lca_warp_trial(const LcaParams& p, const Keys& rk, long long t, int k,
+                               float (&x)[N], const float (&I)[N]) {
   using L = Lca<N, 1>;
   constexpr int NB = N / 4, R = 32 / NB;
   const int lane = threadIdx.x & 31;
   const uint32_t trial = p.trial0 + (uint32_t)t;
   while (true) {
     const float4 z = normals4(noise_block_rk(
-        p.rk, trial, 0u, (uint32_t)(k + lane / NB) * (uint32_t)NB + (uint32_t)(lane % NB)));
+        rk, trial, 0u, (uint32_t)(k + lane / NB) * (uint32_t)NB + (uint32_t)(lane % NB)));
 #pragma unroll 1
     for (int s = 0; s < R; ++s) {
       float e[N];
@@ -258,8 +258,22 @@ __device__ void lca_warp_trial(const LcaParams& p, long long t, int k, float (&x
   }
 }
 
-template <int N>
-__global__ void __launch_bounds__(256) lca_compact(LcaParams p) {
+// MULTI: the trials of several jobs of one model (the serving loop's groups),
+// one list over the jobs in order; a lane holds its trial's list index f and
+// binds the trial's job (inputs, outputs, seed, trial offset) when it takes
+// the trial on, so a trial ends exactly as in a launch of its job alone.
+template <bool MULTI>
+struct TableOf {
+  using type = MultiJobTable;
+};
+template <>
+struct TableOf<false> {   // a single job carries no table
+  struct type {};
+};
+
+template <int N, bool MULTI>
+__global__ void __launch_bounds__(256) lca_compact(
+    LcaParams p, const __grid_constant__ typename TableOf<MULTI>::type tab) {
   using L = Lca<N, 1>;
   extern __shared__ __align__(16) float csm[];
   float* s_x = csm;                          // [N][256]
@@ -268,17 +282,45 @@ __global__ void __launch_bounds__(256) lca_compact(LcaParams p) {
   long long* s_t = reinterpret_cast<long long*>(csm + 3 * N * 256);   // [256]
   int* s_k = reinterpret_cast<int*>(s_t + 256);                        // [256]
   __shared__ int warp_cnt[8];
+  __shared__ MultiJob s_job[MULTI ? kMaxMultiJobs : 1];
+  if constexpr (MULTI) copy_jobs(tab, s_job);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned self = 1u << lane;
   float x[N], I[N], e[N];
-  long long t = 0;
+  // the lane's trial: t its index in its job, f its list entry (MULTI), q the
+  // launch's parameters with the job's inputs, outputs and trial offset
+  LcaParams q = p;
+  KeyPair kp{};
+  long long t = 0, f = 0;
   int k = 0;
-  long long f = fetch_trial(p.cursor, true);
-  bool active = f >= 0 && f < p.n;
+  auto bind = [&](long long fi) {
+    if constexpr (MULTI) {
+      const MultiJob& J = s_job[multi_job_of(s_job, tab.n_jobs, fi)];
+      q.I = J.in;
+      q.choice = J.choice;
+      q.step = J.step;
+      q.xout = J.xout;
+      q.trial0 = J.trial0;
+      kp.k.k0 = J.k0;
+      kp.k.k1 = J.k1;
+      f = fi;
+      t = fi - J.start;
+    } else {
+      t = p.perm ? (long long)__ldg(p.perm + fi) : fi;
+    }
+  };
+  auto noise = [&](int kk, float (&out)[N]) {
+    if constexpr (MULTI)
+      L::noise_k(kp, q.trial0 + (uint32_t)t, kk, 0, out);
+    else
+      L::noise(p, p.trial0 + (uint32_t)t, kk, 0, out);
+  };
+  long long fc = fetch_trial(p.cursor, true);
+  bool active = fc >= 0 && fc < p.n;
   if (active) {
-    t = p.perm ? (long long)__ldg(p.perm + f) : f;
-    L::load(p, t, 0, x, I);
-    L::noise(p, p.trial0 + (uint32_t)t, 0, 0, e);
+    bind(fc);
+    L::load(q, t, 0, x, I);
+    noise(0, e);
   }
   while (true) {
     // ---- a chunk of steps
@@ -286,12 +328,12 @@ __global__ void __launch_bounds__(256) lca_compact(LcaParams p) {
       for (int s = 0; s < p.chunk; ++s) {
         if (active) {
           float en[N];
-          L::noise(p, p.trial0 + (uint32_t)t, k + 1, 0, en);
+          noise(k + 1, en);
           int8_t c = -1;
           const bool hit = L::step(p, e, 0, self, x, I, c);
           ++k;
           if (hit || k >= p.max_steps) {
-            L::store(p, t, 0, hit ? c : (int8_t)-1, hit ? k : p.max_steps, x);
+            L::store(q, t, 0, hit ? c : (int8_t)-1, hit ? k : p.max_steps, x);
             active = false;
           }
 #pragma unroll
@@ -319,7 +361,7 @@ __global__ void __launch_bounds__(256) lca_compact(LcaParams p) {
         s_I[i * 256 + d] = I[i];
         s_e[i * 256 + d] = e[i];
       }
-      s_t[d] = t;
+      s_t[d] = MULTI ? f : t;
       s_k[d] = k;
     }
     __syncthreads();
@@ -331,18 +373,21 @@ __global__ void __launch_bounds__(256) lca_compact(LcaParams p) {
         I[i] = s_I[i * 256 + tid];
         e[i] = s_e[i * 256 + tid];
       }
-      t = s_t[tid];
+      if constexpr (MULTI)
+        bind(s_t[tid]);
+      else
+        t = s_t[tid];
       k = s_k[tid];
     }
     // ---- the free lanes take new trials
-    f = fetch_trial(p.cursor, !active);
-    const bool refilled = !active && f >= 0 && f < p.n;
+    fc = fetch_trial(p.cursor, !active);
+    const bool refilled = !active && fc >= 0 && fc < p.n;
     if (refilled) {
       active = true;
-      t = p.perm ? (long long)__ldg(p.perm + f) : f;
+      bind(fc);
       k = 0;
-      L::load(p, t, 0, x, I);
-      L::noise(p, p.trial0 + (uint32_t)t, 0, 0, e);
+      L::load(q, t, 0, x, I);
+      noise(0, e);
     }
     if constexpr (N % 4 == 0) {
       // no trial left to hand out and at most one per warp still running: a
@@ -354,70 +399,17 @@ __global__ void __launch_bounds__(256) lca_compact(LcaParams p) {
             x[i] = s_x[i * 256 + warp];
             I[i] = s_I[i * 256 + warp];
           }
-          lca_warp_trial<N>(p, s_t[warp], s_k[warp], x, I);
+          if constexpr (MULTI) {
+            bind(s_t[warp]);
+            lca_warp_trial<N>(q, kp, t, s_k[warp], x, I);
+          } else {
+            lca_warp_trial<N>(p, p.rk, s_t[warp], s_k[warp], x, I);
+          }
         }
         return;
       }
     }
     if (!__syncthreads_or(active ? 1 : 0)) break;
-  }
-}
-
-// Several jobs of one model in one launch (the serving loop's groups), one
-// lane per trial: a lane that finishes its trial takes the next entry of the
-// concatenated trial list and runs it with that job's inputs, outputs and
-// seed; the steps are lca_batched's, so each trial ends as in a launch of its
-// job alone.
-template <int N>
-__global__ void __launch_bounds__(256) lca_multi(LcaParams p,
-                                                 const __grid_constant__ MultiJobTable tab) {
-  using L = Lca<N, 1>;
-  __shared__ MultiJob s_job[kMaxMultiJobs];
-  copy_jobs(tab, s_job);
-  const int lane = threadIdx.x & 31;
-  const unsigned self = 1u << lane;
-  float x[N], I[N], e[N];
-  LcaParams q = p;
-  KeyPair kp{};
-  long long t = 0;
-  int k = 0;
-  auto begin = [&](long long f) {
-    const MultiJob& J = s_job[multi_job_of(s_job, tab.n_jobs, f)];
-    q.I = J.in;
-    q.choice = J.choice;
-    q.step = J.step;
-    q.xout = J.xout;
-    q.trial0 = J.trial0;
-    kp.k.k0 = J.k0;
-    kp.k.k1 = J.k1;
-    t = f - J.start;
-    k = 0;
-    L::load(q, t, 0, x, I);
-    L::noise_k(kp, q.trial0 + (uint32_t)t, 0, 0, e);
-  };
-  long long f = fetch_trial(p.cursor, true);
-  bool active = f >= 0 && f < p.n;
-  if (active) begin(f);
-  while (__any_sync(kFull, active)) {
-    bool finished = false;
-    if (active) {
-      float en[N];
-      L::noise_k(kp, q.trial0 + (uint32_t)t, k + 1, 0, en);
-      int8_t c = -1;
-      const bool hit = L::step(q, e, 0, self, x, I, c);
-      ++k;
-      if (hit || k >= p.max_steps) {
-        L::store(q, t, 0, hit ? c : (int8_t)-1, hit ? k : p.max_steps, x);
-        finished = true;
-      }
-#pragma unroll
-      for (int i = 0; i < N; ++i) e[i] = en[i];
-    }
-    f = fetch_trial(p.cursor, finished);
-    if (finished) {
-      active = f < p.n;
-      if (active) begin(f);
-    }
   }
 }
 
@@ -465,9 +457,9 @@ cudaError_t launch_n(const LcaParams& p, int mode, const LaunchCfg& cfg, cudaStr
     case 0: {   // block-level compaction, one lane per trial (256 threads)
       if constexpr (N <= 16) {
         const size_t smem = compact_smem(N);
-        const cudaError_t ea = smem_limit((const void*)lca_compact<N>, (int)smem);
+        const cudaError_t ea = smem_limit((const void*)lca_compact<N, false>, (int)smem);
         if (ea != cudaSuccess) return ea;
-        lca_compact<N><<<grid, 256, smem, s>>>(p);
+        lca_compact<N, false><<<grid, 256, smem, s>>>(p, {});
         break;
       }
       return cudaErrorInvalidValue;
@@ -486,19 +478,23 @@ cudaError_t launch_n(const LcaParams& p, int mode, const LaunchCfg& cfg, cudaStr
 
 template <int N>
 cudaError_t launch_multi_n(const LcaParams& p, const MultiJobTable& tab, cudaStream_t s) {
-  int nb = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, lca_multi<N>, 256, 0);
+  const size_t smem = compact_smem(N);
+  const void* fn = (const void*)lca_compact<N, true>;
+  cudaError_t e = smem_limit(fn, (int)smem);
   if (e != cudaSuccess) return e;
+  int nb = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, smem)) != cudaSuccess)
+    return e;
   long long grid = (long long)num_sms() * (nb > 0 ? nb : 1);
   const long long need = (p.n + 255) / 256;   // one lane per trial
   if (grid > need) grid = need;
-  lca_multi<N><<<(unsigned)grid, 256, 0, s>>>(p, tab);
+  lca_compact<N, true><<<(unsigned)grid, 256, smem, s>>>(p, tab);
   return cudaGetLastError();
 }
 
 template <int N>
 void* compact_fn() {
-  return (void*)lca_compact<N>;
+  return (void*)lca_compact<N, false>;
 }
 
 void* kernel_for(int N, int tpt) {

@@ -457,6 +457,10 @@ dg::LcaParams lca_model_params(const dg_model* m) {
   p.max_steps = m->max_steps;
   p.rectify = m->rectify;
   p.two_sided = m->two_sided;
+  const char* e = getenv("DG_LCA_CHUNK");   // steps between compactions
+  p.chunk = e && atoi(e) > 0 ? atoi(e) : 32;
+  const char* tm = getenv("DG_LCA_TAIL");   // trials left in a block before a warp each
+  p.tail_max = tm ? std::max(0, std::min(8, atoi(tm))) : 8;
   return p;
 }
 
@@ -516,12 +520,6 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
     p.k0 = k0;
     p.k1 = k1;
     p.rk = dg::philox_keys(k0, k1);
-    {
-      const char* e = getenv("DG_LCA_CHUNK");   // steps between compactions
-      p.chunk = e && atoi(e) > 0 ? atoi(e) : 32;
-      const char* tm = getenv("DG_LCA_TAIL");   // trials left in a block before a warp each
-      p.tail_max = tm ? std::max(0, std::min(8, atoi(tm))) : 8;
-    }
     p.choice = choice;
     p.step = step;
     p.xout = fs;
@@ -822,7 +820,11 @@ struct Server {
   // job of at most group_job_trials trials gathers later queued jobs of the
   // same model, up to kMaxMultiJobs jobs and kGroupTrials trials in all.
   long long group_job_trials = 1 << 16;
-  static constexpr long long kGroupTrials = 1 << 22;
+  static constexpr long long kGroupTrials = 1 << 23;
+  // Grouped jobs whose host buffers are pinned (mapped into the device's
+  // address space) are read and written by the kernel in place, over the
+  // host link, with no staging copies.
+  bool zero_copy = true;
   static constexpr size_t kGroupScan = 4096;   // queued jobs looked at per group
   uint64_t next_id = 1;
   int64_t n_running = 0, n_done = 0;
@@ -850,6 +852,7 @@ struct Server {
       slot_jobs.emplace_back();
     }
     if (const char* e = getenv("DG_SERVE_GROUP_TRIALS")) group_job_trials = atoll(e);
+    if (const char* e = getenv("DG_SERVE_ZERO_COPY")) zero_copy = atoi(e) != 0;
     th = std::thread([this] { loop(); });
   }
 
@@ -941,17 +944,49 @@ struct Server {
     return DG_OK;
   }
 
-  // Enqueue a group's copies and one multi-job launch on its slot's stream.
+  // The device address of pinned, mapped host memory; null for anything else
+  // (pageable memory, device memory, an unknown pointer).
+  static void* mapped_alias(const void* h) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+      cudaGetLastError();   // not a pointer the runtime knows: clear the error it left
+      return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+  }
+
+  // A run job's buffers as the kernel can use them in place, if all are
+  // pinned and mapped.
+  static bool in_place(const dg_job& j, Staged* out) {
+    const float* in = (const float*)mapped_alias(j.run.trial_params);
+    int8_t* ch = (int8_t*)mapped_alias(j.choice);
+    int32_t* st = (int32_t*)mapped_alias(j.step);
+    float* fs = j.final_state ? (float*)mapped_alias(j.final_state) : nullptr;
+    if (!in || !ch || !st || (j.final_state && !fs)) return false;
+    out->d = j.run;
+    out->d.trial_params = in;
+    out->choice = ch;
+    out->step = st;
+    out->fs = fs;
+    return true;
+  }
+
+  // Enqueue a group's copies (for jobs not used in place) and one multi-job
+  // launch on its slot's stream.
   dg_status launch_group(const std::vector<std::shared_ptr<JobRec>>& grp, cudaStream_t s) {
     const int n = (int)grp.size();
     std::vector<Staged> g(n);
+    std::vector<char> direct(n, 0);
     std::vector<dg_run_desc> d(n);
     std::vector<int8_t*> ch(n);
     std::vector<int32_t*> stp(n);
     std::vector<float*> fs(n);
     for (int i = 0; i < n; ++i) {
-      dg_status st = stage_run(*grp[i], s, &g[i]);
-      if (st != DG_OK) return st;
+      direct[i] = zero_copy && in_place(grp[i]->job, &g[i]);
+      if (!direct[i]) {
+        dg_status st = stage_run(*grp[i], s, &g[i]);
+        if (st != DG_OK) return st;
+      }
       d[i] = g[i].d;
       ch[i] = g[i].choice;
       stp[i] = g[i].step;
@@ -961,7 +996,7 @@ struct Server {
                                    fs.data(), s);
     if (st != DG_OK) return st;
     for (int i = 0; i < n; ++i)
-      if ((st = unstage_run(*grp[i], s, g[i])) != DG_OK) return st;
+      if (!direct[i] && (st = unstage_run(*grp[i], s, g[i])) != DG_OK) return st;
     return DG_OK;
   }
 

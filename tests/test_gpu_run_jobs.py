@@ -132,7 +132,7 @@ def test_run_jobs_arguments(ctx):
         with pytest.raises(RuntimeError):
             B.dg_run_jobs(md, [], [], [])
         with pytest.raises(RuntimeError):
-            B.dg_run_jobs(md, [d] * 65, [c] * 65, [s] * 65)
+            B.dg_run_jobs(md, [d] * 257, [c] * 257, [s] * 257)
         with pytest.raises(RuntimeError):
             B.dg_run_jobs(mp, [d], [c], [s])
         dp = B.run_desc(10, 1, trial_params=dev(h), mode=B.DG_MODE_PLAIN)
@@ -141,18 +141,29 @@ def test_run_jobs_arguments(ctx):
         dn = B.run_desc(10, 1)   # no trial_params
         with pytest.raises(RuntimeError):
             B.dg_run_jobs(md, [dn], [c], [s])
-        B.dg_run_jobs(md, [d] * 64, [c] * 64, [s] * 64)   # 64 jobs is the limit
+        B.dg_run_jobs(md, [d] * 256, [c] * 256, [s] * 256)   # 256 jobs is the limit
     finally:
         B.dg_model_free(md)
         B.dg_model_free(mp)
 
 
-def test_served_small_jobs_grouped_equal_direct_runs(ctx):
+@pytest.mark.parametrize("pinned", [False, True])
+def test_served_small_jobs_grouped_equal_direct_runs(ctx, pinned):
     """Many small DDM and LCA jobs of several models submitted at once: the
     serving loop groups them into multi-job launches; every job's outputs
-    (final states included) equal a direct dg_run of the job."""
+    (final states included) equal a direct dg_run of the job. With pinned host
+    buffers the kernels read and write them in place."""
+    import torch
     from paper_2110_15425_gb300 import binding as B
     rng = np.random.default_rng(12)
+    keep = []
+
+    def buf(a):
+        if not pinned:
+            return a
+        t = torch.from_numpy(a).pin_memory()
+        keep.append(t)
+        return t.numpy()
     models = dict(ddm=B.compose_ddm(ctx), ddm2=B.compose_ddm(ctx, dt=2e-3, sigma=0.8),
                   lca4=B.compose_lca(ctx, 4), lca8=B.compose_lca(ctx, 8))
     try:
@@ -161,16 +172,16 @@ def test_served_small_jobs_grouped_equal_direct_runs(ctx):
             k = ["ddm", "ddm2", "lca4", "lca8"][int(rng.integers(4))]
             n = int(rng.integers(1, 12000))
             N = 1 if k.startswith("ddm") else int(k[3:])
-            h = _inputs("ddm" if N == 1 else "lca", n, 200 + i, N)
+            h = buf(_inputs("ddm" if N == 1 else "lca", n, 200 + i, N))
             j = B.dg_job()
             j.model = models[k].value
             j.run.n_trials = n
             j.run.seed = int(rng.integers(1, 2 ** 40))
             j.run.trial_offset = int(rng.integers(0, 10 ** 6))
             j.run.trial_params = h.ctypes.data
-            ch = np.zeros(n, np.int8)
-            st = np.zeros(n, np.int32)
-            fs = np.zeros(n * N, np.float32) if i % 3 == 0 else None
+            ch = buf(np.full(n, 9, np.int8))
+            st = buf(np.full(n, -9, np.int32))
+            fs = buf(np.zeros(n * N, np.float32)) if i % 3 == 0 else None
             j.choice = ch.ctypes.data
             j.step = st.ctypes.data
             if fs is not None:
