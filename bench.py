@@ -1083,6 +1083,31 @@ def _plain_job(B, rec, stream):
     stream.synchronize()
 
 
+def _tune_mix(B, prepared, stream):
+    """Tune the launch shapes of the mix's size buckets before serving it, as a
+    deployment would from its tuning cache: one batched run per (kind, trial
+    count bucket) on this thread (the serving thread never times shapes)."""
+    seen = set()
+    for rec in prepared:
+        key = (rec["kind"], int(math.ceil(math.log2(max(rec["n"], 1)))))
+        if key in seen:
+            continue
+        seen.add(key)
+        for d, h in zip(rec["dev_in"], rec["host_in"]):
+            d.copy_(h, non_blocking=True)
+        if rec["kind"] == "grid":
+            pos, l0, l1, l2 = rec["dev_in"]
+            B.dg_grid_search(rec["model"], B.grid_desc([l0, l1, l2], pos, rec["seed"]),
+                             rec["dev_out"][0], stream=stream)
+        else:
+            x = rec["dev_in"][0]
+            d = (B.run_desc(rec["n"], rec["seed"], cond_inputs=x, n_cond=rec["n_cond"],
+                            cond_block=rec["cond_block"]) if rec["cond"] else
+                 B.run_desc(rec["n"], rec["seed"], trial_params=x))
+            B.dg_run(rec["model"], d, rec["dev_out"][0], rec["dev_out"][1], stream=stream)
+    stream.synchronize()
+
+
 def _trial_steps(prepared):
     return sum(r["steps"] if r["kind"] == "grid" else int(r["host_out"][1].numpy().sum())
                for r in prepared)
@@ -1172,11 +1197,14 @@ def served_mix(B, W, torch, ctx, step, n_jobs=SERVE_JOBS, seed=7):
     prepared = _mix(B, W, torch, step, n_jobs, seed)
     stream = torch.cuda.Stream()
     zero = [0.0] * n_jobs
+    with torch.cuda.stream(stream):
+        _tune_mix(B, prepared, stream)
     # warm-up: the serving pool and the plain form's per-stream scratch
     _serve(B, ctx, prepared, zero)
     with torch.cuda.stream(stream):
         _plain(B, prepared, zero, stream)
     steps = _trial_steps(prepared)
+    untuned0 = B.dg_tune_stats(ctx)[1]
     lat_s, wall_s = _serve(B, ctx, prepared, zero)
     with torch.cuda.stream(stream):
         lat_p, wall_p = _plain(B, prepared, zero, stream)
@@ -1193,7 +1221,12 @@ def served_mix(B, W, torch, ctx, step, n_jobs=SERVE_JOBS, seed=7):
                 "plain": _lat_stats(lp, wp, n_jobs, steps)}
     at_served = at(0.7 * cap_s)
     at_plain = at(0.7 * cap_p)
+    tuned_keys, untuned1 = B.dg_tune_stats(ctx)
     out = dict(at_served["served"])
+    # the serving thread never times launch shapes: served launches whose size
+    # bucket had no tuned shape ran the default one
+    out["tuner"] = {"tuned_keys": tuned_keys,
+                    "untuned_launches_in_served_runs": untuned1 - untuned0}
     out.update({
         "jobs": n_jobs, "mix": "stroop/ddm/lca8/grid/wide, trials log-uniform 1e3-1e6",
         "arrival_rate_per_s": at_served["arrival_rate_per_s"],

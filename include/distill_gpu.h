@@ -528,6 +528,12 @@ dg_status dg_submit(dg_ctx* ctx, const dg_job* job, uint64_t* ticket);
    waited for successfully once. */
 dg_status dg_wait(dg_ctx* ctx, uint64_t ticket, int32_t timeout_ms, dg_job_result* result);
 
+/* Autotuner counters: launch-shape keys (model kind, size bucket) with a tuned
+   shape, and launches so far that ran the default shape because their key had
+   none and tuning was not allowed where they ran (the serving thread and graph
+   capture never time shapes). Either pointer may be NULL. */
+dg_status dg_tune_stats(dg_ctx* ctx, int64_t* tuned_keys, int64_t* untuned_launches);
+
 /* Serving counters: jobs queued, running, done; device bytes in use. */
 dg_status dg_serve_stats(dg_ctx* ctx, int64_t* queued, int64_t* running, int64_t* done,
                          uint64_t* bytes_in_use);

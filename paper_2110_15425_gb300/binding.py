@@ -116,7 +116,7 @@ EXPORTS = [
     "dg_batch_launch", "dg_batch_kernels", "dg_batch_free", "dg_submit", "dg_wait", "dg_serve_stats",
     "dg_grid_search_noalloc", "dg_stream_status", "dg_selftest_wait_timeout",
     "dg_argmax_f64_reservoir", "dg_grid_refine", "dg_run_episodes", "dg_selftest_pair_sum",
-    "dg_grid_search_batch", "dg_model_weights", "dg_run_jobs",
+    "dg_grid_search_batch", "dg_model_weights", "dg_run_jobs", "dg_tune_stats",
 ]
 
 _lib = None
@@ -152,6 +152,7 @@ def _declare(L):
         "dg_grid_search_noalloc": [P, C.POINTER(dg_grid_desc), P, P, P],
         "dg_grid_search_batch": [P, i32, C.POINTER(dg_grid_desc), P, P, P],
         "dg_run_jobs": [P, i32, C.POINTER(dg_run_desc), P, P, P, P],
+        "dg_tune_stats": [P, P, P],
         "dg_stream_status": [P, P],
         "dg_selftest_wait_timeout": [P, i32, P],
         "dg_selftest_pair_sum": [P, i64, i32, i32, P, P],
@@ -252,6 +253,13 @@ def dg_model_info(model):
 def dg_run(model, desc, choice, step, final_state=None, stream=None):
     check(lib().dg_run(model, C.byref(desc), ptr(choice), ptr(step), ptr(final_state),
                        stream_handle(stream)))
+
+
+def dg_tune_stats(ctx):
+    """(tuned launch-shape keys, launches that ran an untuned default shape)."""
+    a, b = C.c_int64(), C.c_int64()
+    check(lib().dg_tune_stats(ctx, C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def dg_run_jobs(model, descs, choices, steps, final_states=None, stream=None):

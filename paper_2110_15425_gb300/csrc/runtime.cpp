@@ -99,6 +99,9 @@ struct dg_ctx {
   std::map<std::string, dg::LaunchCfg> tuned;
   std::string tune_file;
   bool autotune = true;
+  // launches that ran a default shape because their key had no tuned shape
+  // and tuning was not allowed there (serving thread, graph capture)
+  std::atomic<int64_t> untuned{0};
   std::unique_ptr<Server> server;
   std::mutex server_mu;
 };
@@ -297,6 +300,7 @@ dg_status autotune(dg_ctx* ctx, const std::string& key, const std::vector<dg::La
     }
   }
   if (!ctx->autotune || t_no_tune || capturing(s) || cands.size() == 1) {
+    if (ctx->autotune && cands.size() > 1) ctx->untuned.fetch_add(1);
     *chosen = cands.front();
     return DG_OK;
   }
@@ -2169,6 +2173,16 @@ dg_status dg_wait(dg_ctx* ctx, uint64_t ticket, int32_t timeout_ms, dg_job_resul
   }
   sv->jobs.erase(ticket);
   if (r->status != DG_OK) return fail((dg_status)r->status, "job %llu failed", (unsigned long long)ticket);
+  return DG_OK;
+}
+
+dg_status dg_tune_stats(dg_ctx* ctx, int64_t* tuned_keys, int64_t* untuned_launches) {
+  if (!ctx) return fail(DG_E_ARG, "dg_tune_stats: null ctx");
+  if (tuned_keys) {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    *tuned_keys = (int64_t)ctx->tuned.size();
+  }
+  if (untuned_launches) *untuned_launches = ctx->untuned.load();
   return DG_OK;
 }
 
