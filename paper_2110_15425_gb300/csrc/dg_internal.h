@@ -160,6 +160,18 @@ struct NetParams {
 };
 cudaError_t launch_net(const NetParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
 
+// One lane per trial for networks of at most kLaneMaxU logistic units and no
+// DDM nodes: the incoming-edge table as a dense matrix (W[u][v] the weight of
+// the edge from unit v into unit u, 0 where there is none), passed by value.
+constexpr int kLaneMaxU = 8;
+struct NetDense {
+  float W[kLaneMaxU][kLaneMaxU];
+  float gain[kLaneMaxU], bias[kLaneMaxU];
+  float rate, noise, thr;
+  int stop_off, stop_size, max_steps;
+};
+cudaError_t launch_net_lane(const NetParams& p, const NetDense& q, cudaStream_t s);
+
 // --------------------------------------------------- wide network (tensor cores) ---
 struct WideParams {
   const float* w_in;             // [H][S + T] FP32: stimulus and task weights side by side

@@ -440,6 +440,13 @@ std::vector<dg::LaunchCfg> grid_candidates(long long n_cand, int lanes) {
 
 // ---------------------------------------------------------- run paths ---
 
+// Small networks without DDM nodes run one lane per trial unless
+// DG_NET_LANE=0 (then a lane group per trial, as networks with DDM nodes do).
+bool net_lane_enabled() {
+  const char* e = getenv("DG_NET_LANE");
+  return !e || atoi(e) != 0;
+}
+
 // The model's part of a DDM or LCA launch (the per-call part is set by the caller).
 dg::DdmParams ddm_model_params(const dg_model* m) {
   dg::DdmParams p{};
@@ -584,6 +591,24 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
     p.yout = fs;
     p.cursor = mode == DG_MODE_BATCHED ? sc->cursor() : nullptr;
     if (mode == DG_MODE_BATCHED) DG_CUDA(cudaMemsetAsync(sc->cursor(), 0, 8, s));
+    const dg::NetLayout& L = m->layout;
+    if (mode == DG_MODE_BATCHED && L.n_ddm == 0 && L.U <= dg::kLaneMaxU && net_lane_enabled()) {
+      dg::NetDense q{};
+      for (int u = 0; u < L.U; ++u) {
+        for (int d = 0; d < L.D; ++d)
+          if (L.w[u][d] != 0.f) q.W[u][L.src[u][d]] = L.w[u][d];
+        q.gain[u] = L.gain[u];
+        q.bias[u] = L.bias[u];
+      }
+      q.rate = L.rate;
+      q.noise = L.noise;
+      q.thr = L.stop_threshold;
+      q.stop_off = L.stop_off;
+      q.stop_size = L.stop_size;
+      q.max_steps = L.max_steps;
+      DG_CUDA(dg::launch_net_lane(p, q, s));
+      return DG_OK;
+    }
     DG_CUDA(dg::launch_net(p, mode, dg::LaunchCfg{}, s));
     return DG_OK;
   }
@@ -1377,6 +1402,29 @@ dg_status compose_transfer(dg_model* m, const dg_mechanism* mechs, int n_mech,
           ++deg[dst];
         }
       }
+  }
+  // each unit's incoming edges in sender order, one edge per sender (the
+  // weights of repeated senders added): every form sums the same terms in the
+  // same order, the one-lane form over a dense row of senders
+  for (int u = 0; u < U; ++u) {
+    std::vector<std::pair<int, double>> row;
+    for (int d = 0; d < deg[u]; ++d) row.emplace_back((int)L.src[u][d], (double)L.w[u][d]);
+    std::stable_sort(row.begin(), row.end(),
+                     [](const std::pair<int, double>& a, const std::pair<int, double>& b) {
+                       return a.first < b.first;
+                     });
+    int n = 0;
+    for (size_t i = 0; i < row.size(); ++i) {
+      if (n > 0 && row[(size_t)n - 1].first == row[i].first)
+        row[(size_t)n - 1].second += row[i].second;
+      else
+        row[(size_t)n++] = row[i];
+    }
+    for (int d = 0; d < dg::kNetMaxInDegree; ++d) {
+      L.src[u][d] = d < n ? (int8_t)row[(size_t)d].first : (int8_t)0;
+      L.w[u][d] = d < n ? (float)row[(size_t)d].second : 0.f;
+    }
+    deg[u] = n;
   }
   L.D = 0;
   for (int u = 0; u < U; ++u) L.D = std::max(L.D, deg[u]);

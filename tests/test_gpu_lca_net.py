@@ -184,3 +184,61 @@ def test_network_with_feedback(ctx, orc, threads):
     ref = _net_ref(orc, w, 700, threads)
     compare_decisions(c, s, ref, "feedback")
     assert rel_err(y, ref["y"], 1e-2) < FLOAT_RTOL
+
+
+def _random_net(seed, sizes, n_in=3, dup=False):
+    """A layered network with an input layer, logistic layers of the given
+    sizes, feed-forward and recurrent edges (and, with dup, a second
+    projection between the same layers, whose weights the library adds)."""
+    rng = np.random.default_rng(seed)
+    layers = [dict(size=n_in, input=True)] + [
+        dict(size=s, bias=float(rng.uniform(-1, 1)), gain=float(rng.uniform(0.5, 2)))
+        for s in sizes]
+    projections = [(0, 1, rng.uniform(-2, 2, (sizes[0], n_in)).astype(np.float32))]
+    for i in range(1, len(sizes)):
+        projections.append((i, i + 1, rng.uniform(-3, 3, (sizes[i], sizes[i - 1])).astype(np.float32)))
+    last = len(sizes)
+    projections.append((last, 1, rng.uniform(-1, 1, (sizes[0], sizes[-1])).astype(np.float32)))
+    projections.append((last, last, rng.uniform(-1, 1, (sizes[-1], sizes[-1])).astype(np.float32)))
+    if dup:
+        projections.append((1, last if last > 1 else 1,
+                            rng.uniform(-1, 1, (sizes[-1], sizes[0])).astype(np.float32)))
+    cond = rng.uniform(0, 1, (5, n_in)).astype(np.float32)
+    return dict(layers=layers, projections=projections, cond_inputs=cond, cond_block=3,
+                n_trials=1500, rate=0.2, noise_sd=0.05, stop_layer=last, stop_threshold=0.25,
+                max_steps=400, seed=seed + 1)
+
+
+NETS = [(11, [2], False), (12, [1, 2], True), (13, [3], False), (14, [3, 2], False),
+        (15, [4, 3], True), (16, [2, 2, 4], False), (17, [4, 4], True), (18, [1, 3], False)]
+
+
+@pytest.mark.parametrize("seed,sizes,dup", NETS)
+def test_net_lane_form_equals_group_form_and_oracle(ctx, orc, threads, monkeypatch, seed, sizes,
+                                                    dup):
+    """Networks of 2 to 8 logistic units: the one-lane-per-trial form gives the
+    lane-group form's results bit for bit (outputs included) and the oracle's
+    decisions."""
+    w = _random_net(seed, sizes, dup=dup)
+    a = _net(ctx, w, 0)
+    monkeypatch.setenv("DG_NET_LANE", "0")
+    b = _net(ctx, w, 0)
+    for u, v in zip(a, b):
+        assert np.array_equal(u.view(np.uint8), v.view(np.uint8)), (seed, sizes)
+    ref = _net_ref(orc, w, w["n_trials"], threads)
+    compare_decisions(a[0], a[1], ref, f"lane form {sizes}")
+    assert rel_err(a[2], ref["y"], 1e-2) < FLOAT_RTOL
+
+
+def test_stroop_lane_form_equals_group_form(ctx, monkeypatch):
+    from paper_2110_15425_gb300 import workloads as W
+    for ws in (0, 4):
+        w = W.stroop_small(weight_seed=ws)
+        a = _net(ctx, w, 0)
+        monkeypatch.setenv("DG_NET_LANE", "0")
+        b = _net(ctx, w, 0)
+        monkeypatch.delenv("DG_NET_LANE")
+        c = _net(ctx, w, 1)
+        for u, v, x in zip(a, b, c):
+            assert np.array_equal(u.view(np.uint8), v.view(np.uint8))
+            assert np.array_equal(u.view(np.uint8), x.view(np.uint8))
