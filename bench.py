@@ -897,6 +897,17 @@ def extensions(B, W, torch, ctx, grid_ms):
             "frac_alu": evals * OPS_PER_UNIT["grid"] / (ms_batch / 1e3) / PEAK_OPS[0],
             "ms_one_call_each": ms_single,
             "candidates_per_s_one_call_each": nb * nc / (ms_single / 1e3)}
+        # a larger batch: 64 searches (the ramp and drain of one launch spread wider)
+        nb4 = 64
+        bw4 = [W.predator_prey(pos_seed=3 + i, noise_seed=13 + i) for i in range(nb4)]
+        bkeep4 = [([cuda(l) for l in w_["levels"]], cuda(w_["pos"])) for w_ in bw4]
+        bdesc4 = [B.grid_desc(lv_, pos_, w_["seed"]) for (lv_, pos_), w_ in zip(bkeep4, bw4)]
+        bres4 = torch.zeros(nb4 * 3, dtype=torch.float64, device="cuda")
+        B.dg_grid_search_batch(pp, bdesc4, bres4)
+        ms4 = _time_ms(torch, lambda: B.dg_grid_search_batch(pp, bdesc4, bres4))
+        out["grid_search_batch"]["searches_64"] = {
+            "ms": ms4, "candidates_per_s": nb4 * nc / (ms4 / 1e3),
+            "frac_alu": nb4 * nc * 64 * OPS_PER_UNIT["grid"] / (ms4 / 1e3) / PEAK_OPS[0]}
         # reservoir tie-break: the 30^3 search with either rule
         res0 = torch.zeros(3, dtype=torch.float64, device="cuda")
         d0 = B.grid_desc(lv, pos, g["seed"])

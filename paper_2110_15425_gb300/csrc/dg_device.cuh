@@ -97,6 +97,11 @@ __device__ __forceinline__ float approx_rsqrt(float x) {
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+__device__ __forceinline__ float approx_sqrt(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ float approx_sin(float x) {
   float r;
   asm("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));

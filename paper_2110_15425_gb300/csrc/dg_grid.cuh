@@ -109,11 +109,13 @@ __device__ __forceinline__ void warp_pair_sum(float& hi, float& lo) {
   lo = __shfl_sync(kFull, lo, 0);
 }
 
-// unit(v), with unit(0) = 0
+// unit(v), with unit(v) = 0 for |v|^2 below the smallest normal number (the
+// hardware reciprocal square root, flush-to-zero form: a position difference
+// that small is zero for this model)
 __device__ __forceinline__ void unit2(float vx, float vy, float& ox, float& oy) {
   const float n2 = vx * vx + vy * vy;
-  if (n2 > 0.f) {
-    const float r = rsqrtf(n2);
+  if (n2 >= FLT_MIN) {
+    const float r = approx_rsqrt(n2);
     ox = vx * r;
     oy = vy * r;
   } else {
@@ -150,7 +152,7 @@ __device__ __forceinline__ float pp_outcome_at(const PhiloxKeys& rk, uint32_t tr
   pp_act(rk, trial, cand, block0, X, sd0, sd1, sd2, weight, ax, ay);
   const float nx = (X[0] + ax) - X[4];
   const float ny = (X[1] + ay) - X[5];
-  return -sqrtf(nx * nx + ny * ny) - cost;
+  return -approx_sqrt(nx * nx + ny * ny) - cost;
 }
 
 }  // namespace dg
