@@ -455,23 +455,6 @@ __global__ void __launch_bounds__(BLay<H>::THREADS, 1) wide_block_kernel(WidePar
       }
     }
     // (an empty slot's rows keep earlier values: their products are not read)
-    // the response units' noise of every row, sigma eps, drawn by all threads:
-    // thread (row, Philox block i, pair h) computes block i of the row's step
-    // (both pairs of a block are drawn by two threads) and its h-th Box-Muller pair
-    for (int w = tid; w < 4 * kRows * 2; w += L::THREADS) {
-      const int row = w & (kRows - 1), i = (w >> 7) & 3, h = w >> 9;
-      const int rs = row & (kSlots - 1), rj = row / kSlots;
-      const long long rt = sh.slot[rs];
-      const int rst = sh.kstep[rs] + rj;
-      float z0 = 0.f, z1 = 0.f;
-      if (rt >= 0 && rst < p.max_steps) {
-        const uint4 wd = noise_block_rk(p.rk, p.trial0 + (uint32_t)rt, 0u,
-                                        (uint32_t)rst * (uint32_t)(L::U / 4) + (uint32_t)(H / 4 + i));
-        box_muller(h ? wd.z : wd.x, h ? wd.w : wd.y, z0, z1);
-      }
-      *reinterpret_cast<float2*>(rnoise + row * 20 + 4 * i + 2 * h) =
-          make_float2(p.noise * z0, p.noise * z1);
-    }
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
@@ -508,6 +491,25 @@ __global__ void __launch_bounds__(BLay<H>::THREADS, 1) wide_block_kernel(WidePar
                                          (uint32_t)hq));
       pre_ok = true;
     }
+    // and the response units' noise of every row, sigma eps, drawn by all
+    // threads: thread (row, Philox block i, pair h) computes block i of the
+    // row's step (both pairs of a block are drawn by two threads) and its h-th
+    // Box-Muller pair
+    for (int w = tid; w < 4 * kRows * 2; w += L::THREADS) {
+      const int row = w & (kRows - 1), i = (w >> 7) & 3, h = w >> 9;
+      const int rs = row & (kSlots - 1), rj = row / kSlots;
+      const long long rt = sh.slot[rs];
+      const int rst = sh.kstep[rs] + rj;
+      float z0 = 0.f, z1 = 0.f;
+      if (rt >= 0 && rst < p.max_steps) {
+        const uint4 wd = noise_block_rk(p.rk, p.trial0 + (uint32_t)rt, 0u,
+                                        (uint32_t)rst * (uint32_t)(L::U / 4) + (uint32_t)(H / 4 + i));
+        box_muller(h ? wd.z : wd.x, h ? wd.w : wd.y, z0, z1);
+      }
+      *reinterpret_cast<float2*>(rnoise + row * 20 + 4 * i + 2 * h) =
+          make_float2(p.noise * z0, p.noise * z1);
+    }
+    __syncthreads();   // every row's response noise is in shared memory
 
     // ---------------------------------------------------------------- 3.
     if (tid < kRows) {
