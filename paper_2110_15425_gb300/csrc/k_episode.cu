@@ -280,17 +280,16 @@ cudaError_t launch_episode_init(const EpisodeParams& p, cudaStream_t s) {
 
 cudaError_t launch_episode_step(const EpisodeParams& p, cudaStream_t s) {
   const bool narrow = grid_lanes(p.L) == 8;
-  static int blocks[2] = {0, 0};
-  if (blocks[narrow] == 0) {
-    int nb = 0;
-    if (narrow)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, episode_step<8>, 256, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, episode_step<32>, 256, 0);
-    blocks[narrow] = num_sms() * (nb > 0 ? nb : 1);
-  }
+  // resident blocks of the current device (asked per launch: a process may
+  // drive GPUs of different sizes)
+  int nb = 0;
+  const cudaError_t e =
+      narrow ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, episode_step<8>, 256, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, episode_step<32>, 256, 0);
+  if (e != cudaSuccess) return e;
+  const long long blocks = (long long)num_sms() * (nb > 0 ? nb : 1);
   long long g = (long long)p.E * p.cpe;
-  if (g > blocks[narrow]) g = blocks[narrow];
+  if (g > blocks) g = blocks;
   if (narrow)
     episode_step<8><<<(unsigned)g, 256, 0, s>>>(p);
   else
