@@ -237,17 +237,19 @@ dg_status dg_model_info(const dg_model* model, int32_t* kind, int32_t* state_siz
 dg_status dg_run(dg_model* model, const dg_run_desc* desc, int8_t* choice, int32_t* step,
                  float* final_state, void* stream);
 
-/* Several jobs of one DDM or LCA model in one persistent launch: Sec. 3.6's
+/* Several jobs of one DDM, LCA or small TRANSFER model (at most 8 logistic
+   units, no DDM nodes) in one persistent launch: Sec. 3.6's
    parallel evaluations taken across jobs as well as within one, so that jobs
    too small to fill the GPU share its lanes and the launch's ramp and drain.
    Job i is exactly dg_run(model, &descs[i], choice[i], step[i],
    final_state ? final_state[i] : NULL): the same trials, random streams and
    results, bit for bit. Each desc is checked as dg_run checks it and must use
    DG_MODE_BATCHED; jobs may differ in n_trials (0 allowed), trial_offset, seed
-   and trial_params. choice, step (and final_state when not NULL) are host
+   and trial_params (networks: cond_inputs, n_cond and cond_block). choice, step
+   (and final_state when not NULL) are host
    arrays of n_jobs device pointers; an entry of final_state may be NULL.
    n_jobs: 1 .. 256; at most 2^31 - 1 trials in all.
-   Errors: DG_E_ARG, DG_E_UNSUPPORTED (not a DDM or LCA model), DG_E_CUDA. */
+   Errors: DG_E_ARG, DG_E_UNSUPPORTED (another model), DG_E_CUDA. */
 dg_status dg_run_jobs(dg_model* model, int32_t n_jobs, const dg_run_desc* descs,
                       int8_t* const* choice, int32_t* const* step, float* const* final_state,
                       void* stream);
@@ -510,12 +512,13 @@ typedef struct {
 /* Queue a job; returns at once with a ticket. The serving loop admits queued
    jobs in arrival order while the HBM budget has room, runs admitted jobs
    concurrently (each launch on its own stream, continuous batching), and frees
-   a job's memory when its results are on the host. A batched DDM or LCA job of
-   at most 65,536 trials (environment DG_SERVE_GROUP_TRIALS; 0 turns this off)
-   takes later queued batched DDM or LCA jobs of the same model, up to that size
+   a job's memory when its results are on the host. A batched job of a model
+   that dg_run_jobs takes, of at most 65,536 trials (environment
+   DG_SERVE_GROUP_TRIALS; 0 turns this off), takes later queued batched jobs of
+   the same model, up to that size
    each, 256 jobs and 2^23 trials in all, into one dg_run_jobs launch; results
-   are those of the jobs run alone. A grouped job whose trial_params, choice,
-   step (and final_state) are all pinned host memory (cudaHostAlloc, or
+   are those of the jobs run alone. A grouped job whose trial_params (or
+   cond_inputs), choice, step (and final_state) are all pinned host memory (cudaHostAlloc, or
    cudaHostRegister'd) is read and written by the kernel in place through the
    memory's device mapping, without staging copies (DG_SERVE_ZERO_COPY=0 turns
    this off).

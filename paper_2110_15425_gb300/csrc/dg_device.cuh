@@ -195,6 +195,16 @@ __device__ __forceinline__ void copy_jobs(const MultiJobTable& tab, MultiJob* s_
   __syncthreads();
 }
 
+// The job-table parameter of a kernel that runs one job or several.
+template <bool MULTI>
+struct TableOf {
+  using type = MultiJobTable;
+};
+template <>
+struct TableOf<false> {   // a single job carries no table
+  struct type {};
+};
+
 __device__ __forceinline__ int multi_job_of(const MultiJob* s_job, int n_jobs, long long f) {
   int lo = 0, hi = n_jobs - 1;
   while (lo < hi) {

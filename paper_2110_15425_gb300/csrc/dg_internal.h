@@ -40,16 +40,18 @@ DG_HD inline PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
 // concatenation of its jobs' trials, job j holding list entries
 // start .. start + n - 1; each job has its own inputs, outputs, seed and
 // trial offset (the model's parameters are the launch's).
-constexpr int kMaxMultiJobs = 256;   // table: 16 KB of kernel parameter space
+constexpr int kMaxMultiJobs = 256;   // table: 18 KB of kernel parameter space
 struct MultiJob {
   long long start;
   long long n;
-  const float* in;               // DDM: [2][n] (A row, z row); LCA: [n][N]
+  const float* in;               // DDM: [2][n] (A row, z row); LCA: [n][N];
+                                 // small network: [n_cond][input units]
   int8_t* choice;
   int32_t* step;
   float* xout;                   // may be null
   uint32_t trial0;
   uint32_t k0, k1;
+  int32_t n_cond, cond_block;    // small network: condition of trial g is (g / cond_block) % n_cond
   uint32_t pad;
 };
 // The jobs of one multi-job launch, passed by value as a kernel parameter.
@@ -171,6 +173,10 @@ struct NetDense {
   int stop_off, stop_size, max_steps;
 };
 cudaError_t launch_net_lane(const NetParams& p, const NetDense& q, cudaStream_t s);
+// Trials of several jobs of one such network in one launch (p: the model's
+// part, p.n the total of the jobs' trials and p.cursor).
+cudaError_t launch_net_lane_multi(const NetParams& p, const NetDense& q, const MultiJobTable& tab,
+                                  cudaStream_t s);
 
 // --------------------------------------------------- wide network (tensor cores) ---
 struct WideParams {

@@ -262,15 +262,6 @@ __device__ void lca_warp_trial(const LcaParams& p, const Keys& rk, long long t, 
 // one list over the jobs in order; a lane holds its trial's list index f and
 // binds the trial's job (inputs, outputs, seed, trial offset) when it takes
 // the trial on, so a trial ends exactly as in a launch of its job alone.
-template <bool MULTI>
-struct TableOf {
-  using type = MultiJobTable;
-};
-template <>
-struct TableOf<false> {   // a single job carries no table
-  struct type {};
-};
-
 template <int N, bool MULTI>
 __global__ void __launch_bounds__(256) lca_compact(
     LcaParams p, const __grid_constant__ typename TableOf<MULTI>::type tab) {

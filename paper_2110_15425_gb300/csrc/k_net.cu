@@ -284,8 +284,15 @@ __global__ void __launch_bounds__(256) net_group(NetParams p) {
 //
 // SS > 0: the stop layer is the last SS units (known when compiling: the stop
 // test and the kept outputs cover those units only); SS = 0: any range.
-template <int U, int SS>
-__global__ void __launch_bounds__(128) net_lane(NetParams p, const __grid_constant__ NetDense q) {
+// MULTI: the trials of several jobs of the network (the serving loop's
+// groups), one list over the jobs in order; a lane binds its trial's job
+// (condition table, outputs, seed, trial offset) when it takes the trial on.
+template <int U, int SS, bool MULTI>
+__global__ void __launch_bounds__(128) net_lane(NetParams p, const __grid_constant__ NetDense q,
+                                               const __grid_constant__
+                                               typename TableOf<MULTI>::type tab) {
+  __shared__ MultiJob s_job[MULTI ? kMaxMultiJobs : 1];
+  if constexpr (MULTI) copy_jobs(tab, s_job);
   constexpr int W = (U % 2 == 0) ? 2 : 4;   // steps per window: W U normals in whole blocks
   constexpr int NZ = W * U;
   const float rate = q.rate, keep = 1.0f - q.rate, noise = q.noise, thr = q.thr;
@@ -299,12 +306,19 @@ __global__ void __launch_bounds__(128) net_lane(NetParams p, const __grid_consta
   long long t = 0;
   int k = 0;
   uint32_t trial = 0;
+  NetParams pj = p;   // the lane's job: the launch's own, or bound from the table
+  KeyPair kp{};
   // the normals of steps k0 .. k0 + W - 1 (k0 a multiple of W)
   auto draw = [&](int k0, float (&out)[NZ]) {
     const uint32_t b0 = (uint32_t)k0 * (uint32_t)U / 4u;
 #pragma unroll
     for (int j = 0; j < NZ / 4; ++j) {
-      const float4 v = normals4(noise_block_rk(p.rk, trial, 0u, b0 + (uint32_t)j));
+      uint4 w;
+      if constexpr (MULTI)
+        w = noise_block_rk(kp, trial, 0u, b0 + (uint32_t)j);
+      else
+        w = noise_block_rk(p.rk, trial, 0u, b0 + (uint32_t)j);
+      const float4 v = normals4(w);
       out[4 * j] = v.x;
       out[4 * j + 1] = v.y;
       out[4 * j + 2] = v.z;
@@ -312,14 +326,28 @@ __global__ void __launch_bounds__(128) net_lane(NetParams p, const __grid_consta
     }
   };
   auto begin = [&](long long tt) {
-    t = tt;
+    if constexpr (MULTI) {
+      const MultiJob& J = s_job[multi_job_of(s_job, tab.n_jobs, tt)];
+      pj.cond = J.in;
+      pj.n_cond = J.n_cond;
+      pj.cond_block = J.cond_block;
+      pj.trial0 = J.trial0;
+      pj.choice = J.choice;
+      pj.step = J.step;
+      pj.yout = J.xout;
+      kp.k.k0 = J.k0;
+      kp.k.k1 = J.k1;
+      t = tt - J.start;
+    } else {
+      t = tt;
+    }
     k = 0;
-    trial = p.trial0 + (uint32_t)t;
+    trial = pj.trial0 + (uint32_t)t;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       s[u] = 0.f;
       y[u] = lg[u](0.f);
-      netc[u] = const_net(p, p.n_in, t, u);
+      netc[u] = const_net(pj, p.n_in, t, u);
     }
     draw(0, z);
   };
@@ -385,14 +413,14 @@ __global__ void __launch_bounds__(128) net_lane(NetParams p, const __grid_consta
       draw(k + W, z);   // k advanced by W: the window after zn's
       steps(zn);
       if (finished) {
-        if (p.yout) {
+        if (pj.yout) {
 #pragma unroll
           for (int u = SS > 0 ? U - SS : 0; u < U; ++u)
             if (SS > 0 || (u >= stop_off && u < stop_end))
-              p.yout[(size_t)t * p.state_size + (u - stop_off)] = ry[u];
+              pj.yout[(size_t)t * p.state_size + (u - stop_off)] = ry[u];
         }
-        p.choice[t] = rc;
-        p.step[t] = rs;
+        pj.choice[t] = rc;
+        pj.step[t] = rs;
       }
     }
     f = fetch_trial(p.cursor, finished);
@@ -403,10 +431,12 @@ __global__ void __launch_bounds__(128) net_lane(NetParams p, const __grid_consta
   }
 }
 
-template <int U, int SS>
-cudaError_t launch_lane_us(const NetParams& p, const NetDense& q, cudaStream_t s) {
+template <int U, int SS, bool MULTI>
+cudaError_t launch_lane_us(const NetParams& p, const NetDense& q, const MultiJobTable* tab,
+                           cudaStream_t s) {
   int nb = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, net_lane<U, SS>, 128, 0);
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, net_lane<U, SS, MULTI>, 128, 0);
   if (e != cudaSuccess) return e;
   // small jobs: blocks of one warp spread over the SMs (a lane's step is a
   // chain of a few hundred instructions; warps sharing a scheduler slow it)
@@ -414,18 +444,38 @@ cudaError_t launch_lane_us(const NetParams& p, const NetDense& q, cudaStream_t s
   long long grid = (long long)num_sms() * (nb > 0 ? nb : 1) * (128 / block);
   const long long need = (p.n + block - 1) / block;
   if (grid > need) grid = need;
-  net_lane<U, SS><<<(unsigned)grid, block, 0, s>>>(p, q);
+  if constexpr (MULTI)
+    net_lane<U, SS, true><<<(unsigned)grid, block, 0, s>>>(p, q, *tab);
+  else
+    net_lane<U, SS, false><<<(unsigned)grid, block, 0, s>>>(p, q, {});
   return cudaGetLastError();
 }
 
-template <int U>
-cudaError_t launch_lane_u(const NetParams& p, const NetDense& q, cudaStream_t s) {
+template <int U, bool MULTI>
+cudaError_t launch_lane_u(const NetParams& p, const NetDense& q, const MultiJobTable* tab,
+                          cudaStream_t s) {
   if (q.stop_off + q.stop_size == U) {   // the stop layer is last
-    if (q.stop_size == 2) return launch_lane_us<U, (U >= 2 ? 2 : 0)>(p, q, s);
-    if (q.stop_size == 3) return launch_lane_us<U, (U >= 3 ? 3 : 0)>(p, q, s);
-    if (q.stop_size == 4) return launch_lane_us<U, (U >= 4 ? 4 : 0)>(p, q, s);
+    if (q.stop_size == 2) return launch_lane_us<U, (U >= 2 ? 2 : 0), MULTI>(p, q, tab, s);
+    if (q.stop_size == 3) return launch_lane_us<U, (U >= 3 ? 3 : 0), MULTI>(p, q, tab, s);
+    if (q.stop_size == 4) return launch_lane_us<U, (U >= 4 ? 4 : 0), MULTI>(p, q, tab, s);
   }
-  return launch_lane_us<U, 0>(p, q, s);
+  return launch_lane_us<U, 0, MULTI>(p, q, tab, s);
+}
+
+template <bool MULTI>
+cudaError_t launch_lane(const NetParams& p, const NetDense& q, const MultiJobTable* tab,
+                        cudaStream_t s) {
+  switch (p.U) {
+    case 1: return launch_lane_u<1, MULTI>(p, q, tab, s);
+    case 2: return launch_lane_u<2, MULTI>(p, q, tab, s);
+    case 3: return launch_lane_u<3, MULTI>(p, q, tab, s);
+    case 4: return launch_lane_u<4, MULTI>(p, q, tab, s);
+    case 5: return launch_lane_u<5, MULTI>(p, q, tab, s);
+    case 6: return launch_lane_u<6, MULTI>(p, q, tab, s);
+    case 7: return launch_lane_u<7, MULTI>(p, q, tab, s);
+    case 8: return launch_lane_u<8, MULTI>(p, q, tab, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 // --------------------------------------------------------------- plain ---
@@ -531,17 +581,14 @@ cudaError_t launch_group(const NetParams& p, const LaunchCfg& cfg, cudaStream_t 
 cudaError_t launch_net_lane(const NetParams& p, const NetDense& q, cudaStream_t s) {
   if (p.n <= 0) return cudaSuccess;
   if (p.n_ddm != 0 || p.cursor == nullptr) return cudaErrorInvalidValue;
-  switch (p.U) {
-    case 1: return launch_lane_u<1>(p, q, s);
-    case 2: return launch_lane_u<2>(p, q, s);
-    case 3: return launch_lane_u<3>(p, q, s);
-    case 4: return launch_lane_u<4>(p, q, s);
-    case 5: return launch_lane_u<5>(p, q, s);
-    case 6: return launch_lane_u<6>(p, q, s);
-    case 7: return launch_lane_u<7>(p, q, s);
-    case 8: return launch_lane_u<8>(p, q, s);
-  }
-  return cudaErrorInvalidValue;
+  return launch_lane<false>(p, q, nullptr, s);
+}
+
+cudaError_t launch_net_lane_multi(const NetParams& p, const NetDense& q, const MultiJobTable& tab,
+                                  cudaStream_t s) {
+  if (p.n <= 0 || tab.n_jobs < 1 || tab.n_jobs > kMaxMultiJobs) return cudaErrorInvalidValue;
+  if (p.n_ddm != 0 || p.cursor == nullptr) return cudaErrorInvalidValue;
+  return launch_lane<true>(p, q, &tab, s);
 }
 
 cudaError_t launch_net(const NetParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s) {

@@ -447,6 +447,29 @@ bool net_lane_enabled() {
   return !e || atoi(e) != 0;
 }
 
+// A small network that the one-lane form runs (at most kLaneMaxU logistic
+// units, no DDM nodes), and its dense edge matrix.
+bool net_lane_model(const dg_model* m) {
+  return m->kind == K_NET && m->layout.n_ddm == 0 && m->layout.U <= dg::kLaneMaxU;
+}
+
+dg::NetDense net_dense(const dg::NetLayout& L) {
+  dg::NetDense q{};
+  for (int u = 0; u < L.U; ++u) {
+    for (int d = 0; d < L.D; ++d)
+      if (L.w[u][d] != 0.f) q.W[u][L.src[u][d]] = L.w[u][d];
+    q.gain[u] = L.gain[u];
+    q.bias[u] = L.bias[u];
+  }
+  q.rate = L.rate;
+  q.noise = L.noise;
+  q.thr = L.stop_threshold;
+  q.stop_off = L.stop_off;
+  q.stop_size = L.stop_size;
+  q.max_steps = L.max_steps;
+  return q;
+}
+
 // The model's part of a DDM or LCA launch (the per-call part is set by the caller).
 dg::DdmParams ddm_model_params(const dg_model* m) {
   dg::DdmParams p{};
@@ -591,22 +614,8 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
     p.yout = fs;
     p.cursor = mode == DG_MODE_BATCHED ? sc->cursor() : nullptr;
     if (mode == DG_MODE_BATCHED) DG_CUDA(cudaMemsetAsync(sc->cursor(), 0, 8, s));
-    const dg::NetLayout& L = m->layout;
-    if (mode == DG_MODE_BATCHED && L.n_ddm == 0 && L.U <= dg::kLaneMaxU && net_lane_enabled()) {
-      dg::NetDense q{};
-      for (int u = 0; u < L.U; ++u) {
-        for (int d = 0; d < L.D; ++d)
-          if (L.w[u][d] != 0.f) q.W[u][L.src[u][d]] = L.w[u][d];
-        q.gain[u] = L.gain[u];
-        q.bias[u] = L.bias[u];
-      }
-      q.rate = L.rate;
-      q.noise = L.noise;
-      q.thr = L.stop_threshold;
-      q.stop_off = L.stop_off;
-      q.stop_size = L.stop_size;
-      q.max_steps = L.max_steps;
-      DG_CUDA(dg::launch_net_lane(p, q, s));
+    if (mode == DG_MODE_BATCHED && net_lane_model(m) && net_lane_enabled()) {
+      DG_CUDA(dg::launch_net_lane(p, net_dense(m->layout), s));
       return DG_OK;
     }
     DG_CUDA(dg::launch_net(p, mode, dg::LaunchCfg{}, s));
@@ -704,7 +713,9 @@ dg_status run_jobs_device(dg_model* m, int n_jobs, const dg_run_desc* d, int8_t*
     dg::MultiJob& J = tab.jobs[tab.n_jobs++];
     J.start = total;
     J.n = d[i].n_trials;
-    J.in = d[i].trial_params;
+    J.in = m->kind == K_NET ? d[i].cond_inputs : d[i].trial_params;
+    J.n_cond = d[i].n_cond;
+    J.cond_block = d[i].cond_block;
     J.choice = choice[i];
     J.step = step[i];
     J.xout = fs ? fs[i] : nullptr;
@@ -725,6 +736,20 @@ dg_status run_jobs_device(dg_model* m, int n_jobs, const dg_run_desc* d, int8_t*
     DG_CUDA(dg::launch_ddm_multi(p, tab, s));
     return DG_OK;
   }
+  if (m->kind == K_NET) {
+    dg::NetParams p{};
+    p.layout = m->d_layout;
+    p.w_in = m->d_w_in;
+    p.n = total;
+    p.U = m->layout.U;
+    p.n_in = m->layout.n_in;
+    p.stop_size = m->layout.stop_size;
+    p.n_ddm = 0;
+    p.state_size = m->state_size;
+    p.cursor = sc->cursor();
+    DG_CUDA(dg::launch_net_lane_multi(p, net_dense(m->layout), tab, s));
+    return DG_OK;
+  }
   dg::LcaParams p = lca_model_params(m);
   p.n = total;
   p.cursor = sc->cursor();
@@ -737,8 +762,9 @@ dg_status check_jobs_args(dg_model* m, int n_jobs, const dg_run_desc* d, int8_t*
   if (!m || !d || !choice || !step || n_jobs < 1 || n_jobs > dg::kMaxMultiJobs)
     return fail(DG_E_ARG, "dg_run_jobs: null model, descs or outputs, or n_jobs outside [1, %d]",
                 dg::kMaxMultiJobs);
-  if (m->kind != K_DDM && m->kind != K_LCA)
-    return fail(DG_E_UNSUPPORTED, "dg_run_jobs: DDM and LCA models only");
+  if (m->kind != K_DDM && m->kind != K_LCA && !net_lane_model(m))
+    return fail(DG_E_UNSUPPORTED, "dg_run_jobs: DDM, LCA and small network models only "
+                                  "(at most %d logistic units, no DDM nodes)", dg::kLaneMaxU);
   long long total = 0;
   for (int i = 0; i < n_jobs; ++i) {
     dg_status st = check_run_args(m, d + i, choice[i], step[i]);
@@ -920,7 +946,8 @@ struct Server {
 
   bool groupable(const JobRec& r) const {
     const dg_job& j = r.job;
-    return !j.is_grid && (j.model->kind == K_DDM || j.model->kind == K_LCA) &&
+    return !j.is_grid &&
+           (j.model->kind == K_DDM || j.model->kind == K_LCA || net_lane_model(j.model)) &&
            j.run.mode == DG_MODE_BATCHED && j.run.n_trials > 0 &&
            j.run.n_trials <= group_job_trials;
   }
@@ -987,13 +1014,17 @@ struct Server {
   // A run job's buffers as the kernel can use them in place, if all are
   // pinned and mapped.
   static bool in_place(const dg_job& j, Staged* out) {
-    const float* in = (const float*)mapped_alias(j.run.trial_params);
+    const bool net = j.model->kind == K_NET;
+    const float* in = (const float*)mapped_alias(net ? j.run.cond_inputs : j.run.trial_params);
     int8_t* ch = (int8_t*)mapped_alias(j.choice);
     int32_t* st = (int32_t*)mapped_alias(j.step);
     float* fs = j.final_state ? (float*)mapped_alias(j.final_state) : nullptr;
     if (!in || !ch || !st || (j.final_state && !fs)) return false;
     out->d = j.run;
-    out->d.trial_params = in;
+    if (net)
+      out->d.cond_inputs = in;
+    else
+      out->d.trial_params = in;
     out->choice = ch;
     out->step = st;
     out->fs = fs;

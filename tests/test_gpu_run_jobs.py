@@ -84,6 +84,59 @@ def test_run_jobs_equal_single_runs(ctx, kind, N):
         B.dg_model_free(model)
 
 
+def _stroop(B, ctx, weight_seed=4):
+    from paper_2110_15425_gb300 import workloads as W
+    w = W.stroop_small(weight_seed=weight_seed)
+    m = B.compose_network(ctx, w["layers"], w["projections"], rate=w["rate"],
+                          noise_sd=w["noise_sd"], stop_layer=w["stop_layer"],
+                          stop_threshold=w["stop_threshold"], max_steps=w["max_steps"])
+    return w, m
+
+
+def _net_desc(B, n, seed, cond, cond_block, offset):
+    return B.run_desc(n, seed, cond_inputs=dev(cond), n_cond=cond.shape[0], cond_block=cond_block,
+                      trial_offset=offset)
+
+
+def test_run_jobs_network_equal_single_runs(ctx):
+    """Jobs of one small network, each with its own condition table, condition
+    block, seed and trial offset, in one launch: each equals its dg_run."""
+    import torch
+    from paper_2110_15425_gb300 import binding as B
+    w, model = _stroop(B, ctx)
+    try:
+        state = B.dg_model_info(model)[1]
+        rng = np.random.default_rng(5)
+        sizes = [0, 1, 37, 1000, 4097, 20000, 3]
+        jobs = []
+        for i, n in enumerate(sizes):
+            nc = int(rng.integers(1, 6))
+            cond = rng.uniform(0, 1, (nc, w["cond_inputs"].shape[1])).astype(np.float32)
+            jobs.append((n, 77 + 1000003 * i, cond, int(rng.integers(1, 300)),
+                         [0, 9, 123456, 0, 5, 2 ** 30, 7][i], i % 2 == 0))
+        descs = [_net_desc(B, n, sd, c, cb, off) for n, sd, c, cb, off, _ in jobs]
+        cs = [torch.full((max(n, 1),), 9, dtype=torch.int8, device="cuda") for n, *_ in jobs]
+        ss = [torch.full((max(n, 1),), -9, dtype=torch.int32, device="cuda") for n, *_ in jobs]
+        fs = [torch.zeros(max(n, 1) * state, dtype=torch.float32, device="cuda") if ws else None
+              for n, *_, ws in jobs]
+        B.dg_run_jobs(model, descs, cs, ss, fs)
+        for i, (n, sd, c, cb, off, ws) in enumerate(jobs):
+            if n == 0:
+                assert host(cs[i])[0] == 9 and host(ss[i])[0] == -9
+                continue
+            c1 = torch.zeros(n, dtype=torch.int8, device="cuda")
+            s1 = torch.zeros(n, dtype=torch.int32, device="cuda")
+            f1 = torch.zeros(n * state, dtype=torch.float32, device="cuda")
+            B.dg_run(model, _net_desc(B, n, sd, c, cb, off), c1, s1, f1)
+            assert np.array_equal(host(cs[i])[:n], host(c1)), i
+            assert np.array_equal(host(ss[i])[:n], host(s1)), i
+            if ws:
+                assert np.array_equal(host(fs[i])[:n * state].view(np.uint32),
+                                      host(f1).view(np.uint32)), i
+    finally:
+        B.dg_model_free(model)
+
+
 def test_run_jobs_against_oracle(ctx, orc, threads):
     """Job i of a multi-job launch against the oracle on a sample of its
     trials, with the job's own seed and trial offset."""
@@ -141,6 +194,18 @@ def test_run_jobs_arguments(ctx):
         dn = B.run_desc(10, 1)   # no trial_params
         with pytest.raises(RuntimeError):
             B.dg_run_jobs(md, [dn], [c], [s])
+        from paper_2110_15425_gb300 import workloads as W
+        wd = W.stroop_wide(n_trials=10, max_steps=20)
+        mw = B.compose_network(ctx, wd["layers"], wd["projections"], rate=wd["rate"],
+                               noise_sd=wd["noise_sd"], stop_layer=3, stop_threshold=0.7,
+                               max_steps=20, bf16_edges=(2,))
+        try:   # the wide network has its own kernel: not a job-table model
+            dw = B.run_desc(10, 1, cond_inputs=dev(wd["cond_inputs"]),
+                            n_cond=wd["cond_inputs"].shape[0], cond_block=1)
+            with pytest.raises(RuntimeError):
+                B.dg_run_jobs(mw, [dw], [c], [s])
+        finally:
+            B.dg_model_free(mw)
         B.dg_run_jobs(md, [d] * 256, [c] * 256, [s] * 256)   # 256 jobs is the limit
     finally:
         B.dg_model_free(md)
@@ -164,21 +229,29 @@ def test_served_small_jobs_grouped_equal_direct_runs(ctx, pinned):
         t = torch.from_numpy(a).pin_memory()
         keep.append(t)
         return t.numpy()
+    w_st, m_st = _stroop(B, ctx)
     models = dict(ddm=B.compose_ddm(ctx), ddm2=B.compose_ddm(ctx, dt=2e-3, sigma=0.8),
-                  lca4=B.compose_lca(ctx, 4), lca8=B.compose_lca(ctx, 8))
+                  lca4=B.compose_lca(ctx, 4), lca8=B.compose_lca(ctx, 8), stroop=m_st)
     try:
         jobs = []
-        for i in range(160):
-            k = ["ddm", "ddm2", "lca4", "lca8"][int(rng.integers(4))]
+        for i in range(200):
+            k = ["ddm", "ddm2", "lca4", "lca8", "stroop"][int(rng.integers(5))]
             n = int(rng.integers(1, 12000))
-            N = 1 if k.startswith("ddm") else int(k[3:])
-            h = buf(_inputs("ddm" if N == 1 else "lca", n, 200 + i, N))
+            N = 1 if k.startswith("ddm") else 2 if k == "stroop" else int(k[3:])
             j = B.dg_job()
             j.model = models[k].value
             j.run.n_trials = n
             j.run.seed = int(rng.integers(1, 2 ** 40))
             j.run.trial_offset = int(rng.integers(0, 10 ** 6))
-            j.run.trial_params = h.ctypes.data
+            if k == "stroop":
+                nc = int(rng.integers(1, 5))
+                h = buf(rng.uniform(0, 1, (nc, w_st["cond_inputs"].shape[1])).astype(np.float32))
+                j.run.cond_inputs = h.ctypes.data
+                j.run.n_cond = nc
+                j.run.cond_block = int(rng.integers(1, 100))
+            else:
+                h = buf(_inputs("ddm" if N == 1 else "lca", n, 200 + i, N))
+                j.run.trial_params = h.ctypes.data
             ch = buf(np.full(n, 9, np.int8))
             st = buf(np.full(n, -9, np.int32))
             fs = buf(np.zeros(n * N, np.float32)) if i % 3 == 0 else None
@@ -192,7 +265,16 @@ def test_served_small_jobs_grouped_equal_direct_runs(ctx, pinned):
             r = B.dg_wait(ctx, t, 120000)
             assert r.status == 0
         for k, n, N, h, j, ch, st, fs in jobs:
-            c, s, f = _alone(B, models[k], h, n, j.run.seed, j.run.trial_offset, N)
+            if k == "stroop":
+                import torch
+                c1 = torch.zeros(n, dtype=torch.int8, device="cuda")
+                s1 = torch.zeros(n, dtype=torch.int32, device="cuda")
+                f1 = torch.zeros(n * N, dtype=torch.float32, device="cuda")
+                B.dg_run(models[k], _net_desc(B, n, j.run.seed, np.asarray(h), j.run.cond_block,
+                                              j.run.trial_offset), c1, s1, f1)
+                c, s, f = host(c1), host(s1), host(f1)
+            else:
+                c, s, f = _alone(B, models[k], h, n, j.run.seed, j.run.trial_offset, N)
             assert np.array_equal(ch, c) and np.array_equal(st, s), (k, n)
             if fs is not None:
                 assert np.array_equal(fs.view(np.uint32), f.view(np.uint32)), (k, n)
