@@ -482,7 +482,12 @@ def run_only(args):
     k = args.only
     if k == "small_jobs":   # the many-small-jobs serving measurement alone
         w, l8 = W.ddm(n_trials=1), W.lca(n_trials=1, N=8)
-        models = [dict(name="ddm", model=B.compose_ddm(ctx, dt=w["dt"], sigma=w["sigma"],
+        st = W.stroop_small()
+        models = [dict(name="stroop", model=B.compose_network(
+                      ctx, st["layers"], st["projections"], rate=st["rate"],
+                      noise_sd=st["noise_sd"], stop_layer=st["stop_layer"],
+                      stop_threshold=st["stop_threshold"], max_steps=st["max_steps"])),
+                  dict(name="ddm", model=B.compose_ddm(ctx, dt=w["dt"], sigma=w["sigma"],
                                                        max_steps=w["max_steps"])),
                   dict(name="lca8", model=B.compose_lca(
                       ctx, 8, leak=l8["leak"], inhibition=l8["inhibition"], sigma=l8["sigma"],
@@ -1163,10 +1168,11 @@ def _plain(B, prepared, arrivals, stream):
 
 
 def served_small_jobs(B, W, torch, ctx, step, n_jobs=SERVE_JOBS, seed=17):
-    """Many small jobs: DDM and LCA (N = 8) jobs of 1e3-1e4 trials, all arriving at
-    once, through the serving API and through the plain form: jobs/s,
-    trial-steps/s and latency."""
-    prepared = _mix(B, W, torch, step, n_jobs, seed, kinds=("ddm", "lca"), log_trials=(3, 4))
+    """Many small jobs: DDM, LCA (N = 8) and Stroop jobs of 1e3-1e4 trials, all
+    arriving at once, through the serving API and through the plain form:
+    jobs/s, trial-steps/s and latency."""
+    prepared = _mix(B, W, torch, step, n_jobs, seed, kinds=("ddm", "lca", "stroop"),
+                    log_trials=(3, 4))
     stream = torch.cuda.Stream()
     zero = [0.0] * n_jobs
     # a second context whose serving loop gives every job its own launch
@@ -1190,7 +1196,7 @@ def served_small_jobs(B, W, torch, ctx, step, n_jobs=SERVE_JOBS, seed=17):
     with torch.cuda.stream(stream):
         lat_p, wall_p = _plain(B, prepared, zero, stream)
     B.dg_destroy(ctx_each)
-    return {"jobs": n_jobs, "mix": "ddm/lca8, trials log-uniform 1e3-1e4, all at once",
+    return {"jobs": n_jobs, "mix": "ddm/lca8/stroop, trials log-uniform 1e3-1e4, all at once",
             "trial_steps": steps,
             "served": dict(_lat_stats(*res["served"], n_jobs, steps),
                            form="serving loop, small jobs of one model share a launch"),

@@ -517,7 +517,10 @@ typedef struct {
    DG_SERVE_GROUP_TRIALS; 0 turns this off), takes later queued batched jobs of
    the same model, up to that size
    each, 256 jobs and 2^23 trials in all, into one dg_run_jobs launch; results
-   are those of the jobs run alone. A grouped job whose trial_params (or
+   are those of the jobs run alone. Likewise whole-grid searches (lowest-index
+   ties, batched mode, at most 65,536 candidates) of one model, grid shape and
+   trial count share a dg_grid_search_batch launch (up to 256 searches). A
+   grouped run job whose trial_params (or
    cond_inputs), choice, step (and final_state) are all pinned host memory (cudaHostAlloc, or
    cudaHostRegister'd) is read and written by the kernel in place through the
    memory's device mapping, without staging copies (DG_SERVE_ZERO_COPY=0 turns

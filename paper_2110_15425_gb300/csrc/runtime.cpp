@@ -848,6 +848,64 @@ dg_status grid_device(dg_model* m, const dg_grid_desc* d, dg_grid_result* result
   return run_tuned(m->ctx, key, grid_candidates(p.n_cand, dg::grid_lanes(p.L)), s, go);
 }
 
+dg_status check_grid_batch(dg_model* m, int32_t n_searches, const dg_grid_desc* descs,
+                           const dg_grid_result* results) {
+  if (!m || !descs || !results || n_searches < 1 || n_searches > dg::kMaxGridBatch)
+    return fail(DG_E_ARG, "dg_grid_search_batch: null model, descs or results, or n_searches "
+                          "outside [1, %d]", dg::kMaxGridBatch);
+  for (int i = 0; i < n_searches; ++i) {
+    const dg_grid_desc& d = descs[i];
+    dg_status st = check_grid_args(m, &d, const_cast<dg_grid_result*>(results));
+    if (st != DG_OK) return st;
+    for (int e = 0; e < 3; ++e)
+      if (d.n_levels[e] != descs[0].n_levels[e])
+        return fail(DG_E_ARG, "dg_grid_search_batch: search %d has another grid shape", i);
+    if (d.n_trials != descs[0].n_trials)
+      return fail(DG_E_ARG, "dg_grid_search_batch: search %d has another trial count", i);
+    if (d.cand_begin != 0 || d.cand_count != 0 || d.tie_break != DG_TIE_LOWEST ||
+        d.mode != DG_MODE_BATCHED)
+      return fail(DG_E_ARG, "dg_grid_search_batch: search %d: whole grids, lowest-index ties "
+                            "and the batched mode only", i);
+  }
+  return DG_OK;
+}
+
+// A checked batch of whole-grid searches of one shape in one launch; search i
+// writes results[i] and, when not null, cand_means[i].
+dg_status grid_batch_device(dg_model* m, int32_t n_searches, const dg_grid_desc* descs,
+                            dg_grid_result* const* results, double* const* cand_means,
+                            cudaStream_t s) {
+  Scratch* sc = nullptr;
+  dg_status st = get_scratch(m->ctx, s, &sc);
+  if (st != DG_OK) return st;
+  dg::GridBatchParams p{};
+  for (int e = 0; e < 3; ++e) p.L[e] = descs[0].n_levels[e];
+  p.n_trials = descs[0].n_trials;
+  p.offset = m->offset;
+  p.weight = m->weight;
+  p.n_cand = (long long)p.L[0] * p.L[1] * p.L[2];
+  p.cpc = (int)((p.n_cand + dg::kGridChunk - 1) / dg::kGridChunk);
+  p.n_search = n_searches;
+  const size_t head = 256 + ((size_t)n_searches * sizeof(unsigned int) + 255) / 256 * 256;
+  const size_t bytes = head + (size_t)n_searches * p.cpc * sizeof(dg::TopTwo);
+  if ((st = scratch_gb(m->ctx, sc, bytes, s)) != DG_OK) return st;
+  p.cursor = reinterpret_cast<unsigned long long*>(sc->gb);
+  p.ticket = reinterpret_cast<unsigned int*>(sc->gb + 256);
+  p.partials = reinterpret_cast<dg::TopTwo*>(sc->gb + head);
+  for (int i = 0; i < n_searches; ++i) {
+    dg::GridBatchItem& it = p.items[i];
+    for (int e = 0; e < 3; ++e) it.lv[e] = descs[i].levels[e];
+    it.pos = descs[i].positions;
+    it.result = results[i];
+    it.means = cand_means ? cand_means[i] : nullptr;
+    it.k0 = (uint32_t)descs[i].seed;
+    it.k1 = (uint32_t)(descs[i].seed >> 32);
+  }
+  DG_CUDA(cudaMemsetAsync(sc->gb, 0, head, s));
+  DG_CUDA(dg::launch_grid_batch(p, s));
+  return DG_OK;
+}
+
 // ------------------------------------------------------------ serving ---
 
 struct JobRec {
@@ -944,12 +1002,32 @@ struct Server {
     return b + 16 * 256;
   }
 
+  static long long grid_cands(const dg_grid_desc& g) {
+    return (long long)g.n_levels[0] * g.n_levels[1] * g.n_levels[2];
+  }
+
+  // Jobs that can share a launch with others: runs of a job-table model up to
+  // group_job_trials trials; whole-grid searches (lowest-index ties) up to as
+  // many candidates.
   bool groupable(const JobRec& r) const {
     const dg_job& j = r.job;
-    return !j.is_grid &&
-           (j.model->kind == K_DDM || j.model->kind == K_LCA || net_lane_model(j.model)) &&
+    if (j.is_grid)
+      return j.model->kind == K_PP && j.grid.mode == DG_MODE_BATCHED &&
+             j.grid.tie_break == DG_TIE_LOWEST && j.grid.cand_begin == 0 &&
+             j.grid.cand_count == 0 && grid_cands(j.grid) <= group_job_trials;
+    return (j.model->kind == K_DDM || j.model->kind == K_LCA || net_lane_model(j.model)) &&
            j.run.mode == DG_MODE_BATCHED && j.run.n_trials > 0 &&
            j.run.n_trials <= group_job_trials;
+  }
+
+  // b may join a's launch: the same model, and for searches the same grid
+  // shape and trial count.
+  static bool same_group(const dg_job& a, const dg_job& b) {
+    if (a.model != b.model || a.is_grid != b.is_grid) return false;
+    if (!a.is_grid) return true;
+    for (int e = 0; e < 3; ++e)
+      if (a.grid.n_levels[e] != b.grid.n_levels[e]) return false;
+    return a.grid.n_trials == b.grid.n_trials;
   }
 
   // Device copies of a run job: inputs copied in, outputs allocated.
@@ -1060,6 +1138,50 @@ struct Server {
     return DG_OK;
   }
 
+  // Enqueue a group of searches of one grid shape: each job's positions and
+  // levels copied in, one batched launch, each job's result (and means) out.
+  dg_status launch_grid_group(const std::vector<std::shared_ptr<JobRec>>& grp, cudaStream_t s) {
+    const int n = (int)grp.size();
+    std::vector<dg_grid_desc> d(n);
+    std::vector<dg_grid_result*> res(n);
+    std::vector<double*> means(n);
+    for (int i = 0; i < n; ++i) {
+      JobRec& r = *grp[i];
+      const dg_job& j = r.job;
+      DG_CUDA(cudaMallocAsync(&r.dmem, r.bytes, s));
+      unsigned char* p = reinterpret_cast<unsigned char*>(r.dmem);
+      auto take = [&](size_t bytes) {
+        unsigned char* q = p;
+        p += (bytes + 255) / 256 * 256;
+        return q;
+      };
+      d[i] = j.grid;
+      float* pos = (float*)take(6 * sizeof(float) * d[i].n_trials);
+      DG_CUDA(cudaMemcpyAsync(pos, j.grid.positions, 6 * sizeof(float) * d[i].n_trials,
+                              cudaMemcpyHostToDevice, s));
+      d[i].positions = pos;
+      for (int e = 0; e < 3; ++e) {
+        float* lv = (float*)take(sizeof(float) * d[i].n_levels[e]);
+        DG_CUDA(cudaMemcpyAsync(lv, j.grid.levels[e], sizeof(float) * d[i].n_levels[e],
+                                cudaMemcpyHostToDevice, s));
+        d[i].levels[e] = lv;
+      }
+      res[i] = (dg_grid_result*)take(sizeof(dg_grid_result));
+      means[i] = (double*)take(sizeof(double) * (size_t)grid_cands(d[i]));
+    }
+    dg_status st = grid_batch_device(grp[0]->job.model, n, d.data(), res.data(), means.data(), s);
+    if (st != DG_OK) return st;
+    for (int i = 0; i < n; ++i) {
+      const dg_job& j = grp[i]->job;
+      DG_CUDA(cudaMemcpyAsync(j.grid_result, res[i], sizeof(dg_grid_result),
+                              cudaMemcpyDeviceToHost, s));
+      if (j.cand_means)
+        DG_CUDA(cudaMemcpyAsync(j.cand_means, means[i], sizeof(double) * (size_t)grid_cands(d[i]),
+                                cudaMemcpyDeviceToHost, s));
+    }
+    return DG_OK;
+  }
+
   // Enqueue a job's copies and kernels on its slot's stream.
   dg_status launch(JobRec& r, cudaStream_t s) {
     const dg_job& j = r.job;
@@ -1151,17 +1273,22 @@ struct Server {
         std::vector<std::shared_ptr<JobRec>> grp{rp};
         size_t bytes = rp->bytes;
         if (groupable(*rp)) {
-          long long total = rp->job.run.n_trials;
+          const bool grid = rp->job.is_grid;
+          const int max_jobs = grid ? dg::kMaxGridBatch : dg::kMaxMultiJobs;
+          auto units = [&](const JobRec& r) {   // trials, or candidate evaluations
+            return grid ? grid_cands(r.job.grid) * r.job.grid.n_trials : r.job.run.n_trials;
+          };
+          long long total = units(*rp);
           size_t scanned = 0;
-          for (auto it = queue.begin(); it != queue.end() && scanned < kGroupScan &&
-                                        (int)grp.size() < dg::kMaxMultiJobs;
+          for (auto it = queue.begin();
+               it != queue.end() && scanned < kGroupScan && (int)grp.size() < max_jobs;
                ++scanned) {
             auto& q = jobs[*it];
-            if (groupable(*q) && q->job.model == rp->job.model &&
-                total + q->job.run.n_trials <= kGroupTrials &&
+            if (groupable(*q) && same_group(rp->job, q->job) &&
+                total + units(*q) <= (grid ? 64 * kGroupTrials : kGroupTrials) &&
                 in_use + bytes + q->bytes <= ctx->budget) {
               grp.push_back(q);
-              total += q->job.run.n_trials;
+              total += units(*q);
               bytes += q->bytes;
               it = queue.erase(it);
             } else {
@@ -1187,7 +1314,9 @@ struct Server {
         for (auto& grp : admitted) {
           const int slot = grp[0]->slot;
           cudaStream_t s = streams[slot];
-          dg_status st = grp.size() == 1 ? launch(*grp[0], s) : launch_group(grp, s);
+          dg_status st = grp.size() == 1      ? launch(*grp[0], s)
+                         : grp[0]->job.is_grid ? launch_grid_group(grp, s)
+                                               : launch_group(grp, s);
           if (st == DG_OK && cudaEventRecord(events[slot], s) != cudaSuccess) st = DG_E_CUDA;
           if (st != DG_OK) {
             cudaStreamSynchronize(s);
@@ -1744,54 +1873,12 @@ dg_status dg_grid_search(dg_model* m, const dg_grid_desc* d, dg_grid_result* res
 
 dg_status dg_grid_search_batch(dg_model* m, int32_t n_searches, const dg_grid_desc* descs,
                                dg_grid_result* results, double* const* cand_means, void* stream) {
-  if (!m || !descs || !results || n_searches < 1 || n_searches > dg::kMaxGridBatch)
-    return fail(DG_E_ARG, "dg_grid_search_batch: null model, descs or results, or n_searches "
-                          "outside [1, %d]", dg::kMaxGridBatch);
-  for (int i = 0; i < n_searches; ++i) {
-    const dg_grid_desc& d = descs[i];
-    dg_status st = check_grid_args(m, &d, results + i);
-    if (st != DG_OK) return st;
-    for (int e = 0; e < 3; ++e)
-      if (d.n_levels[e] != descs[0].n_levels[e])
-        return fail(DG_E_ARG, "dg_grid_search_batch: search %d has another grid shape", i);
-    if (d.n_trials != descs[0].n_trials)
-      return fail(DG_E_ARG, "dg_grid_search_batch: search %d has another trial count", i);
-    if (d.cand_begin != 0 || d.cand_count != 0 || d.tie_break != DG_TIE_LOWEST ||
-        d.mode != DG_MODE_BATCHED)
-      return fail(DG_E_ARG, "dg_grid_search_batch: search %d: whole grids, lowest-index ties "
-                            "and the batched mode only", i);
-  }
-  cudaStream_t s = (cudaStream_t)stream;
-  DG_CUDA(cudaSetDevice(m->ctx->device));
-  Scratch* sc = nullptr;
-  dg_status st = get_scratch(m->ctx, s, &sc);
+  dg_status st = check_grid_batch(m, n_searches, descs, results);
   if (st != DG_OK) return st;
-  dg::GridBatchParams p{};
-  for (int e = 0; e < 3; ++e) p.L[e] = descs[0].n_levels[e];
-  p.n_trials = descs[0].n_trials;
-  p.offset = m->offset;
-  p.weight = m->weight;
-  p.n_cand = (long long)p.L[0] * p.L[1] * p.L[2];
-  p.cpc = (int)((p.n_cand + dg::kGridChunk - 1) / dg::kGridChunk);
-  p.n_search = n_searches;
-  const size_t head = 256 + ((size_t)n_searches * sizeof(unsigned int) + 255) / 256 * 256;
-  const size_t bytes = head + (size_t)n_searches * p.cpc * sizeof(dg::TopTwo);
-  if ((st = scratch_gb(m->ctx, sc, bytes, s)) != DG_OK) return st;
-  p.cursor = reinterpret_cast<unsigned long long*>(sc->gb);
-  p.ticket = reinterpret_cast<unsigned int*>(sc->gb + 256);
-  p.partials = reinterpret_cast<dg::TopTwo*>(sc->gb + head);
-  for (int i = 0; i < n_searches; ++i) {
-    dg::GridBatchItem& it = p.items[i];
-    for (int e = 0; e < 3; ++e) it.lv[e] = descs[i].levels[e];
-    it.pos = descs[i].positions;
-    it.result = results + i;
-    it.means = cand_means ? cand_means[i] : nullptr;
-    it.k0 = (uint32_t)descs[i].seed;
-    it.k1 = (uint32_t)(descs[i].seed >> 32);
-  }
-  DG_CUDA(cudaMemsetAsync(sc->gb, 0, head, s));
-  DG_CUDA(dg::launch_grid_batch(p, s));
-  return DG_OK;
+  DG_CUDA(cudaSetDevice(m->ctx->device));
+  std::vector<dg_grid_result*> res((size_t)n_searches);
+  for (int i = 0; i < n_searches; ++i) res[(size_t)i] = results + i;
+  return grid_batch_device(m, n_searches, descs, res.data(), cand_means, (cudaStream_t)stream);
 }
 
 dg_status dg_argmax_f64(dg_ctx* ctx, const double* values, int64_t n, dg_grid_result* result,

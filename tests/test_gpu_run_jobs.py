@@ -281,3 +281,45 @@ def test_served_small_jobs_grouped_equal_direct_runs(ctx, pinned):
     finally:
         for m in models.values():
             B.dg_model_free(m)
+
+
+def test_served_grid_searches_grouped_equal_direct_searches(ctx):
+    """Grid searches submitted together: those of one grid shape and trial
+    count share a batched launch in the serving loop; each job's result and
+    candidate means equal a direct dg_grid_search of it, bit for bit."""
+    import torch
+    from paper_2110_15425_gb300 import binding as B
+    from paper_2110_15425_gb300 import workloads as W
+    model = B.compose_predator_prey(ctx)
+    try:
+        specs = [(12, 64)] * 20 + [(7, 64)] * 6 + [(12, 33)] * 3 + [(30, 64)]
+        jobs = []
+        for i, (L, T) in enumerate(specs):
+            g = W.predator_prey(levels=L, pos_seed=40 + i, noise_seed=90 + i)
+            pos = np.ascontiguousarray(g["pos"][:T])
+            lvs = [np.ascontiguousarray(x) for x in g["levels"]]
+            j = B.dg_job()
+            j.model = model.value
+            j.is_grid = 1
+            j.grid.positions = pos.ctypes.data
+            j.grid.n_trials = T
+            j.grid.seed = g["seed"]
+            for e in range(3):
+                j.grid.levels[e] = lvs[e].ctypes.data
+                j.grid.n_levels[e] = L
+            res = np.zeros(3, np.float64)
+            means = np.zeros(L ** 3, np.float64)
+            j.grid_result = res.ctypes.data
+            j.cand_means = means.ctypes.data
+            jobs.append((L, T, g, pos, lvs, j, res, means))
+        tickets = [B.dg_submit(ctx, x[5]) for x in jobs]
+        for t in tickets:
+            assert B.dg_wait(ctx, t, 120000).status == 0
+        for L, T, g, pos, lvs, j, res, means in jobs:
+            r2 = torch.zeros(3, dtype=torch.float64, device="cuda")
+            m2 = torch.zeros(L ** 3, dtype=torch.float64, device="cuda")
+            B.dg_grid_search(model, B.grid_desc([dev(x) for x in lvs], dev(pos), g["seed"]), r2, m2)
+            assert np.array_equal(means, host(m2)), (L, T)
+            assert np.array_equal(res, host(r2)), (L, T)
+    finally:
+        B.dg_model_free(model)
