@@ -23,7 +23,9 @@ constexpr unsigned kFull = 0xffffffffu;
 // round multipliers, then mixes the high halves with words 1 and 3 and the
 // key; the key advances by the two Weyl increments between rounds.
 __host__ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#ifdef __CUDA_ARCH__
 #pragma unroll
+#endif
   for (int r = 0; r < 10; ++r) {
     // one 32x32 -> 64-bit multiply gives both halves of each product
     const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53ull;
