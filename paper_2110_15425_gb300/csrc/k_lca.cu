@@ -315,9 +315,14 @@ __global__ void __launch_bounds__(256) lca_compact(
   }
   while (true) {
     // ---- a chunk of steps
+    // (N >= 8, one job: two steps per iteration, the noise buffers in turn: the second
+    // step draws the step after it into e, so no copy is made, and a chunk of
+    // p.chunk steps rounds up to an even count; for smaller N the second copy
+    // of the step costs more in occupancy than it saves)
+    constexpr int kPer = N >= 8 && !MULTI ? 2 : 1;
     if (__any_sync(kFull, active)) {
-      for (int s = 0; s < p.chunk; ++s) {
-        if (active) {
+      for (int s = 0; s < p.chunk; s += kPer) {
+        if (kPer == 1 && active) {
           float en[N];
           noise(k + 1, en);
           int8_t c = -1;
@@ -329,6 +334,25 @@ __global__ void __launch_bounds__(256) lca_compact(
           }
 #pragma unroll
           for (int i = 0; i < N; ++i) e[i] = en[i];
+        } else if (kPer == 2 && active) {
+          float en[N];
+          noise(k + 1, en);
+          int8_t c = -1;
+          bool hit = L::step(p, e, 0, self, x, I, c);
+          ++k;
+          if (hit || k >= p.max_steps) {
+            L::store(q, t, 0, hit ? c : (int8_t)-1, hit ? k : p.max_steps, x);
+            active = false;
+          } else {
+            noise(k + 1, e);
+            c = -1;
+            hit = L::step(p, en, 0, self, x, I, c);
+            ++k;
+            if (hit || k >= p.max_steps) {
+              L::store(q, t, 0, hit ? c : (int8_t)-1, hit ? k : p.max_steps, x);
+              active = false;
+            }
+          }
         }
         if (!__any_sync(kFull, active)) break;
       }
