@@ -15,9 +15,10 @@
 // bits with 40. Error against exact arithmetic stays near 1e-6 after 10,000
 // steps.
 //
-// Batched form: one trial per warp, 128 steps per iteration - lane i draws
-// block k/4 + i, an exact int64 warp scan gives every lane its X_b, and a
-// ballot finds the first crossing - so no lane waits on another lane's trial.
+// Batched form: one trial per warp, 256 steps per iteration - lane i draws
+// blocks k/4 + 2i and k/4 + 2i + 1, an exact warp scan gives every lane its
+// X_b, and a ballot finds the first crossing - so no lane waits on another
+// lane's trial.
 // Plain form: one thread per trial, one block after another.
 #include "dg_device.cuh"
 #include "dg_internal.h"
@@ -83,51 +84,69 @@ __device__ __forceinline__ void ddm_write(const DdmParams& p, long long t, bool 
   if (p.xout) p.xout[t] = x;
 }
 
-// One trial per warp, 128 steps per iteration (the batched form).
+// One trial per warp, 256 steps per iteration (the batched form): lane i takes
+// blocks k/4 + 2i and k/4 + 2i + 1, so the exact scan, the bound ballot and the
+// loop run once per 256 steps.
 template <typename F>
 __device__ __forceinline__ void ddm_trial_warp(const DdmParams& p, long long t,
                                                const DdmTrial& d) {
   using T = typename F::T;
   const int lane = threadIdx.x & 31;
   T x = F::of(p.x0);
-  for (int k = 0; k < p.max_steps; k += 128) {
-    float pre[4];
-    block_partials(p, t, (uint32_t)(k >> 2) + (uint32_t)lane, d.adt, pre);
-    const T q = F::of(pre[3]);
-    T incl = q;   // exact scan of the block sums
+  for (int k = 0; k < p.max_steps; k += 256) {
+    float pa[4], pb[4];
+    const uint32_t b0 = (uint32_t)(k >> 2) + 2u * (uint32_t)lane;
+    block_partials(p, t, b0, d.adt, pa);
+    block_partials(p, t, b0 + 1u, d.adt, pb);
+    const T qa = F::of(pa[3]), q = qa + F::of(pb[3]);
+    T incl = q;   // exact scan of the lanes' two-block sums
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const T v = __shfl_up_sync(kFull, incl, o);
       if (lane >= o) incl += v;
     }
-    const float xb = F::val(x + (incl - q));   // state before this lane's block
-    const int s0 = k + 4 * lane;
-    // does any of this lane's four steps reach the bound? (the step cap only
+    const T xa_fix = x + (incl - q);
+    const float xa = F::val(xa_fix);        // state before this lane's first block
+    const float xb = F::val(xa_fix + qa);   // and before its second
+    const int s0 = k + 8 * lane;
+    // does any of this lane's eight steps reach the bound? (the step cap only
     // matters in the last chunk, a warp-uniform case)
     bool hit;
-    if (k + 128 <= p.max_steps) {
-      const float m = fmaxf(fmaxf(fabsf(xb + pre[0]), fabsf(xb + pre[1])),
-                            fmaxf(fabsf(xb + pre[2]), fabsf(xb + pre[3])));
+    if (k + 256 <= p.max_steps) {
+      const float m = fmaxf(fmaxf(fmaxf(fabsf(xa + pa[0]), fabsf(xa + pa[1])),
+                                  fmaxf(fabsf(xa + pa[2]), fabsf(xa + pa[3]))),
+                            fmaxf(fmaxf(fabsf(xb + pb[0]), fabsf(xb + pb[1])),
+                                  fmaxf(fabsf(xb + pb[2]), fabsf(xb + pb[3]))));
       hit = m >= d.z;
     } else {
       hit = false;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) hit |= s0 + j < p.max_steps && fabsf(xb + pre[j]) >= d.z;
+      for (int j = 0; j < 4; ++j) {
+        hit |= s0 + j < p.max_steps && fabsf(xa + pa[j]) >= d.z;
+        hit |= s0 + 4 + j < p.max_steps && fabsf(xb + pb[j]) >= d.z;
+      }
     }
     const unsigned hit_lanes = __ballot_sync(kFull, hit);
     if (hit_lanes) {
       if (lane == __ffs(hit_lanes) - 1) {
-        int first = 3;
+        int first = 7;
 #pragma unroll
-        for (int j = 2; j >= 0; --j)
-          if (fabsf(xb + pre[j]) >= d.z) first = j;
-        ddm_write(p, t, true, s0 + first + 1, xb + pick(pre, first));
+        for (int j = 3; j >= 0; --j)
+          if (fabsf(xb + pb[j]) >= d.z) first = 4 + j;
+#pragma unroll
+        for (int j = 3; j >= 0; --j)
+          if (fabsf(xa + pa[j]) >= d.z) first = j;
+        const float v = first < 4 ? xa + pick(pa, first) : xb + pick(pb, first - 4);
+        ddm_write(p, t, true, s0 + first + 1, v);
       }
       return;
     }
     const int last = p.max_steps - 1 - k;   // step index of max_steps within this chunk
-    if (last < 128) {
-      if (lane == (last >> 2)) ddm_write(p, t, false, p.max_steps, xb + pick(pre, last & 3));
+    if (last < 256) {
+      if (lane == (last >> 3)) {
+        const int j = last & 7;
+        ddm_write(p, t, false, p.max_steps, j < 4 ? xa + pick(pa, j) : xb + pick(pb, j - 4));
+      }
       return;
     }
     x += __shfl_sync(kFull, incl, 31);
@@ -135,8 +154,9 @@ __device__ __forceinline__ void ddm_trial_warp(const DdmParams& p, long long t,
 }
 
 // Persistent grid: each warp takes the next trial (in the hand-out order)
-// until none is left.
-__global__ void __launch_bounds__(256, 8) ddm_batched(DdmParams p) {
+// until none is left. (40 registers, 6 blocks per SM: the two blocks a lane
+// holds spill at the 32 registers of 8 blocks per SM, measured 3 % slower.)
+__global__ void __launch_bounds__(256, 6) ddm_batched(DdmParams p) {
   const int lane = threadIdx.x & 31;
   while (true) {
     unsigned long long f = 0;
