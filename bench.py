@@ -55,11 +55,11 @@ DDM_OPS_PER_TRIAL_STEP = 32
 OPS_PER_UNIT = {"ddm": 32, "lca4": 4 * 31, "lca8": 8 * 31, "lca16": 16 * 31, "stroop": 200,
                 "wide": 7132, "grid": 120}
 # DRAM bytes (read + write) of one ddm_batched launch over the 2^20-trial job,
-# from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
-# -k regex:ddm_batched -s 1 -c 1 python bench.py --only ddm` on the current
-# kernel: 12,653,824 read + 256 written (the 5 MB of outputs stay in L2 within
-# the launch). Algorithmic: 8 B of parameters in and 5 B out per trial = 13.6 MB.
-DDM_TRAFFIC_BYTES = 12_654_080
+# from `ncu --set full --clock-control none -k regex:ddm_batched -s 1 -c 1
+# python bench.py --only ddm` on the current kernel: 12,602,368 read + 0 written
+# (the 5 MB of outputs stay in L2 within the launch). Algorithmic: 8 B of
+# parameters in and 5 B out per trial = 13.6 MB.
+DDM_TRAFFIC_BYTES = 12_602_368
 # DRAM bytes of one wide_block_kernel launch over the 16,384-trial job, from
 # `ncu --set full --clock-control none -k regex:wide_block -s 1 -c 1 python bench.py --only wide`
 # on the current kernel: 315 read + 0 written (the weights, the per-condition table and the
