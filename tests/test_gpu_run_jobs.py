@@ -323,3 +323,38 @@ def test_served_grid_searches_grouped_equal_direct_searches(ctx):
             assert np.array_equal(res, host(r2)), (L, T)
     finally:
         B.dg_model_free(model)
+
+
+def test_tune_stats_count_tuned_keys_and_untuned_served_launches(monkeypatch):
+    """A direct run tunes its size bucket (one more tuned key); a served job of
+    an untuned bucket runs the default shape and is counted."""
+    import torch
+    from paper_2110_15425_gb300 import binding as B
+    monkeypatch.setenv("DG_SERVE_GROUP_TRIALS", "0")   # every served job its own launch
+    c = B.dg_create(0)
+    model = B.compose_ddm(c)
+    try:
+        keys0, untuned0 = B.dg_tune_stats(c)
+        assert untuned0 == 0
+        h = _inputs("ddm", 5000, 1)
+        ch = torch.zeros(5000, dtype=torch.int8, device="cuda")
+        st = torch.zeros(5000, dtype=torch.int32, device="cuda")
+        B.dg_run(model, B.run_desc(5000, 3, trial_params=dev(h)), ch, st)
+        keys1, untuned1 = B.dg_tune_stats(c)
+        assert keys1 == keys0 + 1 and untuned1 == 0
+        # a size bucket nothing tuned yet, through the serving thread
+        n = 70000
+        hs = _inputs("ddm", n, 2)
+        j = B.dg_job()
+        j.model = model.value
+        j.run.n_trials = n
+        j.run.seed = 4
+        j.run.trial_params = hs.ctypes.data
+        co, so = np.zeros(n, np.int8), np.zeros(n, np.int32)
+        j.choice, j.step = co.ctypes.data, so.ctypes.data
+        assert B.dg_wait(c, B.dg_submit(c, j), 120000).status == 0
+        keys2, untuned2 = B.dg_tune_stats(c)
+        assert keys2 == keys1 and untuned2 >= 1
+    finally:
+        B.dg_model_free(model)
+        B.dg_destroy(c)
