@@ -95,7 +95,7 @@ def parse():
                     help="run warmup + 1 step only (for ncu launch lists)")
     ap.add_argument("--only", default=None,
                     choices=["ddm", "lca4", "lca8", "lca16", "grid", "stroop", "wide", "refine",
-                             "episodes", "grid_batch", "small_jobs"],
+                             "episodes", "grid_batch", "small_jobs", "extended"],
                     help="one job of this kind, default launch shape, 1 warm + 1 timed launch "
                          "(the small case for per-kernel ncu captures)")
     ap.add_argument("--n", type=int, default=0, help="trials (or candidates) for --only")
@@ -545,6 +545,18 @@ def run_only(args):
             m = B.compose_lca(ctx, w["N"])
             p = cuda(w["I"])
             d = B.run_desc(w["I"].shape[0], w["seed"], trial_params=p)
+        elif k == "extended":
+            w = W.extended_stroop()
+            m = B.compose_extended_stroop(
+                ctx, w["layers"], w["projections"],
+                [dict(W=w["ddm_W"][q:q + 1], bias=w["ddm_bias"], dt=w["ddm_dt"],
+                      sigma=w["ddm_sigma"], bound=w["ddm_bound"], max_steps=w["ddm_max"])
+                 for q in range(2)],
+                rate=w["rate"], noise_sd=w["noise_sd"], stop_layer=w["stop_layer"],
+                stop_threshold=w["stop_threshold"], max_steps=w["max_steps"])
+            p = cuda(w["cond_inputs"])
+            d = B.run_desc(w["n_trials"], w["seed"], cond_inputs=p, n_cond=p.shape[0],
+                           cond_block=w["cond_block"])
         else:
             w = (W.stroop_small() if k == "stroop" else
                  W.stroop_wide(n_trials=args.n or WIDE_TRIALS, hidden=args.hidden))

@@ -162,8 +162,9 @@ struct NetParams {
 };
 cudaError_t launch_net(const NetParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s);
 
-// One lane per trial for networks of at most kLaneMaxU logistic units and no
-// DDM nodes: the incoming-edge table as a dense matrix (W[u][v] the weight of
+// One lane per trial for networks of at most kLaneMaxU logistic units (and
+// their DDM nodes, run after the network in the same lane): the incoming-edge
+// table as a dense matrix (W[u][v] the weight of
 // the edge from unit v into unit u, 0 where there is none), passed by value.
 constexpr int kLaneMaxU = 8;
 struct NetDense {
@@ -171,6 +172,11 @@ struct NetDense {
   float gain[kLaneMaxU], bias[kLaneMaxU];
   float rate, noise, thr;
   int stop_off, stop_size, max_steps;
+  // DDM nodes on the stop layer (Extended Stroop; n_ddm = 0: none), as in NetLayout
+  int n_ddm;
+  float ddm_w[kNetMaxDdm][kNetMaxStop];
+  float ddm_bias[kNetMaxDdm], ddm_dt[kNetMaxDdm], ddm_diffusion[kNetMaxDdm], ddm_z[kNetMaxDdm];
+  int ddm_max[kNetMaxDdm];
 };
 cudaError_t launch_net_lane(const NetParams& p, const NetDense& q, cudaStream_t s);
 // Trials of several jobs of one such network in one launch (p: the model's

@@ -32,6 +32,7 @@
 
 #include "dg_device.cuh"
 #include "dg_internal.h"
+#include "dg_net.cuh"
 
 namespace dg {
 
@@ -48,16 +49,6 @@ __device__ __forceinline__ float unit_noise(const NetParams& p, uint32_t trial, 
   return (d & 1u) ? z1 : z0;
 }
 
-__device__ __forceinline__ float const_net(const NetParams& p, int n_in, long long t, int u) {
-  const long long g = (long long)p.trial0 + t;  // global trial id
-  const int cond = (int)((g / p.cond_block) % p.n_cond);
-  const float* cin = p.cond + (size_t)cond * n_in;
-  const float* w = p.w_in + (size_t)u * n_in;
-  float acc = 0.f;
-  for (int q = 0; q < n_in; ++q) acc = fmaf(__ldg(w + q), __ldg(cin + q), acc);
-  return acc;
-}
-
 __device__ __forceinline__ void stage_layout(const NetParams& p, unsigned char* smem) {
   const int words = (int)(sizeof(NetLayout) / 4);
   const uint32_t* src = reinterpret_cast<const uint32_t*>(p.layout);
@@ -65,13 +56,6 @@ __device__ __forceinline__ void stage_layout(const NetParams& p, unsigned char* 
   for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
   __syncthreads();
 }
-
-struct DdmNode {
-  float adt, diff, z;
-  int max;
-  long long X;      // state before block b, fixed point
-  int b;
-};
 
 __device__ __forceinline__ DdmNode ddm_node_begin(const NetLayout& L, int q, float drift) {
   return DdmNode{drift * L.ddm_dt[q], L.ddm_diffusion[q], L.ddm_z[q], L.ddm_max[q], 0ll, 0};
@@ -269,215 +253,6 @@ __global__ void __launch_bounds__(256) net_group(NetParams p) {
   }
 }
 
-// ---------------------------------------------------------- lane form ---
-
-// One lane per trial (U <= kLaneMaxU units, no DDM nodes): the units' states
-// and outputs in the lane's registers, the dense edge matrix read from the
-// kernel parameters as instruction operands, and the normals of W steps (W U
-// of them: whole Philox blocks, as W U is a multiple of 4) drawn together,
-// the next window's while the current one runs. Each unit's incoming edges are
-// sorted by sender, so the dense sum over senders adds the same nonzero terms
-// in the same order as the edge table of the other forms (a zero term adds
-// exactly nothing) and the lane form agrees with them bit for bit. A lane
-// whose trial ends inside a window takes its next trial at the window's end,
-// so that the lanes of a warp draw their noise together.
-//
-// SS > 0: the stop layer is the last SS units (known when compiling: the stop
-// test and the kept outputs cover those units only); SS = 0: any range.
-// MULTI: the trials of several jobs of the network (the serving loop's
-// groups), one list over the jobs in order; a lane binds its trial's job
-// (condition table, outputs, seed, trial offset) when it takes the trial on.
-template <int U, int SS, bool MULTI>
-__global__ void __launch_bounds__(128) net_lane(NetParams p, const __grid_constant__ NetDense q,
-                                               const __grid_constant__
-                                               typename TableOf<MULTI>::type tab) {
-  __shared__ MultiJob s_job[MULTI ? kMaxMultiJobs : 1];
-  if constexpr (MULTI) copy_jobs(tab, s_job);
-  constexpr int W = (U % 2 == 0) ? 2 : 4;   // steps per window: W U normals in whole blocks
-  constexpr int NZ = W * U;
-  const float rate = q.rate, keep = 1.0f - q.rate, noise = q.noise, thr = q.thr;
-  const int stop_off = SS > 0 ? U - SS : q.stop_off;
-  const int stop_end = SS > 0 ? U : q.stop_off + q.stop_size;
-  const int max_steps = q.max_steps;
-  Logistic lg[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) lg[u] = Logistic::of(q.gain[u], q.bias[u]);
-  float s[U], y[U], netc[U], z[NZ];
-  long long t = 0;
-  int k = 0;
-  uint32_t trial = 0;
-  NetParams pj = p;   // the lane's job: the launch's own, or bound from the table
-  KeyPair kp{};
-  // the normals of steps k0 .. k0 + W - 1 (k0 a multiple of W)
-  auto draw = [&](int k0, float (&out)[NZ]) {
-    const uint32_t b0 = (uint32_t)k0 * (uint32_t)U / 4u;
-#pragma unroll
-    for (int j = 0; j < NZ / 4; ++j) {
-      uint4 w;
-      if constexpr (MULTI)
-        w = noise_block_rk(kp, trial, 0u, b0 + (uint32_t)j);
-      else
-        w = noise_block_rk(p.rk, trial, 0u, b0 + (uint32_t)j);
-      const float4 v = normals4(w);
-      out[4 * j] = v.x;
-      out[4 * j + 1] = v.y;
-      out[4 * j + 2] = v.z;
-      out[4 * j + 3] = v.w;
-    }
-  };
-  auto begin = [&](long long tt) {
-    if constexpr (MULTI) {
-      const MultiJob& J = s_job[multi_job_of(s_job, tab.n_jobs, tt)];
-      pj.cond = J.in;
-      pj.n_cond = J.n_cond;
-      pj.cond_block = J.cond_block;
-      pj.trial0 = J.trial0;
-      pj.choice = J.choice;
-      pj.step = J.step;
-      pj.yout = J.xout;
-      kp.k.k0 = J.k0;
-      kp.k.k1 = J.k1;
-      t = tt - J.start;
-    } else {
-      t = tt;
-    }
-    k = 0;
-    trial = pj.trial0 + (uint32_t)t;
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      s[u] = 0.f;
-      y[u] = lg[u](0.f);
-      netc[u] = const_net(pj, p.n_in, t, u);
-    }
-    draw(0, z);
-  };
-  long long f = fetch_trial(p.cursor, true);
-  bool active = f >= 0 && f < p.n;
-  if (active) begin(f);
-  while (__any_sync(kFull, active)) {
-    bool finished = false;
-    if (active) {
-      // two windows per iteration, the noise buffers in turn: while one
-      // window's steps run, the next window's normals are drawn (independent
-      // of the state). The steps run without branches (a trial that ends
-      // inside the iteration runs on to its end, discarded) so that the
-      // compiler can interleave them with the noise; the ending step's
-      // results are kept by selects.
-      int8_t rc = -1;
-      int rs = 0;
-      float ry[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) ry[u] = 0.f;
-      auto steps = [&](const float (&zw)[NZ]) {
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-          // synchronous: every net input from the previous step's outputs
-          float net[U];
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            float a = netc[u];
-#pragma unroll
-            for (int v = 0; v < U; ++v) a = fmaf(q.W[u][v], y[v], a);
-            net[u] = a;
-          }
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            s[u] = fmaf(keep, s[u], fmaf(rate, net[u], noise * zw[w * U + u]));
-            y[u] = lg[u](s[u]);
-          }
-          ++k;
-          // top-1 (lowest index on ties) and top-2 of the stop layer
-          float v1 = -FLT_MAX, v2 = -FLT_MAX;
-          int i1 = 1 << 20;
-#pragma unroll
-          for (int u = SS > 0 ? U - SS : 0; u < U; ++u) {
-            if (SS > 0 || (u >= stop_off && u < stop_end)) {
-              const bool up = y[u] > v1;
-              v2 = up ? v1 : fmaxf(v2, y[u]);
-              i1 = up ? u - stop_off : i1;
-              v1 = up ? y[u] : v1;
-            }
-          }
-          const bool hit = v1 - v2 > thr;
-          const bool ends = !finished && (hit || k >= max_steps);
-          rc = ends ? (hit ? (int8_t)i1 : (int8_t)-1) : rc;
-          rs = ends ? (hit ? k : max_steps) : rs;
-#pragma unroll
-          for (int u = SS > 0 ? U - SS : 0; u < U; ++u) ry[u] = ends ? y[u] : ry[u];
-          finished = finished || ends;
-        }
-      };
-      float zn[NZ];
-      draw(k + W, zn);
-      steps(z);
-      draw(k + W, z);   // k advanced by W: the window after zn's
-      steps(zn);
-      if (finished) {
-        if (pj.yout) {
-#pragma unroll
-          for (int u = SS > 0 ? U - SS : 0; u < U; ++u)
-            if (SS > 0 || (u >= stop_off && u < stop_end))
-              pj.yout[(size_t)t * p.state_size + (u - stop_off)] = ry[u];
-        }
-        pj.choice[t] = rc;
-        pj.step[t] = rs;
-      }
-    }
-    f = fetch_trial(p.cursor, finished);
-    if (finished) {
-      active = f < p.n;
-      if (active) begin(f);
-    }
-  }
-}
-
-template <int U, int SS, bool MULTI>
-cudaError_t launch_lane_us(const NetParams& p, const NetDense& q, const MultiJobTable* tab,
-                           cudaStream_t s) {
-  int nb = 0;
-  cudaError_t e =
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, net_lane<U, SS, MULTI>, 128, 0);
-  if (e != cudaSuccess) return e;
-  // small jobs: blocks of one warp spread over the SMs (a lane's step is a
-  // chain of a few hundred instructions; warps sharing a scheduler slow it)
-  const int block = p.n <= (long long)num_sms() * 32 * 4 ? 32 : 128;
-  long long grid = (long long)num_sms() * (nb > 0 ? nb : 1) * (128 / block);
-  const long long need = (p.n + block - 1) / block;
-  if (grid > need) grid = need;
-  if constexpr (MULTI)
-    net_lane<U, SS, true><<<(unsigned)grid, block, 0, s>>>(p, q, *tab);
-  else
-    net_lane<U, SS, false><<<(unsigned)grid, block, 0, s>>>(p, q, {});
-  return cudaGetLastError();
-}
-
-template <int U, bool MULTI>
-cudaError_t launch_lane_u(const NetParams& p, const NetDense& q, const MultiJobTable* tab,
-                          cudaStream_t s) {
-  if (q.stop_off + q.stop_size == U) {   // the stop layer is last
-    if (q.stop_size == 2) return launch_lane_us<U, (U >= 2 ? 2 : 0), MULTI>(p, q, tab, s);
-    if (q.stop_size == 3) return launch_lane_us<U, (U >= 3 ? 3 : 0), MULTI>(p, q, tab, s);
-    if (q.stop_size == 4) return launch_lane_us<U, (U >= 4 ? 4 : 0), MULTI>(p, q, tab, s);
-  }
-  return launch_lane_us<U, 0, MULTI>(p, q, tab, s);
-}
-
-template <bool MULTI>
-cudaError_t launch_lane(const NetParams& p, const NetDense& q, const MultiJobTable* tab,
-                        cudaStream_t s) {
-  switch (p.U) {
-    case 1: return launch_lane_u<1, MULTI>(p, q, tab, s);
-    case 2: return launch_lane_u<2, MULTI>(p, q, tab, s);
-    case 3: return launch_lane_u<3, MULTI>(p, q, tab, s);
-    case 4: return launch_lane_u<4, MULTI>(p, q, tab, s);
-    case 5: return launch_lane_u<5, MULTI>(p, q, tab, s);
-    case 6: return launch_lane_u<6, MULTI>(p, q, tab, s);
-    case 7: return launch_lane_u<7, MULTI>(p, q, tab, s);
-    case 8: return launch_lane_u<8, MULTI>(p, q, tab, s);
-  }
-  return cudaErrorInvalidValue;
-}
-
 // --------------------------------------------------------------- plain ---
 
 __global__ void __launch_bounds__(128) net_plain(NetParams p) {
@@ -577,19 +352,6 @@ cudaError_t launch_group(const NetParams& p, const LaunchCfg& cfg, cudaStream_t 
 }
 
 }  // namespace
-
-cudaError_t launch_net_lane(const NetParams& p, const NetDense& q, cudaStream_t s) {
-  if (p.n <= 0) return cudaSuccess;
-  if (p.n_ddm != 0 || p.cursor == nullptr) return cudaErrorInvalidValue;
-  return launch_lane<false>(p, q, nullptr, s);
-}
-
-cudaError_t launch_net_lane_multi(const NetParams& p, const NetDense& q, const MultiJobTable& tab,
-                                  cudaStream_t s) {
-  if (p.n <= 0 || tab.n_jobs < 1 || tab.n_jobs > kMaxMultiJobs) return cudaErrorInvalidValue;
-  if (p.n_ddm != 0 || p.cursor == nullptr) return cudaErrorInvalidValue;
-  return launch_lane<true>(p, q, &tab, s);
-}
 
 cudaError_t launch_net(const NetParams& p, int mode, const LaunchCfg& cfg, cudaStream_t s) {
   if (p.n <= 0) return cudaSuccess;

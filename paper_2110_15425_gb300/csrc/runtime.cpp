@@ -440,8 +440,8 @@ std::vector<dg::LaunchCfg> grid_candidates(long long n_cand, int lanes) {
 
 // ---------------------------------------------------------- run paths ---
 
-// Small networks without DDM nodes run one lane per trial unless
-// DG_NET_LANE=0 (then a lane group per trial, as networks with DDM nodes do).
+// Small networks (with or without DDM nodes) run one lane per trial unless
+// DG_NET_LANE=0 (then a lane group per trial).
 bool net_lane_enabled() {
   const char* e = getenv("DG_NET_LANE");
   return !e || atoi(e) != 0;
@@ -467,6 +467,15 @@ dg::NetDense net_dense(const dg::NetLayout& L) {
   q.stop_off = L.stop_off;
   q.stop_size = L.stop_size;
   q.max_steps = L.max_steps;
+  q.n_ddm = L.n_ddm;
+  for (int n = 0; n < L.n_ddm; ++n) {
+    for (int i = 0; i < L.stop_size; ++i) q.ddm_w[n][i] = L.ddm_w[n][i];
+    q.ddm_bias[n] = L.ddm_bias[n];
+    q.ddm_dt[n] = L.ddm_dt[n];
+    q.ddm_diffusion[n] = L.ddm_diffusion[n];
+    q.ddm_z[n] = L.ddm_z[n];
+    q.ddm_max[n] = L.ddm_max[n];
+  }
   return q;
 }
 
@@ -614,7 +623,7 @@ dg_status run_device(dg_model* m, const dg_run_desc* d, int8_t* choice, int32_t*
     p.yout = fs;
     p.cursor = mode == DG_MODE_BATCHED ? sc->cursor() : nullptr;
     if (mode == DG_MODE_BATCHED) DG_CUDA(cudaMemsetAsync(sc->cursor(), 0, 8, s));
-    if (mode == DG_MODE_BATCHED && net_lane_model(m) && net_lane_enabled()) {
+    if (mode == DG_MODE_BATCHED && m->layout.U <= dg::kLaneMaxU && net_lane_enabled()) {
       DG_CUDA(dg::launch_net_lane(p, net_dense(m->layout), s));
       return DG_OK;
     }

@@ -110,13 +110,17 @@ def test_extended_ragged_and_strong(ctx, orc, threads):
             _compare(c, s, fs, _ref(orc, w, 999, threads, bound=bound))
 
 
-def test_extended_batched_equals_plain_bitwise(ctx):
+@pytest.mark.parametrize("lane", ["1", "0"])
+def test_extended_batched_equals_plain_bitwise(ctx, monkeypatch, lane):
+    """The batched form (one lane per trial, or a lane group per trial with
+    DG_NET_LANE=0) gives the plain form's results bit for bit."""
     from paper_2110_15425_gb300 import workloads as W
+    monkeypatch.setenv("DG_NET_LANE", lane)
     w = W.extended_stroop(weight_seed=4)
     a = _gpu(ctx, w, w["n_trials"], 0)
     b = _gpu(ctx, w, w["n_trials"], 1)
     for u, v in zip(a, b):
-        assert np.array_equal(u, v)
+        assert np.array_equal(u.view(np.uint8), v.view(np.uint8))
 
 
 def test_extended_a_equals_b(ctx):
