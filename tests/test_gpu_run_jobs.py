@@ -217,14 +217,20 @@ def test_served_small_jobs_grouped_equal_direct_runs(ctx, pinned):
     """Many small DDM and LCA jobs of several models submitted at once: the
     serving loop groups them into multi-job launches; every job's outputs
     (final states included) equal a direct dg_run of the job. With pinned host
-    buffers the kernels read and write them in place."""
+    buffers the kernels read and write them in place (a job with any pageable
+    buffer is staged through device copies, in the same group)."""
     import torch
     from paper_2110_15425_gb300 import binding as B
     rng = np.random.default_rng(12)
     keep = []
 
+    count = [0]
+
     def buf(a):
-        if not pinned:
+        # pinned: every seventh buffer stays pageable, so that groups mix jobs
+        # used in place with staged ones
+        count[0] += 1
+        if not pinned or count[0] % 7 == 0:
             return a
         t = torch.from_numpy(a).pin_memory()
         keep.append(t)
