@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kRowThreads, 1) wide_rows_kernel(WideParams p)
         const int h = q * HQ + 8 * c + i;
         float& sv = s[8 * c + i];
         const float y = lg_h(sv);
-        sv = fmaf(keep, sv, fmaf(p.rate, net_sm[h * kRows + r], p.noise * e[i]));
+        sv = fmaf(keep, sv, fmaf(p.noise, e[i], p.rate * net_sm[h * kRows + r]));
 #pragma unroll
         for (int n = 0; n < kR; ++n) acc[n] = fmaf(W[n * H + h], y, acc[n]);
       }
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(BLay<H>::THREADS, 1) wide_block_kernel(WidePar
   const float keep = 1.0f - p.rate;
   const Logistic lg_h = Logistic::of(p.gain_h, p.bias_h), lg_r = Logistic::of(p.gain_r, p.bias_r);
 
-  float s[4] = {0.f, 0.f, 0.f, 0.f}, net[4] = {0.f, 0.f, 0.f, 0.f};   // hidden role
+  float s[4] = {0.f, 0.f, 0.f, 0.f}, net[4] = {0.f, 0.f, 0.f, 0.f};   // hidden role (net: rate net)
   float4 zpre = make_float4(0.f, 0.f, 0.f, 0.f);
   bool pre_ok = false;
   float sr[2] = {0.f, 0.f};                                           // response role
@@ -418,10 +418,12 @@ __global__ void __launch_bounds__(BLay<H>::THREADS, 1) wide_block_kernel(WidePar
         const long long g = (long long)p.trial0 + ht;
         const float4 nt = __ldg(reinterpret_cast<const float4*>(
             p.net_table + (size_t)((g / p.cond_block) % p.n_cond) * H + 4 * hq));
-        net[0] = nt.x;
-        net[1] = nt.y;
-        net[2] = nt.z;
-        net[3] = nt.w;
+        // rate net, constant through the trial (the hidden layer's inputs are
+        // clamped), formed once
+        net[0] = p.rate * nt.x;
+        net[1] = p.rate * nt.y;
+        net[2] = p.rate * nt.z;
+        net[3] = p.rate * nt.w;
 #pragma unroll
         for (int i = 0; i < 4; ++i) s[i] = 0.f;
       }
@@ -433,7 +435,7 @@ __global__ void __launch_bounds__(BLay<H>::THREADS, 1) wide_block_kernel(WidePar
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             y[i] = lg_h(s[i]);
-            s[i] = fmaf(keep, s[i], fmaf(p.rate, net[i], p.noise * e[i]));
+            s[i] = fmaf(keep, s[i], fmaf(p.noise, e[i], net[i]));
           }
         }
         uint2 hi, lo;
