@@ -62,10 +62,10 @@ OPS_PER_UNIT = {"ddm": 32, "lca4": 4 * 31, "lca8": 8 * 31, "lca16": 16 * 31, "st
 DDM_TRAFFIC_BYTES = 12_602_368
 # DRAM bytes of one wide_block_kernel launch over the 16,384-trial job, from
 # `ncu --set full --clock-control none -k regex:wide_block -s 1 -c 1 python bench.py --only wide`
-# on the current kernel: 315 read + 0 written (the weights, the per-condition table and the
+# on the current kernel: 316 read + 0 written (the weights, the per-condition table and the
 # outputs stay in L2). Algorithmic: the weights (16 KB BF16 operand image, 32 KB hidden
 # weights), the 256 condition rows and 5 B of outputs per trial: 0.16 MB.
-WIDE_TRAFFIC_BYTES = 315
+WIDE_TRAFFIC_BYTES = 316
 TRAFFIC_BYTES = {"ddm": DDM_TRAFFIC_BYTES, "wide": WIDE_TRAFFIC_BYTES}
 LANES_PER_SM = 128
 PEAK_OPS = [40.27e12]   # SMs x lanes x max SM clock, set from the device in main()
