@@ -69,14 +69,16 @@ WIDE_TRAFFIC_BYTES = 316
 TRAFFIC_BYTES = {"ddm": DDM_TRAFFIC_BYTES, "wide": WIDE_TRAFFIC_BYTES}
 LANES_PER_SM = 128
 PEAK_OPS = [40.27e12]   # SMs x lanes x max SM clock, set from the device in main()
-# The pass's jobs, longest first. Graph branches are created (and served jobs
-# submitted) in this order: the wide network's CTAs take their SMs before the
-# persistent kernels fill the GPU (2-4 % shorter passes than job order).
-LONGEST_FIRST = ("wide", "ddm", "lca16", "lca8", "lca4", "grid", "stroop")
+# Order in which the pass's graph branches are created (and served jobs
+# submitted). The LCA jobs go first: their longest trials end in a
+# latency-bound tail on a few SMs, which then runs beside the later jobs
+# instead of after them (8.21-8.23 ms per pass against 8.34-8.37 ms with the
+# wide network first, two runs each; job order was 2-4 % slower still).
+JOB_ORDER = ("lca4", "lca8", "lca16", "ddm", "wide", "grid", "stroop")
 
 
-def longest_first(jobs):
-    rank = {n: i for i, n in enumerate(LONGEST_FIRST)}
+def in_job_order(jobs):
+    rank = {n: i for i, n in enumerate(JOB_ORDER)}
     return sorted(jobs, key=lambda j: rank.get(j["name"], len(rank)))
 WIDE_TRIALS = 16384
 
@@ -220,7 +222,7 @@ class Step:
         B = self.B
         if self.batch is None:
             self.batch = B.dg_batch_create(ctx)
-            for j in longest_first(self.jobs):
+            for j in in_job_order(self.jobs):
                 if j.get("grid"):
                     B.dg_batch_add_grid(self.batch, j["model"], j["desc"], j["out"]["result"])
                 else:
@@ -948,7 +950,7 @@ def e2e_serving(B, torch, ctx, step, all_ts, world, rank):
     copied back, every step."""
     host_jobs = []
     h2d = d2h = 0
-    for j in longest_first(step.jobs):
+    for j in in_job_order(step.jobs):
         job = B.dg_job()
         job.model = j["model"].value
         keep = []
