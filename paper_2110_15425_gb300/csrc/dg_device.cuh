@@ -144,11 +144,32 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& z0, 
   z1 = -r * approx_sin(ang);
 }
 
+// Two Box-Muller pairs (words x, y and z, w) evaluated side by side: every
+// FP32 add, multiply and fma of box_muller above done once for both pairs by
+// the paired instructions of this architecture, which round each component
+// exactly as the scalar instruction does, so the normals keep their bits.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
 __device__ __forceinline__ float4 normals4(uint4 w) {
-  float4 z;
-  box_muller(w.x, w.y, z.x, z.y);
-  box_muller(w.z, w.w, z.z, z.w);
-  return z;
+  const float2 u = __fadd2_rn(f2(one_plus(w.x), one_plus(w.z)), f2(-0.99999994039535522f));
+  const float2 v = __fadd2_rn(f2(1.0f), f2(-u.x, -u.y));
+  // -2 ln u from the hardware log2, or the series in v = 1 - u near u = 1
+  const float2 y0 = __fmul2_rn(f2(-1.38629436111989062f), f2(approx_lg2(u.x), approx_lg2(u.y)));
+  float2 q = __ffma2_rn(v, f2(0.4f), f2(0.5f));
+  q = __ffma2_rn(v, q, f2(2.0f / 3.0f));
+  q = __ffma2_rn(v, q, f2(1.0f));
+  q = __ffma2_rn(v, q, f2(2.0f));
+  q = __fmul2_rn(v, q);
+  const float2 y = f2(v.x < 0x1p-6f ? q.x : y0.x, v.y < 0x1p-6f ? q.y : y0.y);
+  const float2 r = __fmul2_rn(y, f2(approx_rsqrt(y.x), approx_rsqrt(y.y)));
+  const float2 ang = __ffma2_rn(f2(6.28318530717958648f),
+                                __fadd2_rn(f2(one_plus(w.y), one_plus(w.w)), f2(-1.5f)),
+                                f2(6.28318530717958648f * 0x1p-24f));
+  const float2 nr = f2(-r.x, -r.y);
+  const float2 zc = __fmul2_rn(nr, f2(approx_cos(ang.x), approx_cos(ang.y)));
+  const float2 zs = __fmul2_rn(nr, f2(approx_sin(ang.x), approx_sin(ang.y)));
+  return make_float4(zc.x, zs.x, zc.y, zs.y);
 }
 
 __device__ __forceinline__ float pick4(const float4& z, uint32_t lane) {
