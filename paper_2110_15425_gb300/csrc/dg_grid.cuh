@@ -109,38 +109,39 @@ __device__ __forceinline__ void warp_pair_sum(float& hi, float& lo) {
   lo = __shfl_sync(kFull, lo, 0);
 }
 
+// The x and y components of the 2-D vectors below go through the paired
+// FP32 instructions of this architecture (each component rounded as the
+// scalar instruction), so an evaluation keeps its bits.
+
 // unit(v), with unit(v) = 0 for |v|^2 below the smallest normal number (the
 // hardware reciprocal square root, flush-to-zero form: a position difference
 // that small is zero for this model)
-__device__ __forceinline__ void unit2(float vx, float vy, float& ox, float& oy) {
-  const float n2 = vx * vx + vy * vy;
+__device__ __forceinline__ float2 unit2(float2 v) {
+  const float n2 = v.x * v.x + v.y * v.y;
   if (n2 >= FLT_MIN) {
     const float r = approx_rsqrt(n2);
-    ox = vx * r;
-    oy = vy * r;
-  } else {
-    ox = 0.f;
-    oy = 0.f;
+    return __fmul2_rn(v, f2(r));
   }
+  return f2(0.f);
 }
 
 // Perception and Action nodes: X^_e = X_e + sd_e eps_{2e+c} (normals 0..5 of
 // stream (trial, cand) starting at Philox block block0), then
 // act = unit(unit(Y^ - P^) - weight unit(D^ - P^)).
-__device__ __forceinline__ void pp_act(const PhiloxKeys& rk, uint32_t trial, uint32_t cand,
-                                       uint32_t block0, const float* X, float sd0, float sd1,
-                                       float sd2, float weight, float& ax, float& ay) {
+__device__ __forceinline__ float2 pp_act(const PhiloxKeys& rk, uint32_t trial, uint32_t cand,
+                                         uint32_t block0, const float* X, float sd0, float sd1,
+                                         float sd2, float weight) {
   const float4 z = normals4(noise_block_rk(rk, trial, cand, block0));
   const uint4 w1 = noise_block_rk(rk, trial, cand, block0 + 1u);
   float z4, z5;
   box_muller(w1.x, w1.y, z4, z5);
-  const float phx = fmaf(sd0, z.x, X[0]), phy = fmaf(sd0, z.y, X[1]);
-  const float dhx = fmaf(sd1, z.z, X[2]), dhy = fmaf(sd1, z.w, X[3]);
-  const float yhx = fmaf(sd2, z4, X[4]), yhy = fmaf(sd2, z5, X[5]);
-  float uyx, uyy, udx, udy;
-  unit2(yhx - phx, yhy - phy, uyx, uyy);
-  unit2(dhx - phx, dhy - phy, udx, udy);
-  unit2(fmaf(-weight, udx, uyx), fmaf(-weight, udy, uyy), ax, ay);
+  const float2 ph = __ffma2_rn(f2(sd0), f2(z.x, z.y), f2(X[0], X[1]));
+  const float2 dh = __ffma2_rn(f2(sd1), f2(z.z, z.w), f2(X[2], X[3]));
+  const float2 yh = __ffma2_rn(f2(sd2), f2(z4, z5), f2(X[4], X[5]));
+  const float2 nph = f2(-ph.x, -ph.y);
+  const float2 uy = unit2(__fadd2_rn(yh, nph));
+  const float2 ud = unit2(__fadd2_rn(dh, nph));
+  return unit2(__ffma2_rn(f2(-weight), ud, uy));
 }
 
 // Objective node: -|P + act - Y| - sum_e a_e^2 (cost given), true P and Y.
@@ -148,11 +149,9 @@ __device__ __forceinline__ float pp_outcome_at(const PhiloxKeys& rk, uint32_t tr
                                                uint32_t cand, uint32_t block0, const float* X,
                                                float sd0, float sd1, float sd2, float weight,
                                                float cost) {
-  float ax, ay;
-  pp_act(rk, trial, cand, block0, X, sd0, sd1, sd2, weight, ax, ay);
-  const float nx = (X[0] + ax) - X[4];
-  const float ny = (X[1] + ay) - X[5];
-  return -approx_sqrt(nx * nx + ny * ny) - cost;
+  const float2 a = pp_act(rk, trial, cand, block0, X, sd0, sd1, sd2, weight);
+  const float2 n = __fadd2_rn(__fadd2_rn(f2(X[0], X[1]), a), f2(-X[4], -X[5]));
+  return -approx_sqrt(n.x * n.x + n.y * n.y) - cost;
 }
 
 }  // namespace dg
