@@ -485,31 +485,31 @@ __global__ void __launch_bounds__(BLay<H>::THREADS, 1) wide_block_kernel(WidePar
     }
 
     // while the MMA runs: the normals of the next block's first step, for a
-    // slot that keeps its trial (used only if it does)
+    // slot that keeps its trial (used only if it does), drawn by the warps
+    // that issue no MMA (the issuing lanes' warps take no other work here:
+    // a thread takes a few hundred cycles to issue each MMA)
     pre_ok = false;
-    if (hidden && ht >= 0 && hk + kBlkSteps < p.max_steps) {
+    if (warp >= kAcc && hidden && ht >= 0 && hk + kBlkSteps < p.max_steps) {
       zpre = normals4(noise_block_rk(p.rk, p.trial0 + (uint32_t)ht, 0u,
                                      (uint32_t)(hk + kBlkSteps) * (uint32_t)(L::U / 4) +
                                          (uint32_t)hq));
       pre_ok = true;
     }
-    // and the response units' noise of every row, sigma eps, drawn by all
-    // threads: thread (row, Philox block i, pair h) computes block i of the
-    // row's step (both pairs of a block are drawn by two threads) and its h-th
-    // Box-Muller pair
-    for (int w = tid; w < 4 * kRows * 2; w += L::THREADS) {
-      const int row = w & (kRows - 1), i = (w >> 7) & 3, h = w >> 9;
+    // and the response units' noise of every row, sigma eps, by the threads
+    // of warps 4 on: item (row, Philox block i) draws units 4 i .. 4 i + 3 of
+    // the row's step
+    for (int w = tid - kRows; w >= 0 && w < 4 * kRows; w += L::THREADS - kRows) {
+      const int row = w & (kRows - 1), i = w >> 7;
       const int rs = row & (kSlots - 1), rj = row / kSlots;
       const long long rt = sh.slot[rs];
       const int rst = sh.kstep[rs] + rj;
-      float z0 = 0.f, z1 = 0.f;
-      if (rt >= 0 && rst < p.max_steps) {
-        const uint4 wd = noise_block_rk(p.rk, p.trial0 + (uint32_t)rt, 0u,
-                                        (uint32_t)rst * (uint32_t)(L::U / 4) + (uint32_t)(H / 4 + i));
-        box_muller(h ? wd.z : wd.x, h ? wd.w : wd.y, z0, z1);
-      }
-      *reinterpret_cast<float2*>(rnoise + row * 20 + 4 * i + 2 * h) =
-          make_float2(p.noise * z0, p.noise * z1);
+      float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (rt >= 0 && rst < p.max_steps)
+        z = normals4(noise_block_rk(p.rk, p.trial0 + (uint32_t)rt, 0u,
+                                    (uint32_t)rst * (uint32_t)(L::U / 4) + (uint32_t)(H / 4 + i)));
+      const float2 lo2 = __fmul2_rn(f2(p.noise), f2(z.x, z.y));
+      const float2 hi2 = __fmul2_rn(f2(p.noise), f2(z.z, z.w));
+      *reinterpret_cast<float4*>(rnoise + row * 20 + 4 * i) = make_float4(lo2.x, lo2.y, hi2.x, hi2.y);
     }
     __syncthreads();   // every row's response noise is in shared memory
 
@@ -529,6 +529,8 @@ __global__ void __launch_bounds__(BLay<H>::THREADS, 1) wide_block_kernel(WidePar
       }
       __syncwarp();
       tc_fence_after();
+      // the chains summed in order, ((c0 + c1) + c2) + c3, and u = rate D +
+      // sigma eps, two columns at a time on the paired FP32 instructions
       float d[16];
       tmem_ld16(tmem_d + lane_base, d);
 #pragma unroll
@@ -538,7 +540,11 @@ __global__ void __launch_bounds__(BLay<H>::THREADS, 1) wide_block_kernel(WidePar
           float d2[8];
           tmem_ld8(tmem_d + lane_base + (uint32_t)(c * kR + 8 * h), d2);
 #pragma unroll
-          for (int n = 0; n < 8; ++n) d[8 * h + n] += d2[n];
+          for (int n = 0; n < 8; n += 2) {
+            const float2 t = __fadd2_rn(f2(d[8 * h + n], d[8 * h + n + 1]), f2(d2[n], d2[n + 1]));
+            d[8 * h + n] = t.x;
+            d[8 * h + n + 1] = t.y;
+          }
         }
       tc_fence_before();
       float* u = uy + rj * kUYStep + rs * 20;
@@ -546,12 +552,9 @@ __global__ void __launch_bounds__(BLay<H>::THREADS, 1) wide_block_kernel(WidePar
 #pragma unroll
       for (int n = 0; n < kR; n += 4) {
         const float4 e = *reinterpret_cast<const float4*>(ne + n);
-        float4 v;
-        v.x = fmaf(p.rate, d[n], e.x);
-        v.y = fmaf(p.rate, d[n + 1], e.y);
-        v.z = fmaf(p.rate, d[n + 2], e.z);
-        v.w = fmaf(p.rate, d[n + 3], e.w);
-        *reinterpret_cast<float4*>(u + n) = v;
+        const float2 a = __ffma2_rn(f2(p.rate), f2(d[n], d[n + 1]), f2(e.x, e.y));
+        const float2 b = __ffma2_rn(f2(p.rate), f2(d[n + 2], d[n + 3]), f2(e.z, e.w));
+        *reinterpret_cast<float4*>(u + n) = make_float4(a.x, a.y, b.x, b.y);
       }
       bar_sync_named(1, kRows);
 
@@ -563,16 +566,24 @@ __global__ void __launch_bounds__(BLay<H>::THREADS, 1) wide_block_kernel(WidePar
           sr[1] = 0.f;
         }
         if (sh.slot[s2] >= 0) {
+          // both units on the paired FP32 instructions: the same roundings as
+          // fmaf(keep, s, u) and the logistic's fma and add
+          float2 sv = f2(sr[0], sr[1]);
 #pragma unroll
           for (int j = 0; j < kBlkSteps; ++j) {
             float2* q2 = reinterpret_cast<float2*>(uy + j * kUYStep + s2 * 20 + 2 * p2);
-            float2 v = *q2;
-            sr[0] = fmaf(keep, sr[0], v.x);
-            sr[1] = fmaf(keep, sr[1], v.y);
-            v.x = lg_r(sr[0]);
-            v.y = lg_r(sr[1]);
-            *q2 = v;
+            sv = __ffma2_rn(f2(keep), sv, *q2);
+            const float2 t = __ffma2_rn(sv, f2(lg_r.c1), f2(lg_r.c0));
+            float e0, e1, y0, y1;
+            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e0) : "f"(t.x));
+            asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(t.y));
+            const float2 den = __fadd2_rn(f2(1.0f), f2(e0, e1));
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(den.x));
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(den.y));
+            *q2 = f2(y0, y1);
           }
+          sr[0] = sv.x;
+          sr[1] = sv.y;
         }
       }
       bar_sync_named(1, kRows);
