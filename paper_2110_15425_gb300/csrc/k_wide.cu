@@ -275,7 +275,11 @@ constexpr int kSlots = 16;
 constexpr int kBlkSteps = 8;
 static_assert(kSlots * kBlkSteps == kRows, "one MMA tile per block");
 constexpr int kUYStep = kSlots * 20 + 4;   // floats per step in the u/y scratch (padded)
-constexpr int kAcc = 4;                     // independent MMA accumulation chains
+// independent MMA accumulation chains, each issued by lane 0 of its own warp
+// (a thread takes a few hundred cycles to issue one of these MMAs): eight at
+// H = 256, four below (where eight cost the response phase spills)
+template <int H>
+constexpr int acc_chains() { return H == 256 ? 8 : 4; }
 
 template <int H>
 struct BLay {
@@ -283,6 +287,7 @@ struct BLay {
   static constexpr int K2 = 2 * H;
   static constexpr int U = H + kR;
   static constexpr int THREADS = kSlots * Q > kRows ? kSlots * Q : kRows;
+  static constexpr int ACC = acc_chains<H>();
   // offsets from the 1024-byte aligned start of dynamic shared memory
   static constexpr uint32_t B_OFF = 0;
   static constexpr uint32_t B_BYTES = kR * K2 * 2;      // bf16 W image, 16 x K2, swizzled
@@ -342,6 +347,7 @@ template <int H>
 __global__ void __launch_bounds__(BLay<H>::THREADS, 1) wide_block_kernel(WideParams p) {
   using L = BLay<H>;
   constexpr int Q = L::Q;
+  constexpr int kAcc = L::ACC;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ BlockShared sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -496,9 +502,10 @@ __global__ void __launch_bounds__(BLay<H>::THREADS, 1) wide_block_kernel(WidePar
       pre_ok = true;
     }
     // and the response units' noise of every row, sigma eps, by the threads
-    // of warps 4 on: item (row, Philox block i) draws units 4 i .. 4 i + 3 of
-    // the row's step
-    for (int w = tid - kRows; w >= 0 && w < 4 * kRows; w += L::THREADS - kRows) {
+    // of the warps that issue no MMA: item (row, Philox block i) draws units
+    // 4 i .. 4 i + 3 of the row's step
+    constexpr int kNoise0 = 32 * kAcc < L::THREADS - kRows ? 32 * kAcc : L::THREADS - kRows;
+    for (int w = tid - kNoise0; w >= 0 && w < 4 * kRows; w += L::THREADS - kNoise0) {
       const int row = w & (kRows - 1), i = w >> 7;
       const int rs = row & (kSlots - 1), rj = row / kSlots;
       const long long rt = sh.slot[rs];
@@ -533,17 +540,23 @@ __global__ void __launch_bounds__(BLay<H>::THREADS, 1) wide_block_kernel(WidePar
       // sigma eps, two columns at a time on the paired FP32 instructions
       float d[16];
       tmem_ld16(tmem_d + lane_base, d);
+      // (16 columns per load at H = 256; 8 below, where the wider load
+      // costs the hidden role's registers spills)
+      constexpr int kLd = H == 256 ? 16 : 8;
 #pragma unroll
       for (int c = 1; c < kAcc; ++c)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float d2[8];
-          tmem_ld8(tmem_d + lane_base + (uint32_t)(c * kR + 8 * h), d2);
+        for (int h = 0; h < 16 / kLd; ++h) {
+          float d2[kLd];
+          if constexpr (kLd == 16)
+            tmem_ld16(tmem_d + lane_base + (uint32_t)(c * kR), d2);
+          else
+            tmem_ld8(tmem_d + lane_base + (uint32_t)(c * kR + 8 * h), d2);
 #pragma unroll
-          for (int n = 0; n < 8; n += 2) {
-            const float2 t = __fadd2_rn(f2(d[8 * h + n], d[8 * h + n + 1]), f2(d2[n], d2[n + 1]));
-            d[8 * h + n] = t.x;
-            d[8 * h + n + 1] = t.y;
+          for (int n = 0; n < kLd; n += 2) {
+            const float2 t = __fadd2_rn(f2(d[kLd * h + n], d[kLd * h + n + 1]), f2(d2[n], d2[n + 1]));
+            d[kLd * h + n] = t.x;
+            d[kLd * h + n + 1] = t.y;
           }
         }
       tc_fence_before();
