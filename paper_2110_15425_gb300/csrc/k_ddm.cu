@@ -63,10 +63,14 @@ __device__ __forceinline__ DdmTrial ddm_begin(const DdmParams& p, long long t) {
 __device__ __forceinline__ void block_partials(const DdmParams& p, long long t, uint32_t block,
                                                float adt, float (&pre)[4]) {
   const float4 e = normals4(philox_rk(make_uint4(p.trial0 + (uint32_t)t, 0u, block, 0u), p.rk));
-  pre[0] = fmaf(p.diffusion, e.x, adt);
-  pre[1] = pre[0] + fmaf(p.diffusion, e.y, adt);
-  pre[2] = pre[1] + fmaf(p.diffusion, e.z, adt);
-  pre[3] = pre[2] + fmaf(p.diffusion, e.w, adt);
+  // the four increments A dt + sigma sqrt(dt) eps by two paired fmas (each
+  // component rounded as fmaf), then their running sums in order
+  const float2 ia = __ffma2_rn(f2(p.diffusion), f2(e.x, e.y), f2(adt));
+  const float2 ib = __ffma2_rn(f2(p.diffusion), f2(e.z, e.w), f2(adt));
+  pre[0] = ia.x;
+  pre[1] = pre[0] + ia.y;
+  pre[2] = pre[1] + ib.x;
+  pre[3] = pre[2] + ib.y;
 }
 
 __device__ __forceinline__ float pick(const float (&v)[4], int i) {
