@@ -434,15 +434,16 @@ __global__ void __launch_bounds__(BLay<H>::THREADS, 1) wide_block_kernel(WidePar
         for (int i = 0; i < 4; ++i) s[i] = 0.f;
       }
       // one step: y(t-1) of the thread's units into A row (j, hs), then the update
+      // every step of the block is taken without a test against max_steps: a
+      // running trial starts a block below it and stops at it at the latest,
+      // and the rows after a trial's stopping step are never read
       auto step = [&](int j, float4 z) {
-        float y[4] = {0.f, 0.f, 0.f, 0.f};
-        if (hk + j < p.max_steps) {   // 0-based step hk + j
-          const float e[4] = {z.x, z.y, z.z, z.w};
+        float y[4];
+        const float e[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            y[i] = lg_h(s[i]);
-            s[i] = fmaf(keep, s[i], fmaf(p.noise, e[i], net[i]));
-          }
+        for (int i = 0; i < 4; ++i) {
+          y[i] = lg_h(s[i]);
+          s[i] = fmaf(keep, s[i], fmaf(p.noise, e[i], net[i]));
         }
         uint2 hi, lo;
         split2(y[0], y[1], hi.x, lo.x);
@@ -458,8 +459,7 @@ __global__ void __launch_bounds__(BLay<H>::THREADS, 1) wide_block_kernel(WidePar
 #pragma unroll 2
       for (int j = 1; j < kBlkSteps; ++j) {
         blk += (uint32_t)(L::U / 4);
-        step(j, hk + j < p.max_steps ? normals4(noise_block_rk(p.rk, tg, 0u, blk))
-                                     : make_float4(0.f, 0.f, 0.f, 0.f));
+        step(j, normals4(noise_block_rk(p.rk, tg, 0u, blk)));
       }
     }
     // (an empty slot's rows keep earlier values: their products are not read)
