@@ -109,10 +109,12 @@ struct Lca {
     // computes the same bits (no contraction left to the compiler)
     const float gr = p.dt * (p.inhibition - p.leak);   // g
     const float c = p.dt * p.inhibition;
-    // adjacent accumulators by the paired FP32 instructions (each component
-    // rounded as the scalar fmaf and add), an odd last one alone
+    // with eight or more accumulators per lane, adjacent ones by the paired
+    // FP32 instructions (each component rounded as the scalar fmaf and add;
+    // measured faster at N = 8, slower at N = 4); the rest one at a time
+    constexpr int NP = NU >= 8 ? NU / 2 * 2 : 0;   // accumulators taken in pairs
 #pragma unroll
-    for (int i = 0; i + 1 < NU; i += 2) {
+    for (int i = 0; i + 1 < NP; i += 2) {
       const float2 xi = make_float2(x[i], x[i + 1]);
       float2 v = __ffma2_rn(make_float2(-c, -c), make_float2(S, S), make_float2(I[i], I[i + 1]));
       v = __ffma2_rn(make_float2(p.diffusion, p.diffusion), make_float2(e[i], e[i + 1]), v);
@@ -124,10 +126,11 @@ struct Lca {
       x[i] = v.x;
       x[i + 1] = v.y;
     }
-    if constexpr (NU % 2 == 1) {
-      float v = x[NU - 1] + fmaf(gr, x[NU - 1], fmaf(p.diffusion, e[NU - 1], fmaf(-c, S, I[NU - 1])));
+#pragma unroll
+    for (int i = NP; i < NU; ++i) {
+      float v = x[i] + fmaf(gr, x[i], fmaf(p.diffusion, e[i], fmaf(-c, S, I[i])));
       if (p.rectify) v = fmaxf(v, 0.f);
-      x[NU - 1] = v;
+      x[i] = v;
     }
     if (N == 1 && p.two_sided) {
       if (fabsf(x[0]) >= p.threshold) {
