@@ -62,11 +62,11 @@ OPS_PER_UNIT = {"ddm": 32, "lca4": 4 * 31, "lca8": 8 * 31, "lca16": 16 * 31, "st
 DDM_TRAFFIC_BYTES = 12_603_136
 # DRAM bytes of one wide_block_kernel launch over the 16,384-trial job, from
 # `ncu --set full --clock-control none -k regex:wide_block -s 1 -c 1 python bench.py --only wide`
-# on the current kernel: 331,264 read (10,352 sectors) + 0 written (the outputs stay in
+# on the current kernel: 314,112 read (9,816 sectors) + 0 written (the outputs stay in
 # L2 within the launch). Algorithmic: the weights (16 KB BF16 operand image, 32 KB hidden
 # weights), the 256 condition rows and 5 B of outputs per trial: 0.16 MB; the reads are
-# about twice that, a few hundred KB against a 3.4 ms ALU-bound launch.
-WIDE_TRAFFIC_BYTES = 331_264
+# about twice that, a few hundred KB against a 3 ms ALU-bound launch.
+WIDE_TRAFFIC_BYTES = 314_112
 TRAFFIC_BYTES = {"ddm": DDM_TRAFFIC_BYTES, "wide": WIDE_TRAFFIC_BYTES}
 LANES_PER_SM = 128
 PEAK_OPS = [40.27e12]   # SMs x lanes x max SM clock, set from the device in main()
