@@ -260,9 +260,11 @@ cudaError_t launch_rows(const WideParams& p, cudaStream_t s) {
 //      slot's trial (state and constant net input in registers) and runs them
 //      through the block's kBlkSteps steps, writing y(t-1) of each step as a
 //      bfloat16 hi + lo pair into A row (j, s);
-//   2. one thread issues the MMAs D = A W^T (K = 2H) into TMEM;
-//   3. response (warps 0-3, one thread per row, which is its TMEM lane): the
-//      16 response normals of the row are drawn while the MMA runs; then
+//   2. lane 0 of each of the first kAcc warps issues one accumulation chain
+//      of the MMAs D = A W^T (K = 2H, split in kAcc parts) into TMEM, while
+//      the other warps draw the response units' noise of every row and the
+//      next block's first-step normals;
+//   3. response (warps 0-3, one thread per row, which is its TMEM lane):
 //      u = rate D + noise eps per row, the response integrators advance
 //      through the block's steps (thread (slot, unit pair)), and the stop rule
 //      is applied at every step (thread (slot, step)); the first stopping
@@ -469,8 +471,8 @@ __global__ void __launch_bounds__(BLay<H>::THREADS, 1) wide_block_kernel(WidePar
 
     // ---------------------------------------------------------------- 2.
     // K is split in kAcc parts, each an independent accumulation chain in its
-    // own TMEM columns, issued by lane 0 of warp c (one warp per scheduler) and
-    // committed to the same barrier; the response threads add the parts
+    // own TMEM columns, issued by lane 0 of warp c and committed to the same
+    // barrier; the response threads add the parts
     if (warp < kAcc && lane == 0 && !sh.fail) {
       tc_fence_after();
       // K slice kc = 16 kc .. 16 kc + 15: its 64-element atom, then 32 bytes per
